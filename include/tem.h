@@ -1,0 +1,195 @@
+/* tem.h -- C ABI of the GB300 shifted-system TEM library (libtem.so).
+ *
+ * The library evaluates, on one GPU, the hot path of a Gauss-Newton step of
+ * 3-D transient EM inversion with a rational approximation of the matrix
+ * exponential (Borner, Guttel, Gunther, "Scalable Parallel 3-D TEM Inversion
+ * via Rational Approximation of the Matrix Exponential"):
+ *
+ *   u(t_j) ~ 2 Re sum_i alpha_i^[j] (K - xi_i M)^-1 f            (Section 2.3)
+ *   d_j    = Q u(t_j)                                            (Section 3)
+ *   J_j v  = 2 Re sum_i alpha_i^[j] xi_i Q A_i^-1 [(dM/dm) g_i v]  (Section 3.1)
+ *   J^T w  = sum_j J_j^T w_j                                     (Section 3.1)
+ *   LSQR on [W_d J; sqrt(lambda) L^1/2]                          (Section 3.3, eq. lsqr)
+ *
+ * with K the Whitney-edge curl-curl matrix (1/mu0), M(sigma) the
+ * conductivity mass matrix, A_i = K - xi_i M complex symmetric, g_i = A_i^-1 f,
+ * m = ln(sigma) on the parameter cells, dM/dm_e = sigma_e M1_e.
+ *
+ * Conventions
+ *  - Every call returns an int status: TEM_OK (0) or a negative TEM_ERR_*.
+ *    tem_last_error() returns a message owned by the context (valid until the
+ *    next call on that context).
+ *  - "host" arrays are read during the call only.  "dev" arrays are
+ *    caller-owned device pointers on the context's GPU, contiguous, valid for
+ *    the duration of the call; the library never frees them.
+ *  - The library owns every factor, symbolic table and work buffer; all are
+ *    released by tem_destroy().
+ *  - Device work is issued on the stream given to tem_create(); calls return
+ *    after the stream is synchronised (status words are read back).
+ *  - Calls out of order (e.g. tem_jvp before tem_forward) return
+ *    TEM_ERR_STATE.  Sizes that do not match the context return TEM_ERR_ARG.
+ *  - Data vectors are laid out d[x][r][j] (transmitter, receiver, time),
+ *    row-major, FP64.  Model vectors are FP64 over the parameter cells in
+ *    tetrahedron order.
+ */
+#ifndef TEM_H
+#define TEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TEM_OK 0
+#define TEM_ERR_ARG (-1)     /* bad argument or size */
+#define TEM_ERR_OOM (-2)     /* device memory exhausted */
+#define TEM_ERR_PIVOT (-3)   /* a pivot of some A_i underflowed (singular shift) */
+#define TEM_ERR_TIMEOUT (-4) /* a bounded device wait expired */
+#define TEM_ERR_CUDA (-5)    /* CUDA runtime error */
+#define TEM_ERR_STATE (-6)   /* call out of order */
+#define TEM_ERR_MESH (-7)    /* degenerate mesh / source / receiver */
+
+/* Arithmetic of the factors and solves. */
+#define TEM_FP64 0         /* complex double throughout */
+#define TEM_FP32_REFINED 1 /* complex float factors and solves, FP64 iterative
+                              refinement (residual K - xi M in FP64) */
+
+typedef struct tem_ctx tem_ctx;
+
+typedef struct tem_stats {
+  int64_t n_dof;         /* N: interior edges (unknowns) */
+  int64_t n_tet;         /* tetrahedra */
+  int64_t n_param;       /* P: parameter cells */
+  int64_t n_faces_reg;   /* rows of the regulariser root W */
+  int64_t n_fronts;      /* supernodes of the assembly tree */
+  int64_t n_levels;      /* height of the assembly tree + 1 */
+  int64_t nnz_a;         /* nonzeros of A (full symmetric pattern) */
+  int64_t nnz_l;         /* stored factor entries per pole (incl. diagonal) */
+  double flops_factor;   /* complex MACs of one pole's factorisation */
+  int64_t max_front;     /* largest front order */
+  int64_t bytes_device;  /* device bytes held by the context */
+  int32_t m;             /* pole pairs */
+  int32_t n_times;       /* K */
+  int32_t n_tx, n_rx;
+  int32_t precision;
+  int32_t refine_steps;  /* refinement corrections per solve (FP32 mode) */
+  int32_t last_pivot_front; /* front of the last pivot failure, -1 if none */
+  double min_pivot_abs;  /* smallest |d_kk| seen in the last factorisation */
+} tem_stats;
+
+/* Create a context on the current CUDA device.  precision: TEM_FP64 or
+ * TEM_FP32_REFINED.  stream: a cudaStream_t (NULL = legacy default stream). */
+int tem_create(tem_ctx **ctx, int precision, void *stream);
+
+/* Release everything the context owns.  ctx may be NULL. */
+int tem_destroy(tem_ctx *ctx);
+
+/* Message of the last failure on ctx (or on context creation if ctx NULL). */
+const char *tem_last_error(tem_ctx *ctx);
+
+/* Mesh, conductivity and parameterisation (Section 2.2, Section 3).
+ *   xyz      host [n_vert][3]  vertex coordinates (m)
+ *   tets     host [n_tet][4]   vertex ids of each tetrahedron (any order)
+ *   sigma    host [n_tet]      conductivity (S/m) of every cell; the values
+ *                              of parameter cells are overwritten by
+ *                              exp(log_sigma) in tem_factor
+ *   is_param host [n_tet]      1 = inverted cell (model parameter), else 0
+ * Builds edges, removes edges on the outer boundary (PEC, Section 2.1), the element
+ * matrices, the nested-dissection ordering, the assembly tree and the
+ * regulariser root W = M_div^-1/2 D^T over the parameter cells (Section 3.2), and
+ * uploads the index tables.  leaf_max: largest leaf of the dissection
+ * (0 = default).  May be called once per context. */
+int tem_mesh(tem_ctx *ctx, int64_t n_vert, const double *xyz, int64_t n_tet,
+             const int32_t *tets, const double *sigma, const uint8_t *is_param,
+             int32_t leaf_max);
+
+/* Poles and residues of the rational approximant (Section 2.3).
+ *   xi    host [m][2]        (re, im) of xi_i; each stands for the pair
+ *                            {xi_i, conj xi_i}; system A_i = K - xi_i M
+ *   alpha host [m][n_times][2] (re, im) of alpha_i^[j]
+ * Re xi_i must be < 0 (keeps A_i's real part positive definite). */
+int tem_poles(tem_ctx *ctx, int32_t m, const double *xi, int32_t n_times,
+              const double *alpha);
+
+/* Transmitters and receivers (Section 2.1 source, Section 4.2 observation).
+ *   loop_ptr  host [n_tx+1]  offsets into loop_verts
+ *   loop_verts host          closed polylines of vertex ids; consecutive ids
+ *                            (and last->first) must share a mesh edge; I = 1 A
+ *   rx        host [n_rx][3] receiver positions on a horizontal mesh surface;
+ *                            Q = -(curl e)_z by Stokes on the surface
+ *                            triangles whose closure holds the receiver
+ *                            (area-weighted when it lies on an edge/vertex). */
+int tem_sources(tem_ctx *ctx, int32_t n_tx, const int64_t *loop_ptr,
+                const int32_t *loop_verts, int32_t n_rx, const double *rx);
+
+/* Factor every shifted matrix A_i = K - xi_i M(sigma) (Algorithm 1), with
+ * sigma = exp(log_sigma) on the parameter cells.
+ *   log_sigma dev [P] FP64.
+ * Returns TEM_ERR_PIVOT if a pivot underflows. */
+int tem_factor(tem_ctx *ctx, const double *log_sigma);
+
+/* Forward responses: g_i = A_i^-1 f_x for all poles and transmitters
+ * (kept for the Jacobian products), then d[x][r][j] = 2 Re sum_i
+ * alpha_i^[j] (Q g_i,x)_r.   d dev [n_tx][n_rx][n_times] FP64. */
+int tem_forward(tem_ctx *ctx, double *d);
+
+/* J v.   v dev [P] FP64,  jv dev [n_tx][n_rx][n_times] FP64. */
+int tem_jvp(tem_ctx *ctx, const double *v, double *jv);
+
+/* J^T w.  w dev [n_tx][n_rx][n_times] FP64,  jtw dev [P] FP64. */
+int tem_jtvp(tem_ctx *ctx, const double *w, double *jtw);
+
+/* One Gauss-Newton LSQR solve (Section 3.3, eq. lsqr): n_iter iterations of
+ * Paige-Saunders LSQR, no stopping test, on
+ *   min || [W_d J; sqrt(lambda) W] dm + [W_d (d - d_obs); sqrt(lambda) W (m - m_ref)] ||
+ * at the model of the last tem_factor and the data of the last tem_forward.
+ *   d_obs dev [n_tx][n_rx][n_times], wd dev [same] (diagonal of W_d),
+ *   m_ref dev [P], dm dev [P] (output).  Each iteration is one J v and one
+ *   J^T w ("pair"); all scalars stay on the device in FP64. */
+int tem_lsqr(tem_ctx *ctx, const double *d_obs, const double *wd,
+             const double *m_ref, double lambda, int32_t n_iter, double *dm);
+
+/* TEM_FP32_REFINED mode: refinement corrections per solve (default 6) and
+ * the conductivity floor of the factored matrices (default 1e-4).
+ *
+ * The complex-float factor is of P_i = K - xi_i M(s_i) with the cell
+ * conductivity raised to s_i,t = max(sigma_t, floor_tau / (|xi_i| mu0 h_t^2)),
+ * h_t^2 = vol_t^(2/3); every correction solves with P_i, the residual
+ * b - (K - xi_i M(sigma)) x is formed in FP64 with the true matrix.  Without
+ * the floor the gradient fields of resistive cells (air, 1e-8 S/m) have pivots
+ * below float resolution and the refinement diverges.  Gradients of nodes
+ * whose cells are all floored are eigenvectors of P_i^-1 A_i, every
+ * right-hand side of the path is orthogonal to them and no output reads
+ * them, so the refined data converge to those of A_i.  The FP64 mode factors
+ * A_i itself.  steps in 0..20, floor_tau in [0, 1]. */
+int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau);
+
+/* Time one class of kernels with CUDA events on the context's stream:
+ * 0 trailing update, 1 panel, 2 forward-solve step, 3 backward-solve step,
+ * 4 backward update-row product, 5 extend-add; -1 switches timing off (the
+ * default).  Timing adds an event pair around each launch of that class. */
+int tem_set_profiling(tem_ctx *ctx, int kernel_class);
+
+/* Accumulated device time (ms) and launch count of the timed class since the
+ * last tem_set_profiling. */
+int tem_kernel_time(tem_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* Sizes and counters. */
+int tem_info(tem_ctx *ctx, tem_stats *out);
+
+/* Host copy of the assembled matrices in the library's DoF numbering, for
+ * inspection and tests: K (and M at the last factor) in CSR, FP64.
+ * Pass NULL pointers to query nnz first (returned in *nnz). */
+int tem_export_pattern(tem_ctx *ctx, int64_t *nnz, int64_t *row_ptr,
+                       int32_t *col, double *k_val, double *m_val);
+
+/* Permutation: perm[new] = interior-edge index in the library's own edge
+ * numbering, and the edge's two vertex ids (lower first), host arrays of
+ * length N and [N][2]. */
+int tem_export_dofs(tem_ctx *ctx, int64_t *edge_verts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TEM_H */

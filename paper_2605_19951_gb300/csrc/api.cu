@@ -1,0 +1,714 @@
+// C ABI of libtem (see include/tem.h): context, device memory, and the
+// orchestration of factor / forward / J v / J^T w / LSQR on one GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tem.h"
+#include "kernels.h"
+#include "tem_internal.h"
+
+using namespace tem;
+
+namespace tem {
+thread_local Profiler *g_prof = nullptr;
+
+void Profiler::begin(int c, cudaStream_t s) {
+  if (!on || c != cls) return;
+  if (used + 2 > (int)pool.size()) {
+    size_t old = pool.size();
+    pool.resize(std::max<size_t>(64, 2 * old + 2));
+    for (size_t i = old; i < pool.size(); i++) cudaEventCreate(&pool[i]);
+  }
+  cudaEventRecord(pool[used], s);
+}
+void Profiler::end(int c, cudaStream_t s) {
+  if (!on || c != cls) return;
+  cudaEventRecord(pool[used + 1], s);
+  used += 2;
+}
+void Profiler::collect() {
+  for (int i = 0; i + 1 < used; i += 2) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, pool[i], pool[i + 1]);
+    total_ms += ms;
+    launches++;
+  }
+  used = 0;
+}
+void Profiler::release() {
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+  used = 0;
+}
+}  // namespace tem
+
+namespace {
+
+enum StateBits { ST_MESH = 1, ST_POLES = 2, ST_SOURCES = 4, ST_FACTORED = 8, ST_FORWARD = 16 };
+
+template <typename T>
+struct DVec {
+  T *p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct tem_ctx {
+  int precision = TEM_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  int state = 0;
+  int refine = 6;
+  double floor_tau = 1e-4;   // FP32 mode: conductivity floor of the factored matrix
+  int64_t bytes = 0;
+  std::vector<void *> allocs;
+  Profiler prof;
+
+  Mesh mesh;
+  Symbolic sym;
+  std::vector<LevelDev> levels;
+  int max_level_fronts = 0;
+
+  // mesh tables
+  double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
+  double *tetfloor = nullptr, *mval_fact = nullptr;   // FP32 mode: per-pole floored M values
+  int64_t *rp = nullptr, *mc_ptr = nullptr, *inc_ptr = nullptr, *orig_nz = nullptr, *orig_dst = nullptr;
+  int32_t *ci = nullptr, *inc_tet = nullptr, *tdof = nullptr, *pidx = nullptr, *ptet = nullptr;
+  uint32_t *mc_idx = nullptr;
+  int8_t *inc_loc = nullptr;
+  FrontDev *fronts = nullptr;
+  int32_t *rows = nullptr, *rel = nullptr, *ea_child = nullptr, *ea_col = nullptr, *levfronts = nullptr;
+  int64_t *w_rp = nullptr, *wt_rp = nullptr;
+  int32_t *w_ci = nullptr, *wt_ci = nullptr;
+  double *w_val = nullptr, *wt_val = nullptr;
+
+  // poles
+  int m = 0, K = 0;
+  std::vector<double> xi_h, alpha_h;
+  double2 *xi = nullptr, *alpha = nullptr;
+
+  // sources
+  int n_tx = 0, n_rx = 0, n_qdof = 0;
+  double *f = nullptr;
+  int64_t *q_rp = nullptr, *qt_rp = nullptr;
+  int32_t *q_ci = nullptr, *qt_ci = nullptr, *qt_dof = nullptr;
+  double *q_val = nullptr, *qt_val = nullptr;
+
+  // numeric
+  void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr;
+  DevStatus *status = nullptr;
+  c128 *g = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *fb = nullptr;
+  double *colmax = nullptr;
+  DevStatus status_h{};
+
+  // LSQR
+  double *ls_u = nullptr, *ls_v = nullptr, *ls_w = nullptr, *ls_jv = nullptr, *ls_jtw = nullptr,
+         *ls_tmpd = nullptr, *ls_tmpp = nullptr, *ls_dm = nullptr, *ls_wv = nullptr;
+  LsqrScalars *ls_sc = nullptr;
+  double *d_cur = nullptr;   // data of the last tem_forward
+  double *m_cur = nullptr;   // model of the last tem_factor
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(tem_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(tem_ctx *c, cudaError_t e, const char *where) {
+  cudaGetLastError();
+  int code = (e == cudaErrorMemoryAllocation) ? TEM_ERR_OOM : TEM_ERR_CUDA;
+  return fail(c, code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);    \
+  } while (0)
+
+template <typename T>
+int dalloc(tem_ctx *c, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+  c->allocs.push_back(q);
+  c->bytes += int64_t(count * sizeof(T));
+  *p = (T *)q;
+  return TEM_OK;
+}
+
+template <typename T>
+int upload(tem_ctx *c, T **p, const std::vector<T> &v) {
+  int st = dalloc(c, p, v.size());
+  if (st) return st;
+  if (!v.empty()) {
+    cudaError_t e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+  }
+  return TEM_OK;
+}
+
+#define TRY(x)          \
+  do {                  \
+    int st_ = (x);      \
+    if (st_) return st_; \
+  } while (0)
+
+int sync(tem_ctx *c, const char *where) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  if (c->prof.on) c->prof.collect();
+  return TEM_OK;
+}
+
+struct ProfScope {
+  explicit ProfScope(tem_ctx *c) { g_prof = c->prof.on ? &c->prof : nullptr; }
+  ~ProfScope() { g_prof = nullptr; }
+};
+
+// Grid dimensions of every pivot step (depend on the precision's tile sizes).
+template <typename R>
+void build_steps(tem_ctx *c) {
+  const auto &S = c->sym;
+  c->levels.clear();
+  c->max_level_fronts = 0;
+  int64_t off = 0;
+  for (const Level &L : S.levels) {
+    LevelDev lv;
+    lv.nf = (int)L.fronts.size();
+    lv.fronts = c->levfronts + off;
+    off += lv.nf;
+    lv.lbeg = L.lbeg;
+    lv.lend = L.lend;
+    lv.obeg = L.obeg;
+    lv.oend = L.oend;
+    for (int s = 0; s < 2; s++) {
+      lv.ea_beg[s] = L.ea_beg[s];
+      lv.ea_end[s] = L.ea_end[s];
+    }
+    lv.bwd_upd_tiles = std::max(1, div_up(L.max_k, 8));
+    const int nsteps = div_up(L.max_k, kNB);
+    for (int s = 0; s < nsteps; s++) {
+      StepDims d{};
+      const int j0 = s * kNB;
+      for (int32_t fi : L.fronts) {
+        const Front &F = S.fronts[fi];
+        if (F.k <= j0) break;  // sorted by k descending
+        d.nfronts++;
+        const int nb = std::min(kNB, F.k - j0);
+        const int64_t below = int64_t(F.n) - j0 - nb;
+        d.panel_tiles = std::max(d.panel_tiles, std::max(1, div_up(below, kPanelRT)));
+        const int64_t T = div_up(below, UpdateTile<R>::TM);
+        d.update_tiles = (int)std::max<int64_t>(d.update_tiles, std::max<int64_t>(1, T * (T + 1) / 2));
+        d.fwd_tiles = std::max(d.fwd_tiles, std::max(1, div_up(below, SolveTile<R>::RT)));
+        d.bwd_tiles = std::max(d.bwd_tiles, std::max(1, div_up(j0, SolveTile<R>::CT)));
+      }
+      lv.steps.push_back(d);
+    }
+    c->max_level_fronts = std::max(c->max_level_fronts, lv.nf);
+    c->levels.push_back(std::move(lv));
+  }
+}
+
+template <typename R>
+FactorPlan<R> factor_plan(tem_ctx *c) {
+  FactorPlan<R> P;
+  P.m = c->m;
+  P.L = (cx<R> *)c->L;
+  P.lstride = c->sym.ltotal;
+  P.U = (cx<R> *)c->U;
+  P.ustride = c->sym.utotal;
+  P.F = c->fronts;
+  P.rel = c->rel;
+  P.ea_child = c->ea_child;
+  P.ea_col = c->ea_col;
+  P.orig_nz = c->orig_nz;
+  P.orig_dst = c->orig_dst;
+  P.kval = c->kval;
+  P.mval = c->mval_fact ? c->mval_fact : c->mval;
+  P.mstride = c->mval_fact ? (int64_t)c->mesh.kval.size() : 0;
+  P.xi = c->xi;
+  P.dscr = (cx<R> *)c->dscr;
+  P.status = c->status;
+  return P;
+}
+
+template <typename R>
+SolvePlan<R> solve_plan(tem_ctx *c) {
+  SolvePlan<R> P;
+  P.m = c->m;
+  P.nrhs = c->n_tx;
+  P.L = (const cx<R> *)c->L;
+  P.lstride = c->sym.ltotal;
+  P.F = c->fronts;
+  P.rows = c->rows;
+  P.Y = (cx<R> *)c->Y;
+  P.X = (cx<R> *)c->X;
+  P.vstride = c->mesh.N * c->n_tx;
+  return P;
+}
+
+template <typename R>
+void sweeps(tem_ctx *c) {
+  SolvePlan<R> P = solve_plan<R>(c);
+  const int H = (int)c->levels.size();
+  for (int h = 0; h < H; h++) P.forward_level(c->levels[h], c->stream);
+  for (int h = H - 1; h >= 0; h--) P.backward_level(c->levels[h], c->stream);
+}
+
+// x = A_i^-1 b for all poles; b c128 with pole stride bstride (0 = shared).
+void solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
+  const int64_t N = c->mesh.N;
+  const int nx = c->n_tx, m = c->m;
+  cudaStream_t s = c->stream;
+  if (c->precision == TEM_FP64) {
+    launch_rhs_to_work<double>(b, bstride, (c128 *)c->Y, nullptr, m, N, nx, false, s);
+    sweeps<double>(c);
+    launch_accumulate<double>((const c128 *)c->X, nullptr, x, m, N, nx, false, s);
+  } else {
+    launch_rhs_to_work<float>(b, bstride, (c64 *)c->Y, c->colmax, m, N, nx, true, s);
+    sweeps<float>(c);
+    launch_accumulate<float>((const c64 *)c->X, c->colmax, x, m, N, nx, false, s);
+    for (int it = 0; it < c->refine; it++) {
+      launch_residual(c->rp, c->ci, c->kval, c->mval, c->xi, b, bstride, x, c->r, m, N, nx, s);
+      launch_rhs_to_work<float>(c->r, N * nx, (c64 *)c->Y, c->colmax, m, N, nx, true, s);
+      sweeps<float>(c);
+      launch_accumulate<float>((const c64 *)c->X, c->colmax, x, m, N, nx, true, s);
+    }
+  }
+}
+
+int ensure_numeric(tem_ctx *c) {
+  if (c->L) return TEM_OK;
+  const size_t es = c->precision == TEM_FP64 ? sizeof(c128) : sizeof(c64);
+  const int64_t N = c->mesh.N;
+  const int m = c->m, nx = c->n_tx;
+  void *p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * c->sym.ltotal * es));
+  c->L = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * c->sym.utotal * es));
+  c->U = p;
+  TRY(dalloc(c, (char **)&p, size_t(std::max(1, c->max_level_fronts)) * m * kNB * kNB * es));
+  c->dscr = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
+  c->Y = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
+  c->X = p;
+  TRY(dalloc(c, &c->g, size_t(m) * N * nx));
+  TRY(dalloc(c, &c->b, size_t(m) * N * nx));
+  TRY(dalloc(c, &c->x, size_t(m) * N * nx));
+  if (c->precision != TEM_FP64) {
+    TRY(dalloc(c, &c->r, size_t(m) * N * nx));
+    TRY(dalloc(c, &c->mval_fact, size_t(m) * c->mesh.kval.size()));
+    std::vector<double> tf(c->mesh.nt);
+    for (int64_t t = 0; t < c->mesh.nt; t++) tf[t] = 1.0 / (kMu0 * std::pow(c->mesh.vol[t], 2.0 / 3.0));
+    TRY(upload(c, &c->tetfloor, tf));   // 1 / (mu0 h_t^2); tau applied at factor time
+  }
+  TRY(dalloc(c, &c->fb, size_t(N) * nx));
+  TRY(dalloc(c, &c->colmax, size_t(m) * nx));
+  TRY(dalloc(c, &c->d_cur, size_t(nx) * c->n_rx * c->K));
+  TRY(dalloc(c, &c->m_cur, size_t(std::max<int64_t>(1, c->mesh.P))));
+  return TEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tem_create(tem_ctx **ctx, int precision, void *stream) {
+  if (!ctx) return fail(nullptr, TEM_ERR_ARG, "ctx is NULL");
+  *ctx = nullptr;
+  if (precision != TEM_FP64 && precision != TEM_FP32_REFINED)
+    return fail(nullptr, TEM_ERR_ARG, "unknown precision");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, TEM_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  tem_ctx *c = new tem_ctx();
+  c->precision = precision;
+  c->stream = (cudaStream_t)stream;
+  c->device = dev;
+  c->refine = precision == TEM_FP64 ? 0 : 6;
+  if (dalloc(c, &c->status, 1)) {
+    std::string m = c->err;
+    delete c;
+    return fail(nullptr, TEM_ERR_OOM, m);
+  }
+  *ctx = c;
+  return TEM_OK;
+}
+
+int tem_destroy(tem_ctx *c) {
+  if (!c) return TEM_OK;
+  cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) cudaFree(p);
+  c->prof.release();
+  delete c;
+  return TEM_OK;
+}
+
+const char *tem_last_error(tem_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const int32_t *tets,
+             const double *sigma, const uint8_t *is_param, int32_t leaf_max) {
+  if (!c) return TEM_ERR_ARG;
+  if (c->state & ST_MESH) return fail(c, TEM_ERR_STATE, "mesh already set");
+  if (!xyz || !tets || !sigma || !is_param) return fail(c, TEM_ERR_ARG, "NULL mesh array");
+  std::string msg = build_mesh(c->mesh, n_vert, xyz, n_tet, tets, sigma, is_param, leaf_max, c->sym);
+  if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
+  Mesh &M = c->mesh;
+  Symbolic &S = c->sym;
+  TRY(upload(c, &c->sigma_fixed, M.sigma));
+  TRY(dalloc(c, &c->sigma, M.nt));
+  TRY(upload(c, &c->me1, M.Me1));
+  TRY(upload(c, &c->kval, M.kval));
+  TRY(dalloc(c, &c->mval, M.kval.size()));
+  TRY(upload(c, &c->rp, M.rp));
+  TRY(upload(c, &c->ci, M.ci));
+  TRY(upload(c, &c->mc_ptr, M.mc_ptr));
+  TRY(upload(c, &c->mc_idx, M.mc_idx));
+  TRY(upload(c, &c->inc_ptr, M.inc_ptr));
+  TRY(upload(c, &c->inc_tet, M.inc_tet));
+  TRY(upload(c, &c->inc_loc, M.inc_loc));
+  TRY(upload(c, &c->tdof, M.tdof));
+  TRY(upload(c, &c->pidx, M.pidx));
+  TRY(upload(c, &c->ptet, M.ptet));
+  std::vector<FrontDev> fd(S.fronts.size());
+  for (size_t i = 0; i < S.fronts.size(); i++) {
+    const Front &F = S.fronts[i];
+    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, F.n, F.k, F.c0, F.parent};
+  }
+  TRY(upload(c, &c->fronts, fd));
+  TRY(upload(c, &c->rows, S.rows));
+  TRY(upload(c, &c->rel, S.rel));
+  TRY(upload(c, &c->orig_nz, S.orig_nz));
+  TRY(upload(c, &c->orig_dst, S.orig_dst));
+  TRY(upload(c, &c->ea_child, S.ea_child));
+  TRY(upload(c, &c->ea_col, S.ea_col));
+  std::vector<int32_t> lf;
+  for (const Level &L : S.levels) lf.insert(lf.end(), L.fronts.begin(), L.fronts.end());
+  TRY(upload(c, &c->levfronts, lf));
+  TRY(upload(c, &c->w_rp, M.w_rp));
+  TRY(upload(c, &c->w_ci, M.w_ci));
+  TRY(upload(c, &c->w_val, M.w_val));
+  TRY(upload(c, &c->wt_rp, M.wt_rp));
+  TRY(upload(c, &c->wt_ci, M.wt_ci));
+  TRY(upload(c, &c->wt_val, M.wt_val));
+  if (c->precision == TEM_FP64) build_steps<double>(c);
+  else build_steps<float>(c);
+  for (const LevelDev &lv : c->levels)
+    if (lv.nf > 65535) return fail(c, TEM_ERR_MESH, "more than 65535 fronts in one tree level");
+  TRY(sync(c, "tem_mesh"));
+  c->state |= ST_MESH;
+  return TEM_OK;
+}
+
+int tem_poles(tem_ctx *c, int32_t m, const double *xi, int32_t n_times, const double *alpha) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_MESH)) return fail(c, TEM_ERR_STATE, "tem_mesh first");
+  if (c->state & ST_POLES) return fail(c, TEM_ERR_STATE, "poles already set");
+  if (m <= 0 || m > 32 || n_times <= 0 || !xi || !alpha) return fail(c, TEM_ERR_ARG, "bad poles (1 <= m <= 32)");
+  for (int i = 0; i < m; i++)
+    if (!(xi[2 * i] < 0)) return fail(c, TEM_ERR_ARG, "every pole needs Re xi < 0");
+  c->m = m;
+  c->K = n_times;
+  c->xi_h.assign(xi, xi + 2 * m);
+  c->alpha_h.assign(alpha, alpha + 2 * size_t(m) * n_times);
+  std::vector<double> xv(c->xi_h), av(c->alpha_h);
+  TRY(dalloc(c, &c->xi, m));
+  TRY(dalloc(c, &c->alpha, size_t(m) * n_times));
+  CK(cudaMemcpyAsync(c->xi, xv.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->alpha, av.data(), sizeof(double2) * m * n_times, cudaMemcpyHostToDevice, c->stream));
+  TRY(sync(c, "tem_poles"));
+  c->state |= ST_POLES;
+  return TEM_OK;
+}
+
+int tem_sources(tem_ctx *c, int32_t n_tx, const int64_t *loop_ptr, const int32_t *loop_verts, int32_t n_rx,
+                const double *rx) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_MESH)) return fail(c, TEM_ERR_STATE, "tem_mesh first");
+  if (c->state & ST_SOURCES) return fail(c, TEM_ERR_STATE, "sources already set");
+  if (n_tx <= 0 || n_rx <= 0 || !loop_ptr || !loop_verts || !rx) return fail(c, TEM_ERR_ARG, "bad sources");
+  std::vector<double> f, q_val, qt_val;
+  std::vector<int64_t> q_rp, qt_rp;
+  std::vector<int32_t> q_ci, qt_ci, qt_dof;
+  std::string msg = build_sources(c->mesh, n_tx, loop_ptr, loop_verts, n_rx, rx, f, q_rp, q_ci, q_val, qt_dof,
+                                  qt_rp, qt_ci, qt_val);
+  if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
+  c->n_tx = n_tx;
+  c->n_rx = n_rx;
+  c->n_qdof = (int)qt_dof.size();
+  TRY(upload(c, &c->f, f));
+  TRY(upload(c, &c->q_rp, q_rp));
+  TRY(upload(c, &c->q_ci, q_ci));
+  TRY(upload(c, &c->q_val, q_val));
+  TRY(upload(c, &c->qt_dof, qt_dof));
+  TRY(upload(c, &c->qt_rp, qt_rp));
+  TRY(upload(c, &c->qt_ci, qt_ci));
+  TRY(upload(c, &c->qt_val, qt_val));
+  TRY(sync(c, "tem_sources"));
+  c->state |= ST_SOURCES;
+  return TEM_OK;
+}
+
+int tem_factor(tem_ctx *c, const double *log_sigma) {
+  if (!c) return TEM_ERR_ARG;
+  const int need = ST_MESH | ST_POLES | ST_SOURCES;
+  if ((c->state & need) != need) return fail(c, TEM_ERR_STATE, "tem_mesh, tem_poles and tem_sources first");
+  if (!log_sigma && c->mesh.P > 0) return fail(c, TEM_ERR_ARG, "log_sigma is NULL");
+  TRY(ensure_numeric(c));
+  ProfScope ps(c);
+  cudaStream_t s = c->stream;
+  const Mesh &M = c->mesh;
+  CK(cudaMemcpyAsync(c->sigma, c->sigma_fixed, sizeof(double) * M.nt, cudaMemcpyDeviceToDevice, s));
+  if (M.P > 0) {
+    CK(cudaMemcpyAsync(c->m_cur, log_sigma, sizeof(double) * M.P, cudaMemcpyDeviceToDevice, s));
+    launch_sigma(log_sigma, c->ptet, M.P, c->sigma, s);
+  }
+  launch_mvals(c->mc_ptr, c->mc_idx, c->sigma, c->me1, (int64_t)M.kval.size(), c->mval, s);
+  if (c->mval_fact)
+    launch_mvals_floor(c->mc_ptr, c->mc_idx, c->sigma, c->tetfloor, c->me1, c->xi, c->floor_tau, c->m,
+                       (int64_t)M.kval.size(), c->mval_fact, s);
+  DevStatus init{};
+  init.pivot_fail = 0;
+  init.pivot_front = -1;
+  double big = 1e308;
+  memcpy(&init.min_pivot_bits, &big, sizeof(double));
+  CK(cudaMemcpyAsync(c->status, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+  const int H = (int)c->levels.size();
+  if (c->precision == TEM_FP64) {
+    FactorPlan<double> P = factor_plan<double>(c);
+    for (int h = 0; h < H; h++) P.level(h, c->levels[h], s);
+  } else {
+    FactorPlan<float> P = factor_plan<float>(c);
+    for (int h = 0; h < H; h++) P.level(h, c->levels[h], s);
+  }
+  CK(cudaMemcpyAsync(&c->status_h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  TRY(sync(c, "tem_factor"));
+  c->state &= ~(ST_FACTORED | ST_FORWARD);
+  if (c->status_h.pivot_fail) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "pivot underflow in front %d", c->status_h.pivot_front);
+    return fail(c, TEM_ERR_PIVOT, buf);
+  }
+  c->state |= ST_FACTORED;
+  return TEM_OK;
+}
+
+int tem_forward(tem_ctx *c, double *d) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_FACTORED)) return fail(c, TEM_ERR_STATE, "tem_factor first");
+  if (!d) return fail(c, TEM_ERR_ARG, "d is NULL");
+  ProfScope ps(c);
+  cudaStream_t s = c->stream;
+  const int64_t N = c->mesh.N;
+  launch_real_to_c128(c->f, c->fb, N * c->n_tx, s);
+  solve_all(c, c->fb, 0, c->g);
+  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->g, d, c->m, N, c->n_tx, c->n_rx, c->K, s);
+  CK(cudaMemcpyAsync(c->d_cur, d, sizeof(double) * c->n_tx * c->n_rx * c->K, cudaMemcpyDeviceToDevice, s));
+  TRY(sync(c, "tem_forward"));
+  c->state |= ST_FORWARD;
+  return TEM_OK;
+}
+
+namespace {
+void jvp_async(tem_ctx *c, const double *v, double *jv) {
+  const int64_t N = c->mesh.N;
+  launch_dm_apply(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->pidx, v, c->sigma, c->me1, c->xi, c->g, c->b,
+                  c->m, N, c->n_tx, c->stream);
+  solve_all(c, c->b, N * c->n_tx, c->x);
+  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->n_tx, c->n_rx, c->K, c->stream);
+}
+void jtvp_async(tem_ctx *c, const double *w, double *jtw) {
+  const int64_t N = c->mesh.N;
+  launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->n_tx,
+                c->n_rx, c->K, c->stream);
+  solve_all(c, c->b, N * c->n_tx, c->x);
+  launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->n_tx,
+                  c->stream);
+}
+}  // namespace
+
+int tem_jvp(tem_ctx *c, const double *v, double *jv) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
+  if (!v || !jv) return fail(c, TEM_ERR_ARG, "NULL vector");
+  ProfScope ps(c);
+  jvp_async(c, v, jv);
+  return sync(c, "tem_jvp");
+}
+
+int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
+  if (!w || !jtw) return fail(c, TEM_ERR_ARG, "NULL vector");
+  ProfScope ps(c);
+  jtvp_async(c, w, jtw);
+  return sync(c, "tem_jtvp");
+}
+
+int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref, double lambda,
+             int32_t n_iter, double *dm) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
+  if (!d_obs || !wd || !m_ref || !dm || n_iter < 0 || !(lambda >= 0)) return fail(c, TEM_ERR_ARG, "bad LSQR args");
+  const int64_t nd = int64_t(c->n_tx) * c->n_rx * c->K, P = c->mesh.P, nf = c->mesh.nf;
+  if (!c->ls_u) {
+    TRY(dalloc(c, &c->ls_u, nd + nf));
+    TRY(dalloc(c, &c->ls_v, P));
+    TRY(dalloc(c, &c->ls_w, P));
+    TRY(dalloc(c, &c->ls_jv, nd));
+    TRY(dalloc(c, &c->ls_jtw, P));
+    TRY(dalloc(c, &c->ls_tmpd, nd));
+    TRY(dalloc(c, &c->ls_tmpp, P));
+    TRY(dalloc(c, &c->ls_wv, std::max<int64_t>(nf, 1)));
+    TRY(dalloc(c, &c->ls_sc, 1));
+  }
+  ProfScope ps(c);
+  cudaStream_t s = c->stream;
+  const double sl = std::sqrt(lambda);
+  double *u1 = c->ls_u, *u2 = c->ls_u + nd;
+  LsqrScalars *sc = c->ls_sc;
+  CK(cudaMemsetAsync(sc, 0, sizeof(LsqrScalars), s));
+  // u = b = -[W_d (d - d_obs); sqrt(lam) W (m - m_ref)]
+  launch_lsqr_kernel(6, sc, u1, c->d_cur, d_obs, wd, nd, s);
+  launch_csr_mv(c->w_rp, c->w_ci, c->w_val, c->m_cur, u2, nf, -sl, 0.0, s);
+  launch_csr_mv(c->w_rp, c->w_ci, c->w_val, m_ref, u2, nf, sl, 1.0, s);
+  launch_sumsq(c->ls_u, nd + nf, &sc->sumsq, s);
+  launch_lsqr_kernel(0, sc, c->ls_u, nullptr, nullptr, nullptr, nd + nf, s);
+  launch_lsqr_scalars(sc, 0, s);  // beta
+  // v = A^T u
+  launch_lsqr_kernel(5, sc, c->ls_tmpd, u1, wd, nullptr, nd, s);
+  jtvp_async(c, c->ls_tmpd, c->ls_jtw);
+  CK(cudaMemcpyAsync(c->ls_v, c->ls_jtw, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
+  launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, c->ls_v, P, sl, 1.0, s);
+  launch_sumsq(c->ls_v, P, &sc->sumsq, s);
+  launch_lsqr_kernel(1, sc, c->ls_v, nullptr, nullptr, nullptr, P, s);
+  launch_lsqr_scalars(sc, 1, s);  // alpha
+  launch_lsqr_scalars(sc, 2, s);  // phibar, rhobar
+  CK(cudaMemcpyAsync(c->ls_w, c->ls_v, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(dm, 0, sizeof(double) * P, s));
+  for (int it = 0; it < n_iter; it++) {
+    // u = A v - alpha u
+    jvp_async(c, c->ls_v, c->ls_jv);
+    launch_lsqr_kernel(2, sc, u1, c->ls_jv, wd, nullptr, nd, s);
+    launch_csr_mv(c->w_rp, c->w_ci, c->w_val, c->ls_v, c->ls_wv, nf, sl, 0.0, s);
+    launch_lsqr_kernel(7, sc, u2, c->ls_wv, nullptr, nullptr, nf, s);  // u2 = sl W v - alpha u2
+    launch_sumsq(c->ls_u, nd + nf, &sc->sumsq, s);
+    launch_lsqr_kernel(0, sc, c->ls_u, nullptr, nullptr, nullptr, nd + nf, s);
+    launch_lsqr_scalars(sc, 0, s);  // beta
+    // v = A^T u - beta v
+    launch_lsqr_kernel(5, sc, c->ls_tmpd, u1, wd, nullptr, nd, s);
+    jtvp_async(c, c->ls_tmpd, c->ls_jtw);
+    launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, c->ls_jtw, P, sl, 1.0, s);
+    launch_lsqr_kernel(3, sc, c->ls_v, c->ls_jtw, nullptr, nullptr, P, s);
+    launch_sumsq(c->ls_v, P, &sc->sumsq, s);
+    launch_lsqr_kernel(1, sc, c->ls_v, nullptr, nullptr, nullptr, P, s);
+    launch_lsqr_scalars(sc, 1, s);  // alpha
+    launch_lsqr_scalars(sc, 3, s);  // rho, c, s, theta, phi
+    launch_lsqr_kernel(4, sc, dm, c->ls_w, c->ls_v, nullptr, P, s);
+  }
+  return sync(c, "tem_lsqr");
+}
+
+int tem_set_refine(tem_ctx *c, int32_t steps, double floor_tau) {
+  if (!c) return TEM_ERR_ARG;
+  if (steps < 0 || steps > 20) return fail(c, TEM_ERR_ARG, "refine steps in 0..20");
+  if (!(floor_tau >= 0) || floor_tau > 1.0) return fail(c, TEM_ERR_ARG, "floor_tau in [0, 1]");
+  c->refine = steps;
+  c->floor_tau = floor_tau;
+  return TEM_OK;
+}
+
+int tem_info(tem_ctx *c, tem_stats *o) {
+  if (!c || !o) return TEM_ERR_ARG;
+  memset(o, 0, sizeof(*o));
+  o->n_dof = c->mesh.N;
+  o->n_tet = c->mesh.nt;
+  o->n_param = c->mesh.P;
+  o->n_faces_reg = c->mesh.nf;
+  o->n_fronts = (int64_t)c->sym.fronts.size();
+  o->n_levels = (int64_t)c->sym.levels.size();
+  o->nnz_a = (int64_t)c->mesh.ci.size();
+  o->nnz_l = c->sym.nnz_l;
+  o->flops_factor = c->sym.flops;
+  o->max_front = c->sym.max_front;
+  o->bytes_device = c->bytes;
+  o->m = c->m;
+  o->n_times = c->K;
+  o->n_tx = c->n_tx;
+  o->n_rx = c->n_rx;
+  o->precision = c->precision;
+  o->refine_steps = c->refine;
+  o->last_pivot_front = c->status_h.pivot_fail ? c->status_h.pivot_front : -1;
+  double mp;
+  memcpy(&mp, &c->status_h.min_pivot_bits, sizeof(double));
+  o->min_pivot_abs = mp;
+  return TEM_OK;
+}
+
+int tem_export_pattern(tem_ctx *c, int64_t *nnz, int64_t *row_ptr, int32_t *col, double *k_val, double *m_val) {
+  if (!c || !nnz) return TEM_ERR_ARG;
+  if (!(c->state & ST_MESH)) return fail(c, TEM_ERR_STATE, "tem_mesh first");
+  const Mesh &M = c->mesh;
+  *nnz = (int64_t)M.ci.size();
+  if (row_ptr) memcpy(row_ptr, M.rp.data(), sizeof(int64_t) * M.rp.size());
+  if (col) memcpy(col, M.ci.data(), sizeof(int32_t) * M.ci.size());
+  if (k_val) memcpy(k_val, M.kval.data(), sizeof(double) * M.kval.size());
+  if (m_val) {
+    if (!(c->state & ST_FACTORED)) return fail(c, TEM_ERR_STATE, "M values exist after tem_factor");
+    CK(cudaMemcpy(m_val, c->mval, sizeof(double) * M.kval.size(), cudaMemcpyDeviceToHost));
+  }
+  return TEM_OK;
+}
+
+int tem_export_dofs(tem_ctx *c, int64_t *edge_verts) {
+  if (!c || !edge_verts) return TEM_ERR_ARG;
+  if (!(c->state & ST_MESH)) return fail(c, TEM_ERR_STATE, "tem_mesh first");
+  const Mesh &M = c->mesh;
+  std::vector<int64_t> old_edge(M.N);
+  for (int64_t e = 0; e < M.ne; e++)
+    if (M.dof_old[e] >= 0) old_edge[M.dof_old[e]] = e;
+  for (int64_t i = 0; i < M.N; i++) {
+    int64_t e = old_edge[M.perm[i]];
+    edge_verts[2 * i] = M.ev[2 * e];
+    edge_verts[2 * i + 1] = M.ev[2 * e + 1];
+  }
+  return TEM_OK;
+}
+
+int tem_set_profiling(tem_ctx *c, int kernel_class) {
+  if (!c) return TEM_ERR_ARG;
+  if (kernel_class < -1 || kernel_class >= KC_COUNT) return fail(c, TEM_ERR_ARG, "bad kernel class");
+  c->prof.on = kernel_class >= 0;
+  c->prof.cls = kernel_class;
+  c->prof.total_ms = 0;
+  c->prof.launches = 0;
+  c->prof.used = 0;
+  return TEM_OK;
+}
+
+int tem_kernel_time(tem_ctx *c, double *total_ms, int64_t *launches) {
+  if (!c || !total_ms || !launches) return TEM_ERR_ARG;
+  *total_ms = c->prof.total_ms;
+  *launches = c->prof.launches;
+  return TEM_OK;
+}
+
+}  // extern "C"

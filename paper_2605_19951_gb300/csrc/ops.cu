@@ -1,0 +1,429 @@
+// Vector kernels around the solves: right-hand-side staging and iterative
+// refinement (FP64 residual r = b - (K - xi M) x), residue sums through the
+// observation operator (Section 2.3, Section 3), the element-local mass-derivative
+// products of J v and J^T w (Section 3.1), sparse matrix-vector products of the
+// regulariser root, and the device-scalar LSQR steps (Section 3.3).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tem {
+
+// ---- right-hand sides and refinement ---------------------------------------
+
+__global__ void k_colmax(const c128 *__restrict__ b, int64_t bstride, double *colmax, int64_t N,
+                         int nrhs) {
+  const int p = blockIdx.y;
+  const c128 *bp = b + p * bstride;
+  const int64_t cnt = N * nrhs;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    c128 v = bp[e];
+    double a = fmax(fabs(v.x), fabs(v.y));
+    if (a > 0)
+      atomicMax((unsigned long long *)&colmax[p * nrhs + e % nrhs],
+                (unsigned long long)__double_as_longlong(a));
+  }
+}
+
+template <typename R>
+__global__ void k_rhs_to_work(const c128 *__restrict__ b, int64_t bstride, cx<R> *__restrict__ Y,
+                              const double *__restrict__ colmax, int64_t N, int nrhs) {
+  const int p = blockIdx.y;
+  const c128 *bp = b + p * bstride;
+  cx<R> *yp = Y + p * N * nrhs;
+  const int64_t cnt = N * nrhs;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    c128 v = bp[e];
+    double s = 1.0;
+    if (colmax) {
+      double c = colmax[p * nrhs + e % nrhs];
+      s = c > 0 ? 1.0 / c : 1.0;
+    }
+    yp[e] = mk<R>(R(v.x * s), R(v.y * s));
+  }
+}
+
+template <typename R>
+void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax, int m, int64_t N,
+                        int nrhs, bool scale, cudaStream_t s) {
+  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
+  if (scale) {
+    cudaMemsetAsync(colmax, 0, sizeof(double) * m * nrhs, s);
+    k_colmax<<<g, 256, 0, s>>>(b, bstride, colmax, N, nrhs);
+  }
+  k_rhs_to_work<R><<<g, 256, 0, s>>>(b, bstride, Y, scale ? colmax : nullptr, N, nrhs);
+}
+
+template <typename R>
+__global__ void k_accumulate(const cx<R> *__restrict__ X, const double *__restrict__ colmax,
+                             c128 *__restrict__ x, int64_t N, int nrhs, int add) {
+  const int p = blockIdx.y;
+  const cx<R> *Xp = X + p * N * nrhs;
+  c128 *xp = x + p * N * nrhs;
+  const int64_t cnt = N * nrhs;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    double s = 1.0;
+    if (colmax) {
+      double c = colmax[p * nrhs + e % nrhs];
+      s = c > 0 ? c : 1.0;
+    }
+    cx<R> v = Xp[e];
+    c128 o = add ? xp[e] : mk<double>(0.0, 0.0);
+    xp[e] = mk<double>(o.x + s * double(v.x), o.y + s * double(v.y));
+  }
+}
+
+template <typename R>
+void launch_accumulate(const cx<R> *X, const double *colmax, c128 *x, int m, int64_t N, int nrhs,
+                       bool add, cudaStream_t s) {
+  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
+  k_accumulate<R><<<g, 256, 0, s>>>(X, colmax, x, N, nrhs, add ? 1 : 0);
+}
+
+// r = b - (K - xi_p M) x for every pole; one warp per row, lanes over RHS.
+__global__ void k_residual(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ kv, const double *__restrict__ mv,
+                           const double2 *__restrict__ xi, const c128 *__restrict__ b,
+                           int64_t bstride, const c128 *__restrict__ x, c128 *__restrict__ r,
+                           int64_t N, int nrhs) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= N) return;
+  const double2 s = xi[p];
+  const c128 *xp = x + p * N * nrhs;
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int rhs = c0 + lane;
+    if (rhs >= nrhs) break;
+    c128 acc = b[p * bstride + row * nrhs + rhs];
+    for (int64_t z = rp[row]; z < rp[row + 1]; z++) {
+      const double k = kv[z], m = mv[z];
+      const c128 a = mk<double>(k - s.x * m, -s.y * m);
+      cfms(acc, a, xp[int64_t(ci[z]) * nrhs + rhs]);
+    }
+    r[p * N * nrhs + row * nrhs + rhs] = acc;
+  }
+}
+
+void launch_residual(const int64_t *rp, const int32_t *ci, const double *kv, const double *mv,
+                     const double2 *xi, const c128 *b, int64_t bstride, const c128 *x, c128 *r,
+                     int m, int64_t N, int nrhs, cudaStream_t s) {
+  dim3 g(div_up(N, 8), m);
+  k_residual<<<g, 256, 0, s>>>(rp, ci, kv, mv, xi, b, bstride, x, r, N, nrhs);
+}
+
+__global__ void k_real_to_c128(const double *__restrict__ f, c128 *__restrict__ b, int64_t cnt) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt;
+       e += int64_t(gridDim.x) * blockDim.x)
+    b[e] = mk<double>(f[e], 0.0);
+}
+
+void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s) {
+  k_real_to_c128<<<(unsigned)std::min<int64_t>(div_up(count, 256), 4096), 256, 0, s>>>(f, b, count);
+}
+
+// ---- observation and residue sums ------------------------------------------
+
+constexpr int kMaxPoles = 32;
+
+// d[x][r][j] = 2 Re sum_p alpha[p][j] (Q y_p)[r][x]
+__global__ void k_residue(const int64_t *__restrict__ q_rp, const int32_t *__restrict__ q_ci,
+                          const double *__restrict__ q_val, const double2 *__restrict__ alpha,
+                          const c128 *__restrict__ y, double *__restrict__ d, int m, int64_t N,
+                          int nrhs, int n_rx, int K) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= int64_t(n_rx) * nrhs) return;
+  const int x = int(t % nrhs), r = int(t / nrhs);
+  c128 yq[kMaxPoles];
+  for (int p = 0; p < m; p++) {
+    c128 acc = mk<double>(0.0, 0.0);
+    const c128 *yp = y + p * N * nrhs;
+    for (int64_t z = q_rp[r]; z < q_rp[r + 1]; z++) {
+      const c128 v = yp[int64_t(q_ci[z]) * nrhs + x];
+      acc.x += q_val[z] * v.x;
+      acc.y += q_val[z] * v.y;
+    }
+    yq[p] = acc;
+  }
+  for (int j = 0; j < K; j++) {
+    double s = 0;
+    for (int p = 0; p < m; p++) {
+      const double2 a = alpha[p * K + j];
+      s += a.x * yq[p].x - a.y * yq[p].y;
+    }
+    d[(int64_t(x) * n_rx + r) * K + j] = 2.0 * s;
+  }
+}
+
+void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_val,
+                    const double2 *alpha, const c128 *y, double *d, int m, int64_t N, int nrhs,
+                    int n_rx, int K, cudaStream_t s) {
+  const int64_t cnt = int64_t(n_rx) * nrhs;
+  k_residue<<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, n_rx, K);
+}
+
+// rhs_p[qdof][x] = sum_{r} Qt[qdof][r] * sum_j alpha[p][j] w[x][r][j]
+__global__ void k_qt_rhs(const int32_t *__restrict__ qt_dof, const int64_t *__restrict__ qt_rp,
+                         const int32_t *__restrict__ qt_ci, const double *__restrict__ qt_val,
+                         int n_qdof, const double2 *__restrict__ alpha, const double *__restrict__ w,
+                         c128 *__restrict__ rhs, int64_t N, int nrhs, int n_rx, int K) {
+  const int p = blockIdx.y;
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= int64_t(n_qdof) * nrhs) return;
+  const int x = int(t % nrhs), q = int(t / nrhs);
+  c128 acc = mk<double>(0.0, 0.0);
+  for (int64_t z = qt_rp[q]; z < qt_rp[q + 1]; z++) {
+    const int r = qt_ci[z];
+    const double *wr = w + (int64_t(x) * n_rx + r) * K;
+    double sr = 0, si = 0;
+    for (int j = 0; j < K; j++) {
+      const double2 a = alpha[p * K + j];
+      sr += a.x * wr[j];
+      si += a.y * wr[j];
+    }
+    acc.x += qt_val[z] * sr;
+    acc.y += qt_val[z] * si;
+  }
+  rhs[p * N * nrhs + int64_t(qt_dof[q]) * nrhs + x] = acc;
+}
+
+void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
+                   const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,
+                   int m, int64_t N, int nrhs, int n_rx, int K, cudaStream_t s) {
+  cudaMemsetAsync(rhs, 0, sizeof(c128) * m * N * nrhs, s);
+  const int64_t cnt = int64_t(n_qdof) * nrhs;
+  if (cnt == 0) return;
+  dim3 g(div_up(cnt, 128), m);
+  k_qt_rhs<<<g, 128, 0, s>>>(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, N, nrhs, n_rx, K);
+}
+
+// ---- mass-derivative products ------------------------------------------------
+
+// h_p[d][x] = xi_p sum over the tets t at unknown d (local edge a) of
+//             v_t sigma_t sum_b M1_t[a][b] g_p[tdof_t[b]][x]
+__global__ void k_dm_apply(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_tet,
+                           const int8_t *__restrict__ inc_loc, const int32_t *__restrict__ tdof,
+                           const int32_t *__restrict__ pidx, const double *__restrict__ v,
+                           const double *__restrict__ sigma, const double *__restrict__ me1,
+                           const double2 *__restrict__ xi, const c128 *__restrict__ g,
+                           c128 *__restrict__ h, int64_t N, int nrhs) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int64_t d = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (d >= N) return;
+  const c128 *gp = g + p * N * nrhs;
+  const double2 s = xi[p];
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int x = c0 + lane;
+    if (x >= nrhs) break;
+    c128 acc = mk<double>(0.0, 0.0);
+    for (int64_t q = inc_ptr[d]; q < inc_ptr[d + 1]; q++) {
+      const int32_t t = inc_tet[q];
+      const int32_t pt = pidx[t];
+      if (pt < 0) continue;
+      const double coef = v[pt] * sigma[t];
+      if (coef == 0.0) continue;
+      const int a = inc_loc[q];
+      const double *Me = me1 + int64_t(t) * 36 + a * 6;
+      c128 sum = mk<double>(0.0, 0.0);
+      for (int b = 0; b < 6; b++) {
+        const int32_t db = tdof[int64_t(t) * 6 + b];
+        if (db < 0) continue;
+        const c128 gv = gp[int64_t(db) * nrhs + x];
+        sum.x += Me[b] * gv.x;
+        sum.y += Me[b] * gv.y;
+      }
+      acc.x += coef * sum.x;
+      acc.y += coef * sum.y;
+    }
+    h[p * N * nrhs + d * nrhs + x] = mk<double>(s.x * acc.x - s.y * acc.y, s.x * acc.y + s.y * acc.x);
+  }
+}
+
+void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc,
+                     const int32_t *tdof, const int32_t *pidx, const double *v, const double *sigma,
+                     const double *me1, const double2 *xi, const c128 *g, c128 *h, int m, int64_t N,
+                     int nrhs, cudaStream_t s) {
+  dim3 gr(div_up(N, 8), m);
+  k_dm_apply<<<gr, 256, 0, s>>>(inc_ptr, inc_tet, inc_loc, tdof, pidx, v, sigma, me1, xi, g, h, N, nrhs);
+}
+
+// grad[pt] = 2 sigma_t Re sum_i xi_i sum_x (P_t z_ix)^T M1_t (P_t g_ix); one warp per cell.
+__global__ void k_bilinear(const int32_t *__restrict__ ptet, int64_t P, const int32_t *__restrict__ tdof,
+                           const double *__restrict__ sigma, const double *__restrict__ me1,
+                           const double2 *__restrict__ xi, const c128 *__restrict__ g,
+                           const c128 *__restrict__ z, double *__restrict__ grad, int m, int64_t N,
+                           int nrhs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t pt = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (pt >= P) return;
+  const int32_t t = ptet[pt];
+  int32_t td[6];
+  for (int a = 0; a < 6; a++) td[a] = tdof[int64_t(t) * 6 + a];
+  const double *Me = me1 + int64_t(t) * 36;
+  double total = 0;
+  for (int p = 0; p < m; p++) {
+    const c128 *gp = g + p * N * nrhs;
+    const c128 *zp = z + p * N * nrhs;
+    c128 acc = mk<double>(0.0, 0.0);
+    for (int x = lane; x < nrhs; x += 32) {
+      c128 gl[6], zl[6];
+      for (int a = 0; a < 6; a++) {
+        gl[a] = td[a] >= 0 ? gp[int64_t(td[a]) * nrhs + x] : mk<double>(0.0, 0.0);
+        zl[a] = td[a] >= 0 ? zp[int64_t(td[a]) * nrhs + x] : mk<double>(0.0, 0.0);
+      }
+      for (int a = 0; a < 6; a++) {
+        c128 mg = mk<double>(0.0, 0.0);
+        for (int b = 0; b < 6; b++) {
+          mg.x += Me[a * 6 + b] * gl[b].x;
+          mg.y += Me[a * 6 + b] * gl[b].y;
+        }
+        cfma(acc, zl[a], mg);
+      }
+    }
+    const double2 s = xi[p];
+    total += s.x * acc.x - s.y * acc.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
+  if (lane == 0) grad[pt] = 2.0 * sigma[t] * total;
+}
+
+void launch_bilinear(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
+                     const double *me1, const double2 *xi, const c128 *g, const c128 *z, double *grad,
+                     int m, int64_t N, int nrhs, cudaStream_t s) {
+  if (P == 0) return;
+  k_bilinear<<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
+}
+
+__global__ void k_csr_mv(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                         const double *__restrict__ val, const double *__restrict__ x,
+                         double *__restrict__ y, int64_t rows, double alpha, double beta) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    double s = 0;
+    for (int64_t z = rp[r]; z < rp[r + 1]; z++) s += val[z] * x[ci[z]];
+    y[r] = alpha * s + (beta == 0.0 ? 0.0 : beta * y[r]);
+  }
+}
+
+void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,
+                   int64_t rows, double alpha, double beta, cudaStream_t s) {
+  if (rows == 0) return;
+  k_csr_mv<<<(unsigned)std::min<int64_t>(div_up(rows, 256), 4096), 256, 0, s>>>(rp, ci, val, x, y, rows,
+                                                                                alpha, beta);
+}
+
+// ---- LSQR (all scalars on the device) ----------------------------------------
+
+__global__ void k_sumsq(const double *__restrict__ x, int64_t n, double *out) {
+  double s = 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n;
+       e += int64_t(gridDim.x) * blockDim.x)
+    s += x[e] * x[e];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+void launch_sumsq(const double *x, int64_t n, double *out, cudaStream_t s) {
+  if (n == 0) return;
+  k_sumsq<<<(unsigned)std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(x, n, out);
+}
+
+// LSQR element-wise steps; op selects the formula, scalars come from sc.
+//   0: a = a / sqrt(sumsq)          (normalise; beta <- norm)
+//   1: a = a / sqrt(sumsq)          (normalise; alpha <- norm)
+//   2: a = b * c - alpha * a         (u1 <- W_d (J v) - alpha u1)
+//   3: a = b - beta * a              (v <- (A^T u) - beta v)
+//   4: x(a) += phi/rho * w(b); w(b) = v(c) - theta/rho * w(b)
+//   5: a = b * c                     (element-wise product)
+//   6: a = -(b - c) * wd             (u1 <- -W_d (d - d_obs))
+//   7: a = b - alpha * a             (u2 <- sqrt(lam) W v - alpha u2)
+__global__ void k_lsqr(int op, LsqrScalars *sc, double *__restrict__ a, const double *__restrict__ b,
+                       const double *__restrict__ c, const double *__restrict__ wd, int64_t n) {
+  const int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t st = int64_t(gridDim.x) * blockDim.x;
+  if (op == 0 || op == 1) {
+    const double nrm = sqrt(sc->sumsq);
+    const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+    for (int64_t i = i0; i < n; i += st) a[i] *= inv;
+  } else if (op == 2) {
+    const double al = sc->alpha;
+    for (int64_t i = i0; i < n; i += st) a[i] = b[i] * c[i] - al * a[i];
+  } else if (op == 3) {
+    const double be = sc->beta;
+    for (int64_t i = i0; i < n; i += st) a[i] = b[i] - be * a[i];
+  } else if (op == 4) {
+    const double f1 = sc->phi / sc->rho, f2 = sc->theta / sc->rho;
+    double *w = const_cast<double *>(b);
+    for (int64_t i = i0; i < n; i += st) {
+      const double wi = w[i];
+      a[i] += f1 * wi;
+      w[i] = c[i] - f2 * wi;
+    }
+  } else if (op == 5) {
+    for (int64_t i = i0; i < n; i += st) a[i] = b[i] * c[i];
+  } else if (op == 6) {
+    for (int64_t i = i0; i < n; i += st) a[i] = -(b[i] - c[i]) * wd[i];
+  } else if (op == 7) {
+    const double al = sc->alpha;
+    for (int64_t i = i0; i < n; i += st) a[i] = b[i] - al * a[i];
+  }
+}
+
+// Scalar bookkeeping: which = 0 -> beta = sqrt(sumsq); 1 -> alpha = sqrt(sumsq);
+// 2 -> start (phibar = beta, rhobar = alpha); 3 -> Givens step of one iteration.
+__global__ void k_lsqr_scalars(LsqrScalars *sc, int which) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (which == 0) {
+    sc->beta = sqrt(sc->sumsq);
+  } else if (which == 1) {
+    sc->alpha = sqrt(sc->sumsq);
+  } else if (which == 2) {
+    sc->phibar = sc->beta;
+    sc->rhobar = sc->alpha;
+  } else {
+    const double rho = hypot(sc->rhobar, sc->beta);
+    const double c = rho > 0 ? sc->rhobar / rho : 1.0;
+    const double s = rho > 0 ? sc->beta / rho : 0.0;
+    sc->rho = rho > 0 ? rho : 1.0;
+    sc->c = c;
+    sc->sn = s;
+    sc->theta = s * sc->alpha;
+    sc->rhobar = -c * sc->alpha;
+    sc->phi = c * sc->phibar;
+    sc->phibar = s * sc->phibar;
+  }
+  sc->sumsq = 0.0;
+}
+
+void launch_lsqr_kernel(int op, LsqrScalars *sc, double *a, const double *b, const double *c,
+                        const double *wd, int64_t n, cudaStream_t s) {
+  if (n == 0) return;
+  k_lsqr<<<(unsigned)std::min<int64_t>(div_up(n, 256), 2048), 256, 0, s>>>(op, sc, a, b, c, wd, n);
+}
+
+void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s) {
+  k_lsqr_scalars<<<1, 32, 0, s>>>(sc, which);
+}
+
+template void launch_rhs_to_work<float>(const c128 *, int64_t, c64 *, double *, int, int64_t, int, bool,
+                                        cudaStream_t);
+template void launch_rhs_to_work<double>(const c128 *, int64_t, c128 *, double *, int, int64_t, int, bool,
+                                         cudaStream_t);
+template void launch_accumulate<float>(const c64 *, const double *, c128 *, int, int64_t, int, bool,
+                                       cudaStream_t);
+template void launch_accumulate<double>(const c128 *, const double *, c128 *, int, int64_t, int, bool,
+                                        cudaStream_t);
+
+}  // namespace tem

@@ -1,0 +1,240 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (per data entry, floored at 1e-4 of the largest |value| of the
+same transmitter-receiver pair over time):  FP64 path 1e-9, FP32 factors with
+FP64 refinement 1e-6.  J^T w: relative 2-norm 1e-9 / 1e-6.  J v of the FP64
+path: 1e-8, ten times the spread between two FP64 runs of the oracle that
+differ only in their elimination ordering (9.9e-10 on the 20^3 box): the
+residue sum of J v cancels more than that of the response.  The shifted
+matrices are ill-conditioned on the air's gradient fields, which is why the
+comparison is made on the data, never on the solution vectors themselves.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.inversion import gn_operator, gn_rhs, lsqr, regulariser
+from oracle.tem import Oracle
+from paper_2605_19951_gb300 import inputs
+
+TOL = {"fp64": 1e-9, "fp32r": 1e-6}
+TOL_JV = {"fp64": 1e-8, "fp32r": 1e-6}
+
+
+def _tem():
+    from paper_2605_19951_gb300 import build, tem
+    import os
+    if not os.path.exists(tem.LIB_PATH):
+        build.build()
+    return tem
+
+
+def floored_err(a, ref, floor=1e-4):
+    a, ref = np.asarray(a), np.asarray(ref)
+    peak = np.abs(ref).max(axis=2, keepdims=True)
+    return np.abs(a - ref) / np.maximum(np.abs(ref), floor * peak)
+
+
+def _model(s, xi, al, prec, leaf=0):
+    tem = _tem()
+    p = tem.TEM_FP64 if prec == "fp64" else tem.TEM_FP32_REFINED
+    return tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al, precision=p, leaf_max=leaf)
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+class Case:
+    def __init__(self, idx, seed):
+        self.s = inputs.make_config(idx)
+        self.xi, self.al = inputs.load_rational(self.s.m, self.s.times)
+        rng = np.random.default_rng(seed)
+        self.m0 = self.s.log_sigma() + 0.2 * rng.standard_normal(self.s.n_param)
+        self.o = Oracle(self.s.xyz, self.s.tets, self.s.sigma, self.s.is_param, self.s.loops, self.s.rx,
+                        self.xi, self.al)
+        self.o.set_model(self.m0)
+        self.d = self.o.forward()
+        self.v = rng.standard_normal(self.s.n_param)
+        self.w = rng.standard_normal(self.d.shape)
+        self.jv = self.o.jvp(self.v)
+        self.jtw = self.o.jtvp(self.w)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return Case(1, 101)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return Case(2, 202)
+
+
+def _check_case(case, prec, leaf=0):
+    mdl = _model(case.s, case.xi, case.al, prec, leaf)
+    try:
+        mdl.factor(_cuda(case.m0))
+        d = mdl.forward().cpu().numpy()
+        assert floored_err(d, case.d).max() <= TOL[prec]
+        jv = mdl.jvp(_cuda(case.v)).cpu().numpy()
+        assert floored_err(jv, case.jv).max() <= TOL_JV[prec]
+        jtw = mdl.jtvp(_cuda(case.w)).cpu().numpy()
+        assert np.linalg.norm(jtw - case.jtw) <= TOL[prec] * np.linalg.norm(case.jtw)
+        info = mdl.info()
+        assert info["last_pivot_front"] == -1 and info["min_pivot_abs"] > 0
+    finally:
+        mdl.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
+def test_c1(c1, prec):
+    _check_case(c1, prec)
+
+
+@pytest.mark.parametrize("leaf", [8, 33, 300])
+def test_c1_leaf_sizes(c1, leaf):
+    """Different dissection leaves give ragged fronts (k not a multiple of
+    the 32-wide pivot block, single-front trees)."""
+    _check_case(c1, "fp64", leaf)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
+def test_c2(c2, prec):
+    _check_case(c2, prec)
+
+
+def test_assembly_matches_oracle(c1):
+    """K and M(sigma) of the library equal the oracle's, entry by entry, after
+    mapping unknowns through their edge end points."""
+    tem = _tem()
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        mdl.factor(_cuda(c1.m0))
+        rp, ci, kv, mv = tem.tem_export_pattern(mdl.ctx, with_m=True)
+        ev = tem.tem_export_dofs(mdl.ctx)
+    finally:
+        mdl.close()
+    fe = c1.o.fe
+    nv = fe.xyz.shape[0]
+    okey = fe.edges[:, 0] * nv + fe.edges[:, 1]
+    lkey = ev[:, 0] * nv + ev[:, 1]
+    e = np.searchsorted(okey, lkey)
+    assert np.array_equal(okey[e], lkey)
+    odof = fe.dof[e]
+    assert np.all(odof >= 0)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    K = c1.o.fe.K.tocsr()
+    M = c1.o.M.tocsr()
+    ko = np.asarray(K[odof[rows], odof[ci]]).ravel()
+    mo = np.asarray(M[odof[rows], odof[ci]]).ravel()
+    assert np.abs(kv - ko).max() <= 1e-12 * np.abs(ko).max()
+    assert np.abs(mv - mo).max() <= 1e-12 * np.abs(mo).max()
+    assert K.nnz == len(kv)
+
+
+def test_adjoint_gpu(c1):
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        mdl.factor(_cuda(c1.m0))
+        mdl.forward()
+        rng = np.random.default_rng(9)
+        for _ in range(3):
+            v = rng.standard_normal(c1.s.n_param)
+            w = rng.standard_normal(c1.d.shape)
+            a = float(np.sum(mdl.jvp(_cuda(v)).cpu().numpy() * w))
+            b = float(np.sum(v * mdl.jtvp(_cuda(w)).cpu().numpy()))
+            assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+    finally:
+        mdl.close()
+
+
+def test_many_transmitters():
+    """More than 32 right-hand sides (two RHS chunks of the solve kernels)."""
+    s = inputs.make_config(1)
+    n, na = s.n, s.n_air
+    loops = [inputs.square_loop(n, na, 1 + (i % 5), 1 + (i // 5) % 5, 1 + i % 2) for i in range(37)]
+    s.loops = loops
+    xi, al = inputs.load_rational(8, s.times)
+    rng = np.random.default_rng(37)
+    m0 = s.log_sigma()
+    o = Oracle(s.xyz, s.tets, s.sigma, s.is_param, loops, s.rx, xi, al)
+    o.set_model(m0)
+    w = rng.standard_normal((37, 1, len(s.times)))
+    ref_d, ref_jtw = o.forward(), o.jtvp(w)
+    for prec in ("fp64", "fp32r"):
+        mdl = _model(s, xi, al, prec)
+        try:
+            mdl.factor(_cuda(m0))
+            d = mdl.forward().cpu().numpy()
+            assert floored_err(d, ref_d).max() <= TOL[prec]
+            jtw = mdl.jtvp(_cuda(w)).cpu().numpy()
+            assert np.linalg.norm(jtw - ref_jtw) <= TOL[prec] * np.linalg.norm(ref_jtw)
+        finally:
+            mdl.close()
+
+
+def test_lsqr_matches_oracle(c1):
+    """Device LSQR (FP64 scalars on the GPU) against the oracle's LSQR on the
+    same Gauss-Newton system, Section 3.3."""
+    s = c1.s
+    W = regulariser(s.xyz, s.tets, s.is_param)
+    d_obs = c1.d * (1 + 0.03 * np.random.default_rng(3).standard_normal(c1.d.shape))
+    wd = 1.0 / (0.03 * np.abs(d_obs) + 1e-4 * np.abs(d_obs).max())
+    m_ref = s.log_sigma()
+    lam = 10.0
+    mv, rmv = gn_operator(c1.o, W, wd.ravel(), lam)
+    b = gn_rhs(c1.d, d_obs, wd.ravel(), W, c1.m0, m_ref, lam)
+    for n_iter, tol in ((3, 1e-9), (12, 1e-7)):
+        x_ref, _ = lsqr(mv, rmv, b, n_iter)
+        mdl = _model(s, c1.xi, c1.al, "fp64")
+        try:
+            mdl.factor(_cuda(c1.m0))
+            mdl.forward()
+            dm = mdl.lsqr(_cuda(d_obs), _cuda(wd), _cuda(m_ref), lam, n_iter).cpu().numpy()
+        finally:
+            mdl.close()
+        assert np.linalg.norm(dm - x_ref) <= tol * np.linalg.norm(x_ref), n_iter
+
+
+def test_autograd_function(c1):
+    tem = _tem()
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        m = _cuda(c1.m0).requires_grad_(True)
+        d = tem.TemForward.apply(mdl, m)
+        loss = (d * _cuda(c1.w)).sum()
+        loss.backward()
+        g = m.grad.cpu().numpy()
+        assert np.linalg.norm(g - c1.jtw) <= 1e-9 * np.linalg.norm(c1.jtw)
+    finally:
+        mdl.close()
+
+
+def test_errors_are_statuses(c1):
+    tem = _tem()
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        with pytest.raises(tem.TemError) as e:
+            mdl.jvp(_cuda(c1.v))
+        assert e.value.code == -6                      # TEM_ERR_STATE
+        with pytest.raises(tem.TemError) as e:
+            tem.tem_set_refine(mdl.ctx, 99, 3e-5)
+        assert e.value.code == -1
+    finally:
+        mdl.close()
+    ctx = tem.tem_create(tem.TEM_FP64)
+    try:
+        tem.tem_mesh(ctx, c1.s.xyz, c1.s.tets, c1.s.sigma, c1.s.is_param)
+        with pytest.raises(tem.TemError) as e:
+            tem.tem_poles(ctx, np.array([1.0 + 1j]), np.ones((1, 4)))   # Re xi >= 0 refused
+        assert e.value.code == -1
+        bad = [np.array([0, 1, 2], dtype=np.int32)]                     # not a closed mesh path
+        tem.tem_poles(ctx, c1.xi, c1.al)
+        with pytest.raises(tem.TemError) as e:
+            tem.tem_sources(ctx, bad, c1.s.rx)
+        assert e.value.code == -7
+    finally:
+        tem.tem_destroy(ctx)
