@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the shifted-system TEM hot path on one GB300.
+
+Workload: 46^3-cube Kuhn box (700,534 edges, 662,446 unknowns), two seeded
+conductive blocks (0.1, 0.3 S/m) in 0.01 S/m under 1e-8 S/m air, 32 square
+loops, 128 surface receivers, 40 times, 10 conjugate pole pairs.  Synthetic
+data: the forward of the true model plus 3% Gaussian noise; the Gauss-Newton
+step starts from the 0.01 S/m half-space (also the reference model).
+
+Metric: J.v + J^T.w pairs per second (one LSQR iteration = one pair, all
+10 poles x 32 transmitters, refinement included), with the factor time of
+all shifts reported beside it.  A step is one LSQR iteration of the
+Gauss-Newton system at the factored start model; the factor and the forward
+are timed once each before the steps.  Refined FP32 (headline) and FP64
+are measured on the same GPU.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path is
+not sharded across GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = 4
+LAMBDA = 10.0
+N_LSQR_GN = 30          # LSQR iterations of one Gauss-Newton iteration (configuration)
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+METRIC = "J.v+J^T.w pairs/s and factor time at 700k DoF, refined FP32 vs FP64, same GPU"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--n", type=int, default=46,
+                    help="cubes per side (46 = the 700k-DoF workload; smaller only for profiling captures)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ids = [x for x in vis.split(",") if x.strip()] if vis else []
+        self.index = ids[local_rank].strip() if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def synthetic(tem, s, xi, al, torch):
+    """Observed data: forward of the true model (refined FP32 library call) + 3% noise."""
+    import numpy as np
+    mdl = tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al,
+                    precision=tem.TEM_FP32_REFINED)
+    m_true = torch.as_tensor(s.log_sigma(), device="cuda")
+    mdl.factor(m_true)
+    d_true = mdl.forward().cpu().numpy()
+    rng = np.random.default_rng(19951 + CONFIG)
+    eps_a = 1e-4 * np.abs(d_true).reshape(d_true.shape[0], -1).max(axis=1)[:, None, None]
+    sd = 0.03 * np.abs(d_true) + eps_a
+    d_obs = d_true + sd * rng.standard_normal(d_true.shape)
+    wd = 1.0 / (0.03 * np.abs(d_obs) + eps_a)
+    return mdl, d_obs, wd
+
+
+def timed(torch, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2605_19951_gb300 import inputs, tem
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    s = inputs.make_config(CONFIG, n=args.n)
+    xi, al = inputs.load_rational(s.m, s.times)
+    mdl, d_obs_h, wd_h = synthetic(tem, s, xi, al, torch)
+    info = mdl.info()
+    m0 = torch.as_tensor(np.log(s.sigma_start[s.is_param.astype(bool)]), device="cuda")
+    d_obs = torch.as_tensor(d_obs_h, device="cuda")
+    wd = torch.as_tensor(wd_h, device="cuda")
+
+    # factor time of all shifts and the forward at the start model
+    factor_ms, _ = timed(torch, lambda: mdl.factor(m0))
+    forward_ms, _ = timed(torch, lambda: mdl.forward())
+
+    # which kernel class dominates a pair (one untimed profiling pass per class)
+    per_class = {}
+    for cls in ("fwd", "bwd", "bwd_upd"):
+        tem.tem_set_profiling(mdl.ctx, cls)
+        mdl.lsqr(d_obs, wd, m0, LAMBDA, 1)
+        per_class[cls] = tem.tem_kernel_time(mdl.ctx)
+    tem.tem_set_profiling(mdl.ctx, None)
+    dom = max(per_class, key=lambda c: per_class[c][0])
+
+    # warm-up, then K timed LSQR iterations in one device-resident LSQR call
+    for _ in range(args.warmup):
+        mdl.lsqr(d_obs, wd, m0, LAMBDA, 1)
+    tem.tem_set_profiling(mdl.ctx, dom)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = tem.tem_launch_count()
+    torch.cuda.nvtx.range_push("tem_timed")
+    t_ms, _ = timed(torch, lambda: mdl.lsqr(d_obs, wd, m0, LAMBDA, args.steps))
+    torch.cuda.nvtx.range_pop()
+    launches = tem.tem_launch_count() - l0
+    ck = clocks.stop()
+    barrier()
+    dom_ms, dom_launches = tem.tem_kernel_time(mdl.ctx)
+    tem.tem_set_profiling(mdl.ctx, None)
+    if dist is not None:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+
+    # end to end through the public API: pinned host inputs, result read back
+    d_obs_p = torch.as_tensor(d_obs_h).pin_memory()
+    wd_p = torch.as_tensor(wd_h).pin_memory()
+    m0_p = m0.cpu().pin_memory()
+    dm_p = torch.empty(info["n_param"], dtype=torch.float64).pin_memory()
+
+    def e2e():
+        a = d_obs_p.to("cuda", non_blocking=True)
+        b = wd_p.to("cuda", non_blocking=True)
+        c = m0_p.to("cuda", non_blocking=True)
+        dm = mdl.lsqr(a, b, c, LAMBDA, args.steps)
+        dm_p.copy_(dm, non_blocking=True)
+        return dm_p
+
+    e2e_ms, _ = timed(torch, e2e)
+    h2d = (d_obs_p.numel() + wd_p.numel() + m0_p.numel()) * 8
+    d2h = dm_p.numel() * 8
+
+    # roofline of the dominant kernel class (algorithmic flops of its share of
+    # the sweeps: complex MACs of the factor entries it applies x 32 RHS x poles)
+    N, m, nrhs = info["n_dof"], info["m"], info["n_tx"]
+    refine = info["refine_steps"]
+    solves = (2 * args.steps + 1) * (1 + refine)
+    l11_off = info["nnz_l11"] - N                 # strictly lower pivot-block entries
+    l21 = info["nnz_l"] - info["nnz_l11"]
+    cmac_per_solve = {"fwd": l11_off + l21, "bwd": l11_off, "bwd_upd": l21}[dom]
+    flops = 8.0 * cmac_per_solve * nrhs * m * solves
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    roof = {"kernel": {"fwd": "k_fwd_step", "bwd": "k_bwd_step", "bwd_upd": "k_bwd_upd"}[dom],
+            "bound": "alu", "achieved": round(achieved, 3),
+            "peak": round(FP32_SIMT_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / FP32_SIMT_PEAK_TFLOPS, 4), "traffic": None,
+            "launches": dom_launches, "avg_launch_us": round(1e3 * dom_ms / max(dom_launches, 1), 2),
+            "share_of_step": round(dom_ms / t_ms, 3),
+            "peak_note": "FP32 SIMT from unit counts x max SM clock (no measured FP32 peak in "
+                         "MEASURED_PEAKS.json); cuBLAS SGEMM measured 69.7 TFLOP/s on this GPU"}
+
+    pairs_per_s = args.steps / (t_ms * 1e-3) * world
+    out = {
+        "metric": METRIC, "value": round(pairs_per_s, 4), "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 factor/solves + f64 refinement, residue sums, LSQR",
+        "data": "synthetic (seeded model, forward of the true model + 3% noise)",
+        "config": {"workload": f"{s.n}^3 Kuhn box, {N} DoF, 10 pole pairs, 32 loops, 128 rx, 40 times",
+                   "precision": "fp32-refined", "refine_steps": refine,
+                   "l2": "inputs larger than L2 (factors %.1f GB per sweep)" % (info["nnz_l"] * m * 8 / 1e9),
+                   "step": "one LSQR iteration = one J.v + one J^T.w over all poles x transmitters"},
+        "factor_s": round(factor_ms / 1e3, 3), "forward_s": round(forward_ms / 1e3, 3),
+        "gn_iteration_s": round((factor_ms + forward_ms + N_LSQR_GN * t_ms / args.steps) / 1e3, 2),
+        "gn_iteration_note": "factor + forward + 30 LSQR pairs at the measured rates (linear model, Fig. 10)",
+        "roofline": roof,
+        "e2e": {"value": round(args.steps / (e2e_ms * 1e-3) * world, 4), "unit": "pairs/s",
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": int(launches), "clocks": ck,
+        "per_class_ms_1pair": {k: round(v[0], 2) for k, v in per_class.items()},
+    }
+    mdl.close()
+    del mdl
+    torch.cuda.empty_cache()
+
+    if not args.no_fp64:
+        md = tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al, precision=tem.TEM_FP64)
+        f64_factor, _ = timed(torch, lambda: md.factor(m0))
+        f64_fwd, _ = timed(torch, lambda: md.forward())
+        vv = torch.randn(info["n_param"], dtype=torch.float64, device="cuda")
+        ww = torch.randn(*md.shape, dtype=torch.float64, device="cuda")
+        f64_pair, _ = timed(torch, lambda: (md.jvp(vv), md.jtvp(ww)))
+        out["fp64"] = {"factor_s": round(f64_factor / 1e3, 2), "forward_s": round(f64_fwd / 1e3, 3),
+                       "pair_s": round(f64_pair / 1e3, 3), "pairs_per_s": round(1e3 / f64_pair, 4),
+                       "gn_iteration_s": round((f64_factor + f64_fwd + N_LSQR_GN * f64_pair) / 1e3, 1),
+                       "note": "one factor, one forward, one J.v + J^T.w pair timed with CUDA events"}
+        md.close()
+        del md
+        torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(steps=1, n=args.n)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(steps=1, warmup=0, n=46):
+    """The oracle as it stands, on this host, on a bounded sample: one (or
+    `steps`) J.v + J^T.w pair of the 20^3 box (8 poles x 4 loops) after its
+    factorisation, scaled to the 46^3 workload by factor entries x right-hand
+    sides x poles (from the library's symbolic analysis of both meshes)."""
+    import numpy as np
+    from oracle.tem import Oracle
+    from paper_2605_19951_gb300 import inputs, tem
+
+    s2 = inputs.make_config(2)
+    xi2, al2 = inputs.load_rational(s2.m, s2.times)
+    o = Oracle(s2.xyz, s2.tets, s2.sigma, s2.is_param, s2.loops, s2.rx, xi2, al2)
+    o.set_model(s2.log_sigma())
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(s2.n_param)
+    w = rng.standard_normal(o.forward_shape)
+    for _ in range(warmup):
+        o.jvp(v)
+        o.jtvp(w)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.jvp(v)
+        o.jtvp(w)
+    t_pair = (time.perf_counter() - t0) / steps
+    s4 = inputs.make_config(CONFIG, n=n)
+    units = {}
+    for key, s in (("c2", s2), ("c4", s4)):
+        ctx = tem.tem_create(tem.TEM_FP64)
+        try:
+            tem.tem_mesh(ctx, s.xyz, s.tets, s.sigma, s.is_param)
+            units[key] = tem.tem_info(ctx)["nnz_l"] * s.m * len(s.loops)
+        finally:
+            tem.tem_destroy(ctx)
+    scale = units["c4"] / units["c2"]
+    return {"value": round(1.0 / (t_pair * scale), 6), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle pair(s) of the 20^3 box ({t_pair:.2f} s each, one thread), "
+                      f"scaled by factor entries x RHS x poles ({scale:.0f}x) to the {n}^3 workload",
+            "pair_s_sample": round(t_pair, 3), "scale": round(scale, 1)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch  # noqa: F401  (the library context for the symbolic sizes needs the GPU)
+    t0 = time.perf_counter()
+    cb = cpu_baseline(steps=args.steps, warmup=args.warmup, n=args.n)
+    per_pair_s = 1.0 / cb["value"]
+    out = {"metric": METRIC, "value": cb["value"], "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(per_pair_s * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{s.n}^3 Kuhn box, {N} DoF, 10 pole pairs, 32 loops, 128 rx, 40 times",
+                      "sample": cb["sample"]},
+           "impl": "reference", "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": round(time.perf_counter() - t0, 1)}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

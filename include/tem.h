@@ -76,6 +76,8 @@ typedef struct tem_stats {
   int32_t refine_steps;  /* refinement corrections per solve (FP32 mode) */
   int32_t last_pivot_front; /* front of the last pivot failure, -1 if none */
   double min_pivot_abs;  /* smallest |d_kk| seen in the last factorisation */
+  int64_t nnz_l11;       /* factor entries in the pivot blocks (sum k(k+1)/2) */
+  int64_t n_solve_launch;/* kernel launches of one solve (forward + backward sweep) */
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or
@@ -174,6 +176,9 @@ int tem_set_profiling(tem_ctx *ctx, int kernel_class);
 /* Accumulated device time (ms) and launch count of the timed class since the
  * last tem_set_profiling. */
 int tem_kernel_time(tem_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* Kernel launches issued by the library since it was loaded (all contexts). */
+int64_t tem_launch_count(void);
 
 /* Sizes and counters. */
 int tem_info(tem_ctx *ctx, tem_stats *out);

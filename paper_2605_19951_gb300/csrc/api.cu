@@ -15,8 +15,13 @@
 
 using namespace tem;
 
+#include <atomic>
+
 namespace tem {
 thread_local Profiler *g_prof = nullptr;
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(); }
 
 void Profiler::begin(int c, cudaStream_t s) {
   if (!on || c != cls) return;
@@ -660,6 +665,10 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   double mp;
   memcpy(&mp, &c->status_h.min_pivot_bits, sizeof(double));
   o->min_pivot_abs = mp;
+  o->nnz_l11 = c->sym.nnz_l11;
+  int64_t nl = 0;
+  for (const LevelDev &lv : c->levels) nl += 2 * (int64_t)lv.steps.size() + (lv.nf > 0 ? 1 : 0);
+  o->n_solve_launch = nl;
   return TEM_OK;
 }
 
@@ -703,6 +712,8 @@ int tem_set_profiling(tem_ctx *c, int kernel_class) {
   c->prof.used = 0;
   return TEM_OK;
 }
+
+int64_t tem_launch_count(void) { return launch_total(); }
 
 int tem_kernel_time(tem_ctx *c, double *total_ms, int64_t *launches) {
   if (!c || !total_ms || !launches) return TEM_ERR_ARG;

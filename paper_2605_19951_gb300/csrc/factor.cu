@@ -311,12 +311,15 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
 // launch wrappers
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s) {
-  if (P > 0) k_sigma<<<div_up(P, 256), 256, 0, s>>>(logs, ptet, P, sigma);
+  if (P == 0) return;
+  tem::count_launch();
+  k_sigma<<<div_up(P, 256), 256, 0, s>>>(logs, ptet, P, sigma);
 }
 
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
                   const double *me1, int64_t nnz, double *mval, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>(div_up(nnz, 256), 152 * 16);
+  tem::count_launch();
   k_mvals<<<blocks, 256, 0, s>>>(mc_ptr, mc_idx, sigma, me1, nnz, mval);
 }
 
@@ -324,6 +327,7 @@ void launch_mvals_floor(const int64_t *mc_ptr, const uint32_t *mc_idx, const dou
                         const double *tetfloor, const double *me1, const double2 *xi, double tau, int m,
                         int64_t nnz, double *mval, cudaStream_t s) {
   dim3 g((unsigned)std::min<int64_t>(div_up(nnz, 256), 1024), m);
+  tem::count_launch();
   k_mvals_floor<<<g, 256, 0, s>>>(mc_ptr, mc_idx, sigma, tetfloor, me1, xi, tau, nnz, mval);
 }
 
@@ -336,12 +340,14 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
       cudaMemsetAsync(L + p * lstride + lv.lbeg, 0, (lv.lend - lv.lbeg) * sizeof(cx<R>), s);
   if (lv.nf > 0) {
     dim3 g(64, lv.nf, m);
+    tem::count_launch();
     k_zero_u<R><<<g, 256, 0, s>>>(U, ustride, F, lv.fronts);
   }
   // 2. original entries of A_i
   const int64_t cnt = lv.oend - lv.obeg;
   if (cnt > 0) {
     dim3 g((unsigned)std::min<int64_t>(div_up(cnt, 256), 4096), m);
+    tem::count_launch();
     k_assemble_orig<R><<<g, 256, 0, s>>>(L, lstride, kval, mval, mstride, orig_nz + lv.obeg,
                                          orig_dst + lv.obeg, cnt, xi);
   }
@@ -352,6 +358,7 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
     if (nt <= 0) continue;
     dim3 g((unsigned)nt, m);
     if (g_prof) g_prof->begin(KC_EXTEND_ADD, s);
+    tem::count_launch();
     k_extend_add<R><<<g, 128, 0, s>>>(L, lstride, U, ustride, F, rel, ea_child + lv.ea_beg[sl],
                                        ea_col + lv.ea_beg[sl]);
     if (g_prof) g_prof->end(KC_EXTEND_ADD, s);
@@ -361,10 +368,12 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
     const StepDims &sd = lv.steps[step];
     dim3 gp(sd.panel_tiles, sd.nfronts, m);
     if (g_prof) g_prof->begin(KC_PANEL, s);
+    tem::count_launch();
     k_panel<R, kNB, kPanelRT><<<gp, kPanelRT, 0, s>>>(L, lstride, F, lv.fronts, step, dscr, status);
     if (g_prof) g_prof->end(KC_PANEL, s);
     dim3 gu(sd.update_tiles, sd.nfronts, m);
     if (g_prof) g_prof->begin(KC_UPDATE, s);
+    tem::count_launch();
     k_update<R, kNB, UpdateTile<R>::TM><<<gu, 256, 0, s>>>(L, lstride, U, ustride, F, lv.fronts, step,
                                                             dscr);
     if (g_prof) g_prof->end(KC_UPDATE, s);

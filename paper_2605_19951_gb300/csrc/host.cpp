@@ -431,6 +431,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
   s.rows.clear();
   s.flops = 0;
   s.nnz_l = 0;
+  s.nnz_l11 = 0;
   s.max_front = 0;
   int64_t lofs = 0;
   int32_t H = 0;
@@ -451,6 +452,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
     s.max_front = std::max(s.max_front, F.n);
     const int64_t b = F.n - F.k;
     s.nnz_l += int64_t(F.k) * (F.k + 1) / 2 + int64_t(F.k) * b;
+    s.nnz_l11 += int64_t(F.k) * (F.k + 1) / 2;
     for (int64_t j = 0; j < F.k; j++) {
       double t = double(F.n - j - 1);
       s.flops += t + t * (t + 1) / 2;

@@ -161,4 +161,8 @@ struct Profiler {
 };
 extern thread_local Profiler *g_prof;   // set by the API layer around a call
 
+// Kernel launches issued by this library (all threads), for reporting.
+int64_t launch_total();
+void count_launch();
+
 }  // namespace tem

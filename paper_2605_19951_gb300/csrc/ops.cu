@@ -52,8 +52,10 @@ void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax
   dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
   if (scale) {
     cudaMemsetAsync(colmax, 0, sizeof(double) * m * nrhs, s);
+    tem::count_launch();
     k_colmax<<<g, 256, 0, s>>>(b, bstride, colmax, N, nrhs);
   }
+  tem::count_launch();
   k_rhs_to_work<R><<<g, 256, 0, s>>>(b, bstride, Y, scale ? colmax : nullptr, N, nrhs);
 }
 
@@ -81,6 +83,7 @@ template <typename R>
 void launch_accumulate(const cx<R> *X, const double *colmax, c128 *x, int m, int64_t N, int nrhs,
                        bool add, cudaStream_t s) {
   dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
+  tem::count_launch();
   k_accumulate<R><<<g, 256, 0, s>>>(X, colmax, x, N, nrhs, add ? 1 : 0);
 }
 
@@ -113,6 +116,7 @@ void launch_residual(const int64_t *rp, const int32_t *ci, const double *kv, con
                      const double2 *xi, const c128 *b, int64_t bstride, const c128 *x, c128 *r,
                      int m, int64_t N, int nrhs, cudaStream_t s) {
   dim3 g(div_up(N, 8), m);
+  tem::count_launch();
   k_residual<<<g, 256, 0, s>>>(rp, ci, kv, mv, xi, b, bstride, x, r, N, nrhs);
 }
 
@@ -123,6 +127,7 @@ __global__ void k_real_to_c128(const double *__restrict__ f, c128 *__restrict__ 
 }
 
 void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s) {
+  tem::count_launch();
   k_real_to_c128<<<(unsigned)std::min<int64_t>(div_up(count, 256), 4096), 256, 0, s>>>(f, b, count);
 }
 
@@ -163,6 +168,7 @@ void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_va
                     const double2 *alpha, const c128 *y, double *d, int m, int64_t N, int nrhs,
                     int n_rx, int K, cudaStream_t s) {
   const int64_t cnt = int64_t(n_rx) * nrhs;
+  tem::count_launch();
   k_residue<<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, n_rx, K);
 }
 
@@ -198,6 +204,7 @@ void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *q
   const int64_t cnt = int64_t(n_qdof) * nrhs;
   if (cnt == 0) return;
   dim3 g(div_up(cnt, 128), m);
+  tem::count_launch();
   k_qt_rhs<<<g, 128, 0, s>>>(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, N, nrhs, n_rx, K);
 }
 
@@ -249,6 +256,7 @@ void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_
                      const double *me1, const double2 *xi, const c128 *g, c128 *h, int m, int64_t N,
                      int nrhs, cudaStream_t s) {
   dim3 gr(div_up(N, 8), m);
+  tem::count_launch();
   k_dm_apply<<<gr, 256, 0, s>>>(inc_ptr, inc_tet, inc_loc, tdof, pidx, v, sigma, me1, xi, g, h, N, nrhs);
 }
 
@@ -296,6 +304,7 @@ void launch_bilinear(const int32_t *ptet, int64_t P, const int32_t *tdof, const 
                      const double *me1, const double2 *xi, const c128 *g, const c128 *z, double *grad,
                      int m, int64_t N, int nrhs, cudaStream_t s) {
   if (P == 0) return;
+  tem::count_launch();
   k_bilinear<<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
 }
 
@@ -313,6 +322,7 @@ __global__ void k_csr_mv(const int64_t *__restrict__ rp, const int32_t *__restri
 void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,
                    int64_t rows, double alpha, double beta, cudaStream_t s) {
   if (rows == 0) return;
+  tem::count_launch();
   k_csr_mv<<<(unsigned)std::min<int64_t>(div_up(rows, 256), 4096), 256, 0, s>>>(rp, ci, val, x, y, rows,
                                                                                 alpha, beta);
 }
@@ -337,6 +347,7 @@ __global__ void k_sumsq(const double *__restrict__ x, int64_t n, double *out) {
 
 void launch_sumsq(const double *x, int64_t n, double *out, cudaStream_t s) {
   if (n == 0) return;
+  tem::count_launch();
   k_sumsq<<<(unsigned)std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(x, n, out);
 }
 
@@ -410,10 +421,12 @@ __global__ void k_lsqr_scalars(LsqrScalars *sc, int which) {
 void launch_lsqr_kernel(int op, LsqrScalars *sc, double *a, const double *b, const double *c,
                         const double *wd, int64_t n, cudaStream_t s) {
   if (n == 0) return;
+  tem::count_launch();
   k_lsqr<<<(unsigned)std::min<int64_t>(div_up(n, 256), 2048), 256, 0, s>>>(op, sc, a, b, c, wd, n);
 }
 
 void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s) {
+  tem::count_launch();
   k_lsqr_scalars<<<1, 32, 0, s>>>(sc, which);
 }
 

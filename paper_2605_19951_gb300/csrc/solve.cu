@@ -193,6 +193,7 @@ void SolvePlan<R>::forward_level(const LevelDev &lv, cudaStream_t s) {
     const StepDims &sd = lv.steps[step];
     dim3 g(sd.fwd_tiles, sd.nfronts, m * nchunk);
     if (g_prof) g_prof->begin(KC_FWD, s);
+    tem::count_launch();
     k_fwd_step<R, kNB, SolveTile<R>::RT><<<g, 256, 0, s>>>(L, lstride, F, lv.fronts, rows, step, Y, X,
                                                             vstride, nrhs, nchunk);
     if (g_prof) g_prof->end(KC_FWD, s);
@@ -205,12 +206,14 @@ void SolvePlan<R>::backward_level(const LevelDev &lv, cudaStream_t s) {
   if (lv.nf == 0) return;
   dim3 gu(lv.bwd_upd_tiles, lv.nf, m * nchunk);
   if (g_prof) g_prof->begin(KC_BWD_UPD, s);
+  tem::count_launch();
   k_bwd_upd<R><<<gu, 256, 0, s>>>(L, lstride, F, lv.fronts, rows, Y, X, vstride, nrhs, nchunk);
   if (g_prof) g_prof->end(KC_BWD_UPD, s);
   for (int step = (int)lv.steps.size() - 1; step >= 0; step--) {
     const StepDims &sd = lv.steps[step];
     dim3 g(sd.bwd_tiles, sd.nfronts, m * nchunk);
     if (g_prof) g_prof->begin(KC_BWD, s);
+    tem::count_launch();
     k_bwd_step<R, kNB, SolveTile<R>::CT><<<g, 256, 0, s>>>(L, lstride, F, lv.fronts, step, Y, X, vstride, nrhs,
                                                   nchunk);
     if (g_prof) g_prof->end(KC_BWD, s);

@@ -85,6 +85,7 @@ struct Symbolic {
   int64_t utotal = 0;                   // update arena elements per pole
   double flops = 0;                     // complex MACs per pole
   int64_t nnz_l = 0;                    // meaningful factor entries per pole
+  int64_t nnz_l11 = 0;                  // of which in the pivot blocks
   int32_t max_front = 0;
 };
 

@@ -185,8 +185,10 @@ def _seeded_block(rng, n, n_air, di, dj, dk):
     return i0, j0, k0
 
 
-def make_config(idx, m=None):
-    """Configurations C1..C4 (idx 1..4) of the synthetic workloads."""
+def make_config(idx, m=None, n=None):
+    """Configurations C1..C4 (idx 1..4) of the synthetic workloads.  For idx 4
+    a smaller n keeps its structure (32 loops, 128 receivers, 10 poles) on a
+    smaller box, for profiling captures."""
     rng = np.random.default_rng(19951 + idx)
     if idx == 1:
         n, h = 8, 50.0
@@ -195,7 +197,8 @@ def make_config(idx, m=None):
     elif idx == 3:
         n, h = 40, 12.5
     elif idx == 4:
-        n, h = 46, 100.0 / 9.0
+        n = 46 if n is None else int(n)
+        h = (100.0 / 9.0) * 46.0 / n
     else:
         raise ValueError(idx)
     n_air = (3 * n) // 8
@@ -242,13 +245,18 @@ def make_config(idx, m=None):
             blocks.append((i0, j0, k0, 6, 6, 4, val))
         sig = _block_sigma(n, n_air, sig, blocks)
         loops = []
-        for jy in range(4):
-            for ix in range(8):
-                loops.append(square_loop(n, n_air, 3 + 4 * ix, 7 + 8 * jy, 9))
+        side = max(2, (9 * n) // 46)
+        xs_ = np.linspace(3, n - 3 - side, 8).round().astype(int)
+        ys_ = np.linspace(3, n - 3 - side, 4).round().astype(int)
+        for jy in ys_:
+            for ix in xs_:
+                loops.append(square_loop(n, n_air, int(ix), int(jy), side))
         ks = n - n_air
-        rx = np.array([[xyz[vertex_id(n, 8 + 2 * a, 9 + 4 * b, ks), 0],
-                        xyz[vertex_id(n, 8 + 2 * a, 9 + 4 * b, ks), 1], 0.0]
-                       for b in range(8) for a in range(16)])
+        ia = np.linspace(3, n - 3, 16).round().astype(int)
+        jb = np.linspace(4, n - 4, 8).round().astype(int)
+        rx = np.array([[xyz[vertex_id(n, int(a), int(b), ks), 0],
+                        xyz[vertex_id(n, int(a), int(b), ks), 1], 0.0]
+                       for b in jb for a in ia])
         K, mm = 40, 10
     start = np.full(tets.shape[0], SIGMA_AIR)
     start[earth] = 0.01

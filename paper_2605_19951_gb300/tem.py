@@ -40,6 +40,7 @@ SIGNATURES = {
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D]),
     "tem_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "tem_launch_count": (_I64, []),
     "tem_info": (ctypes.c_int, [_P, _P]),
     "tem_export_pattern": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P, _P, _P, _P]),
     "tem_export_dofs": (ctypes.c_int, [_P, _P]),
@@ -52,7 +53,7 @@ class TemStats(ctypes.Structure):
                 ("flops_factor", _D), ("max_front", _I64), ("bytes_device", _I64),
                 ("m", _I32), ("n_times", _I32), ("n_tx", _I32), ("n_rx", _I32),
                 ("precision", _I32), ("refine_steps", _I32), ("last_pivot_front", _I32),
-                ("min_pivot_abs", _D)]
+                ("min_pivot_abs", _D), ("nnz_l11", _I64), ("n_solve_launch", _I64)]
 
 
 class TemError(RuntimeError):
@@ -175,6 +176,10 @@ def tem_kernel_time(ctx):
     ms, n = _D(), _I64()
     _check(ctx, load().tem_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def tem_launch_count():
+    return int(load().tem_launch_count())
 
 
 def tem_info(ctx):
