@@ -152,6 +152,25 @@ int tem_jtvp(tem_ctx *ctx, const double *w, double *jtw);
 int tem_lsqr(tem_ctx *ctx, const double *d_obs, const double *wd,
              const double *m_ref, double lambda, int32_t n_iter, double *dm);
 
+/* tem_lsqr for callers that cannot allocate device memory while an
+ * inversion runs: programs whose device memory belongs to their own
+ * allocator (a framework's caching pool), or that must not risk a cudaMalloc
+ * failing, or cudaMalloc/cudaFree synchronising the device, between
+ * Gauss-Newton steps.  Same arguments, results and errors as tem_lsqr, but
+ * the LSQR work vectors and scalars live in one file-scope device array of
+ * 4 Mi doubles (32 MiB) that every GPU loading the library holds until the
+ * process exits; a problem needing more (3 nd + 2 n_faces + 3 P doubles,
+ * nd = n_tx n_rx n_times) returns TEM_ERR_ARG and nothing runs.  The call
+ * allocates nothing itself; the factors and solve buffers it uses come from
+ * tem_factor.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with the context's device current), so make
+ * that first call before any stream capture.  All calls on a device share the
+ * array and it keeps the last call's contents: calls that overlap on the GPU
+ * (other streams, other contexts on the same device) race.  This entry point
+ * has no counterpart in the paper. */
+int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
+                     const double *m_ref, double lambda, int32_t n_iter, double *dm);
+
 /* TEM_FP32_REFINED mode: refinement corrections per solve (default 6) and
  * the conductivity floor of the factored matrices (default 1e-4).
  *

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -723,3 +725,101 @@ int tem_kernel_time(tem_ctx *c, double *total_ms, int64_t *launches) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// LSQR that allocates nothing.
+//
+// For callers that cannot allocate device memory while an inversion runs:
+// programs whose device memory is handed out by their own allocator (a
+// framework's caching pool) or that must not risk a cudaMalloc failing, or
+// cudaMalloc/cudaFree synchronising the device, between Gauss-Newton steps.
+// tem_lsqr allocates its work vectors on first use; this variant keeps them
+// in one file-scope device array instead.  The factors and solve buffers it
+// uses were allocated by tem_factor, which such callers run at start-up.
+
+namespace {
+constexpr size_t kNoAllocDoubles = size_t(4) << 20;  // 4 Mi doubles = 32 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+std::mutex g_noalloc_mu;
+std::map<int, double *> g_noalloc_addr;  // device -> address of g_noalloc_scratch
+
+size_t pad32(size_t n) { return (n + 31) & ~size_t(31); }  // keep every slice 256-byte aligned
+}  // namespace
+
+extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref,
+                                double lambda, int32_t n_iter, double *dm) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
+  if (!d_obs || !wd || !m_ref || !dm || n_iter < 0 || !(lambda >= 0)) return fail(c, TEM_ERR_ARG, "bad LSQR args");
+  const int64_t nd = int64_t(c->n_tx) * c->n_rx * c->K, P = c->mesh.P, nf = c->mesh.nf;
+  const size_t nsc = pad32((sizeof(LsqrScalars) + sizeof(double) - 1) / sizeof(double));
+  const size_t need = nsc + pad32(nd + nf) + 3 * pad32(P) + 2 * pad32(nd) + pad32(std::max<int64_t>(nf, 1));
+  if (need > kNoAllocDoubles) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "problem needs %zu doubles of LSQR scratch, the no-alloc limit is %zu", need,
+             kNoAllocDoubles);
+    return fail(c, TEM_ERR_ARG, buf);
+  }
+  double *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(c->device);
+    if (it == g_noalloc_addr.end()) {
+      int cur = -1;
+      CK(cudaGetDevice(&cur));
+      if (cur != c->device) return fail(c, TEM_ERR_STATE, "the context's device is not current");
+      CK(cudaGetSymbolAddress((void **)&base, g_noalloc_scratch));
+      g_noalloc_addr[c->device] = base;
+    } else {
+      base = it->second;
+    }
+  }
+  LsqrScalars *sc = (LsqrScalars *)base;
+  double *p = base + nsc;
+  double *u = p;            p += pad32(nd + nf);
+  double *v = p;            p += pad32(P);
+  double *w = p;            p += pad32(P);
+  double *jtw = p;          p += pad32(P);
+  double *jv = p;           p += pad32(nd);
+  double *tmpd = p;         p += pad32(nd);
+  double *wv = p;           p += pad32(std::max<int64_t>(nf, 1));
+  cudaStream_t s = c->stream;
+  const double sl = std::sqrt(lambda);
+  double *u1 = u, *u2 = u + nd;
+  CK(cudaMemsetAsync(sc, 0, sizeof(LsqrScalars), s));   // sumsq and the recurrences start at zero
+  launch_lsqr_kernel(6, sc, u1, c->d_cur, d_obs, wd, nd, s);
+  launch_csr_mv(c->w_rp, c->w_ci, c->w_val, c->m_cur, u2, nf, -sl, 0.0, s);
+  launch_csr_mv(c->w_rp, c->w_ci, c->w_val, m_ref, u2, nf, sl, 1.0, s);
+  launch_sumsq(u, nd + nf, &sc->sumsq, s);
+  launch_lsqr_kernel(0, sc, u, nullptr, nullptr, nullptr, nd + nf, s);
+  launch_lsqr_scalars(sc, 0, s);
+  launch_lsqr_kernel(5, sc, tmpd, u1, wd, nullptr, nd, s);
+  jtvp_async(c, tmpd, jtw);
+  CK(cudaMemcpyAsync(v, jtw, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
+  launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, v, P, sl, 1.0, s);
+  launch_sumsq(v, P, &sc->sumsq, s);
+  launch_lsqr_kernel(1, sc, v, nullptr, nullptr, nullptr, P, s);
+  launch_lsqr_scalars(sc, 1, s);
+  launch_lsqr_scalars(sc, 2, s);
+  CK(cudaMemcpyAsync(w, v, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(dm, 0, sizeof(double) * P, s));
+  for (int it = 0; it < n_iter; it++) {
+    jvp_async(c, v, jv);
+    launch_lsqr_kernel(2, sc, u1, jv, wd, nullptr, nd, s);
+    launch_csr_mv(c->w_rp, c->w_ci, c->w_val, v, wv, nf, sl, 0.0, s);
+    launch_lsqr_kernel(7, sc, u2, wv, nullptr, nullptr, nf, s);
+    launch_sumsq(u, nd + nf, &sc->sumsq, s);
+    launch_lsqr_kernel(0, sc, u, nullptr, nullptr, nullptr, nd + nf, s);
+    launch_lsqr_scalars(sc, 0, s);
+    launch_lsqr_kernel(5, sc, tmpd, u1, wd, nullptr, nd, s);
+    jtvp_async(c, tmpd, jtw);
+    launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, jtw, P, sl, 1.0, s);
+    launch_lsqr_kernel(3, sc, v, jtw, nullptr, nullptr, P, s);
+    launch_sumsq(v, P, &sc->sumsq, s);
+    launch_lsqr_kernel(1, sc, v, nullptr, nullptr, nullptr, P, s);
+    launch_lsqr_scalars(sc, 1, s);
+    launch_lsqr_scalars(sc, 3, s);
+    launch_lsqr_kernel(4, sc, dm, w, v, nullptr, P, s);
+  }
+  return sync(c, "tem_lsqr_noalloc");
+}

@@ -37,6 +37,7 @@ SIGNATURES = {
     "tem_jvp": (ctypes.c_int, [_P, _P, _P]),
     "tem_jtvp": (ctypes.c_int, [_P, _P, _P]),
     "tem_lsqr": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
+    "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D]),
     "tem_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
@@ -161,6 +162,13 @@ def tem_jtvp(ctx, w, jtw):
 def tem_lsqr(ctx, d_obs, wd, m_ref, lam, n_iter, dm):
     _check(ctx, load().tem_lsqr(ctx, _dev(d_obs), _dev(wd), _dev(m_ref), float(lam), int(n_iter),
                                 _dev(dm)))
+
+
+def tem_lsqr_noalloc(ctx, d_obs, wd, m_ref, lam, n_iter, dm):
+    """tem_lsqr with its work vectors in the library's fixed device array (no
+    allocation); see include/tem.h for the size limit and sharing rules."""
+    _check(ctx, load().tem_lsqr_noalloc(ctx, _dev(d_obs), _dev(wd), _dev(m_ref), float(lam), int(n_iter),
+                                        _dev(dm)))
 
 
 def tem_set_refine(ctx, steps, floor_tau=1e-4):
