@@ -187,9 +187,10 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
 int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau);
 
 /* Time one class of kernels with CUDA events on the context's stream:
- * 0 trailing update, 1 panel, 2 forward-solve step, 3 backward-solve step,
- * 4 backward update-row product, 5 extend-add; -1 switches timing off (the
- * default).  Timing adds an event pair around each launch of that class. */
+ * 0 trailing update, 1 panel, 2 forward pivot-block step, 3 backward
+ * pivot-block step, 4 backward update-row product (L21^T), 5 extend-add,
+ * 6 forward update-row product (L21); -1 switches timing off (the default).
+ * Timing adds an event pair around each launch of that class. */
 int tem_set_profiling(tem_ctx *ctx, int kernel_class);
 
 /* Accumulated device time (ms) and launch count of the timed class since the

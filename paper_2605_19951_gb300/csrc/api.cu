@@ -83,6 +83,9 @@ struct tem_ctx {
   Symbolic sym;
   std::vector<LevelDev> levels;
   int max_level_fronts = 0;
+  int64_t inv_blocks = 0;                 // diagonal-block inverses per pole
+  std::vector<int2> f21_h, b21_h;         // task lists of the L21 products (all levels)
+  int2 *f21 = nullptr, *b21 = nullptr;
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -110,7 +113,7 @@ struct tem_ctx {
   double *q_val = nullptr, *qt_val = nullptr;
 
   // numeric
-  void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr;
+  void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr, *linv = nullptr;
   DevStatus *status = nullptr;
   c128 *g = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *fb = nullptr;
   double *colmax = nullptr;
@@ -194,6 +197,8 @@ template <typename R>
 void build_steps(tem_ctx *c) {
   const auto &S = c->sym;
   c->levels.clear();
+  c->f21_h.clear();
+  c->b21_h.clear();
   c->max_level_fronts = 0;
   int64_t off = 0;
   for (const Level &L : S.levels) {
@@ -210,6 +215,23 @@ void build_steps(tem_ctx *c) {
       lv.ea_end[s] = L.ea_end[s];
     }
     lv.bwd_upd_tiles = std::max(1, div_up(L.max_k, 8));
+    lv.n_f21 = 0;
+    lv.n_b21 = 0;
+    const size_t f21_beg = c->f21_h.size(), b21_beg = c->b21_h.size();
+    for (int32_t fi : L.fronts) {
+      const Front &F = S.fronts[fi];
+      const int b = F.n - F.k;
+      if (F.k <= 0) continue;
+      // the forward product only where there are update rows; the backward
+      // one for every front (it also forms w = D^-1 y of the pivots)
+      if (b > 0)
+        for (int t = 0; t < div_up(b, SolveTile<R>::BM); t++) c->f21_h.push_back(make_int2(fi, t));
+      for (int t = 0; t < div_up(F.k, SolveTile<R>::BN); t++) c->b21_h.push_back(make_int2(fi, t));
+    }
+    lv.n_f21 = int(c->f21_h.size() - f21_beg);
+    lv.n_b21 = int(c->b21_h.size() - b21_beg);
+    lv.f21_tasks = (const int2 *)(uintptr_t)f21_beg;   // offsets until the lists are on the device
+    lv.b21_tasks = (const int2 *)(uintptr_t)b21_beg;
     const int nsteps = div_up(L.max_k, kNB);
     for (int s = 0; s < nsteps; s++) {
       StepDims d{};
@@ -223,7 +245,7 @@ void build_steps(tem_ctx *c) {
         d.panel_tiles = std::max(d.panel_tiles, std::max(1, div_up(below, kPanelRT)));
         const int64_t T = div_up(below, UpdateTile<R>::TM);
         d.update_tiles = (int)std::max<int64_t>(d.update_tiles, std::max<int64_t>(1, T * (T + 1) / 2));
-        d.fwd_tiles = std::max(d.fwd_tiles, std::max(1, div_up(below, SolveTile<R>::RT)));
+        d.fwd_tiles = std::max(d.fwd_tiles, std::max(1, div_up(F.k - j0 - nb, SolveTile<R>::RT)));
         d.bwd_tiles = std::max(d.bwd_tiles, std::max(1, div_up(j0, SolveTile<R>::CT)));
       }
       lv.steps.push_back(d);
@@ -252,6 +274,8 @@ FactorPlan<R> factor_plan(tem_ctx *c) {
   P.mstride = c->mval_fact ? (int64_t)c->mesh.kval.size() : 0;
   P.xi = c->xi;
   P.dscr = (cx<R> *)c->dscr;
+  P.linv = (cx<R> *)c->linv;
+  P.istride = c->inv_blocks * kNB * kNB;
   P.status = c->status;
   return P;
 }
@@ -263,6 +287,8 @@ SolvePlan<R> solve_plan(tem_ctx *c) {
   P.nrhs = c->n_tx;
   P.L = (const cx<R> *)c->L;
   P.lstride = c->sym.ltotal;
+  P.Linv = (const cx<R> *)c->linv;
+  P.istride = c->inv_blocks * kNB * kNB;
   P.F = c->fronts;
   P.rows = c->rows;
   P.Y = (cx<R> *)c->Y;
@@ -313,6 +339,8 @@ int ensure_numeric(tem_ctx *c) {
   c->U = p;
   TRY(dalloc(c, (char **)&p, size_t(std::max(1, c->max_level_fronts)) * m * kNB * kNB * es));
   c->dscr = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * std::max<int64_t>(1, c->inv_blocks) * kNB * kNB * es));
+  c->linv = p;
   TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
   c->Y = p;
   TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
@@ -396,10 +424,13 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->pidx, M.pidx));
   TRY(upload(c, &c->ptet, M.ptet));
   std::vector<FrontDev> fd(S.fronts.size());
+  int64_t inv = 0;
   for (size_t i = 0; i < S.fronts.size(); i++) {
     const Front &F = S.fronts[i];
-    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, F.n, F.k, F.c0, F.parent};
+    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, inv, F.n, F.k, F.c0, F.parent};
+    inv += div_up(F.k, kNB);
   }
+  c->inv_blocks = inv;
   TRY(upload(c, &c->fronts, fd));
   TRY(upload(c, &c->rows, S.rows));
   TRY(upload(c, &c->rel, S.rel));
@@ -418,6 +449,12 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->wt_val, M.wt_val));
   if (c->precision == TEM_FP64) build_steps<double>(c);
   else build_steps<float>(c);
+  TRY(upload(c, &c->f21, c->f21_h));
+  TRY(upload(c, &c->b21, c->b21_h));
+  for (LevelDev &lv : c->levels) {
+    lv.f21_tasks = c->f21 + (uintptr_t)lv.f21_tasks;
+    lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
+  }
   for (const LevelDev &lv : c->levels)
     if (lv.nf > 65535) return fail(c, TEM_ERR_MESH, "more than 65535 fronts in one tree level");
   TRY(sync(c, "tem_mesh"));
@@ -669,7 +706,8 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   o->min_pivot_abs = mp;
   o->nnz_l11 = c->sym.nnz_l11;
   int64_t nl = 0;
-  for (const LevelDev &lv : c->levels) nl += 2 * (int64_t)lv.steps.size() + (lv.nf > 0 ? 1 : 0);
+  for (const LevelDev &lv : c->levels)
+    nl += 2 * (int64_t)lv.steps.size() + (lv.n_f21 > 0 ? 1 : 0) + (lv.n_b21 > 0 ? 1 : 0);
   o->n_solve_launch = nl;
   return TEM_OK;
 }

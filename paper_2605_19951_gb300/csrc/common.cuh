@@ -75,6 +75,7 @@ struct FrontDev {
   int64_t uofs;    // update block offset in the arena (b x b, ld b), -1 if b == 0
   int64_t rows_off;
   int64_t rel_off;
+  int64_t inv_off;  // first NB x NB diagonal-block inverse of this front (in blocks)
   int32_t n, k, c0, parent;
 };
 

@@ -139,7 +139,8 @@ template <typename R, int NB, int RT>
 __global__ void __launch_bounds__(RT) k_panel(cx<R> *__restrict__ L, int64_t lstride,
                                               const FrontDev *__restrict__ F,
                                               const int32_t *__restrict__ lev, int step,
-                                              cx<R> *__restrict__ dscr, DevStatus *st) {
+                                              cx<R> *__restrict__ dscr, cx<R> *__restrict__ linv,
+                                              int64_t istride, DevStatus *st) {
   const int fi = blockIdx.y;
   const FrontDev f = F[lev[fi]];
   const int p = blockIdx.z;
@@ -195,6 +196,24 @@ __global__ void __launch_bounds__(RT) k_panel(cx<R> *__restrict__ L, int64_t lst
       int r = idx % NB, c = idx / NB;
       if (r < nb && c < nb && r >= c) ds[c * NB + r] = Dg[r][c];
     }
+    // inverse of the unit lower block for the solves: column c by forward
+    // substitution (thread c), zero padded to NB x NB, stored column-major
+    __shared__ cx<R> Iv[NB][NB + 1];
+    if (tid < NB) {
+      const int c = tid;
+      for (int r = 0; r < NB; r++) Iv[c][r] = mk<R>(R(0), R(0));
+      if (c < nb) {
+        Iv[c][c] = mk<R>(R(1), R(0));
+        for (int r = c + 1; r < nb; r++) {
+          cx<R> acc = mk<R>(R(0), R(0));
+          for (int q = c; q < r; q++) cfma(acc, Dg[r][q], Iv[c][q]);
+          Iv[c][r] = mk<R>(-acc.x, -acc.y);
+        }
+      }
+    }
+    __syncthreads();
+    cx<R> *iv = linv + p * istride + (f.inv_off + step) * (NB * NB);
+    for (int idx = tid; idx < NB * NB; idx += RT) iv[idx] = Iv[idx / NB][idx % NB];
   }
   const int64_t r = rbeg + int64_t(tile) * RT + tid;
   if (r < n) {
@@ -369,7 +388,8 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
     dim3 gp(sd.panel_tiles, sd.nfronts, m);
     if (g_prof) g_prof->begin(KC_PANEL, s);
     tem::count_launch();
-    k_panel<R, kNB, kPanelRT><<<gp, kPanelRT, 0, s>>>(L, lstride, F, lv.fronts, step, dscr, status);
+    k_panel<R, kNB, kPanelRT><<<gp, kPanelRT, 0, s>>>(L, lstride, F, lv.fronts, step, dscr, linv, istride,
+                                                      status);
     if (g_prof) g_prof->end(KC_PANEL, s);
     dim3 gu(sd.update_tiles, sd.nfronts, m);
     if (g_prof) g_prof->begin(KC_UPDATE, s);

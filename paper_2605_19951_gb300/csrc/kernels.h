@@ -26,13 +26,19 @@ template <typename R>
 struct SolveTile;
 template <>
 struct SolveTile<float> {
-  static constexpr int RT = 64;  // rows per CTA in the forward sweep
-  static constexpr int CT = 32;  // columns per CTA in the backward sweep
+  static constexpr int RT = 64;   // pivot rows per CTA in a forward step
+  static constexpr int CT = 32;   // pivot columns per CTA in a backward step
+  static constexpr int BM = 128;  // update rows per CTA of the forward L21 product
+  static constexpr int BN = 64;   // pivot columns per CTA of the backward L21 product
+  static constexpr int KC = 32;   // inner chunk of both products
 };
 template <>
 struct SolveTile<double> {
   static constexpr int RT = 16;
   static constexpr int CT = 16;
+  static constexpr int BM = 64;
+  static constexpr int BN = 64;
+  static constexpr int KC = 16;
 };
 
 // Grid sizes of one pivot step of one level (host-computed).
@@ -47,6 +53,10 @@ struct StepDims {
 struct LevelDev {
   const int32_t *fronts = nullptr;  // device list, sorted by k descending
   int nf = 0;
+  const int2 *f21_tasks = nullptr;  // (front, row tile) of the forward L21 product
+  int n_f21 = 0;
+  const int2 *b21_tasks = nullptr;  // (front, column tile) of the backward L21 product
+  int n_b21 = 0;
   int bwd_upd_tiles = 0;            // ceil(max k / 8)
   int64_t lbeg = 0, lend = 0, obeg = 0, oend = 0;
   int64_t ea_beg[2] = {0, 0}, ea_end[2] = {0, 0};
@@ -71,6 +81,8 @@ struct FactorPlan {
   int64_t mstride = 0;              // pole stride of mval (0: one M for all poles)
   const double2 *xi = nullptr;
   cx<R> *dscr = nullptr;            // [max fronts per level][m][NB*NB]
+  cx<R> *linv = nullptr;            // [m][inv blocks][NB*NB] diagonal-block inverses (output)
+  int64_t istride = 0;
   DevStatus *status = nullptr;
   void level(int h, const LevelDev &lv, cudaStream_t s);
 };
@@ -81,6 +93,8 @@ struct SolvePlan {
   int nrhs = 0;
   const cx<R> *L = nullptr;
   int64_t lstride = 0;
+  const cx<R> *Linv = nullptr;
+  int64_t istride = 0;
   const FrontDev *F = nullptr;
   const int32_t *rows = nullptr;
   cx<R> *Y = nullptr;   // [m][N][nrhs] right-hand sides in, work space
@@ -146,7 +160,7 @@ void launch_lsqr_kernel(int op, LsqrScalars *sc, double *a, const double *b, con
 void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 
 // Kernel classes that can be timed individually with CUDA events.
-enum KernelClass { KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_COUNT };
+enum KernelClass { KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_COUNT };
 struct Profiler {
   bool on = false;
   int cls = -1;                        // class being timed

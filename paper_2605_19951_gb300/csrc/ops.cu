@@ -12,18 +12,31 @@ namespace tem {
 
 // ---- right-hand sides and refinement ---------------------------------------
 
+// Column maxima of max(|re|, |im|) per (pole, rhs): 8 row groups x 32 RHS
+// lanes per block, shared-memory reduction over the groups, one atomic per
+// block and column.
 __global__ void k_colmax(const c128 *__restrict__ b, int64_t bstride, double *colmax, int64_t N,
                          int nrhs) {
   const int p = blockIdx.y;
   const c128 *bp = b + p * bstride;
-  const int64_t cnt = N * nrhs;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    c128 v = bp[e];
-    double a = fmax(fabs(v.x), fabs(v.y));
-    if (a > 0)
-      atomicMax((unsigned long long *)&colmax[p * nrhs + e % nrhs],
-                (unsigned long long)__double_as_longlong(a));
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  __shared__ double red[8][32];
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int rhs = c0 + lane;
+    double mx = 0.0;
+    if (rhs < nrhs)
+      for (int64_t r = blockIdx.x * int64_t(8) + grp; r < N; r += int64_t(gridDim.x) * 8) {
+        const c128 v = bp[r * nrhs + rhs];
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      }
+    red[grp][lane] = mx;
+    __syncthreads();
+    if (grp == 0 && rhs < nrhs) {
+      for (int g = 1; g < 8; g++) mx = fmax(mx, red[g][lane]);
+      if (mx > 0)
+        atomicMax((unsigned long long *)&colmax[p * nrhs + rhs], (unsigned long long)__double_as_longlong(mx));
+    }
+    __syncthreads();
   }
 }
 
@@ -52,8 +65,9 @@ void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax
   dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
   if (scale) {
     cudaMemsetAsync(colmax, 0, sizeof(double) * m * nrhs, s);
+    dim3 gc((unsigned)std::min<int64_t>(div_up(N, 8), 512), m);
     tem::count_launch();
-    k_colmax<<<g, 256, 0, s>>>(b, bstride, colmax, N, nrhs);
+    k_colmax<<<gc, 256, 0, s>>>(b, bstride, colmax, N, nrhs);
   }
   tem::count_launch();
   k_rhs_to_work<R><<<g, 256, 0, s>>>(b, bstride, Y, scale ? colmax : nullptr, N, nrhs);
