@@ -26,7 +26,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_total() { return g_launches.load(); }
 
 void Profiler::begin(int c, cudaStream_t s) {
-  if (!on || c != cls) return;
+  if (!on || c != cls || (level >= 0 && cur_level != level)) return;
   if (used + 2 > (int)pool.size()) {
     size_t old = pool.size();
     pool.resize(std::max<size_t>(64, 2 * old + 2));
@@ -35,7 +35,7 @@ void Profiler::begin(int c, cudaStream_t s) {
   cudaEventRecord(pool[used], s);
 }
 void Profiler::end(int c, cudaStream_t s) {
-  if (!on || c != cls) return;
+  if (!on || c != cls || (level >= 0 && cur_level != level)) return;
   cudaEventRecord(pool[used + 1], s);
   used += 2;
 }
@@ -86,6 +86,8 @@ struct tem_ctx {
   int64_t inv_blocks = 0;                 // diagonal-block inverses per pole
   std::vector<int2> f21_h, b21_h;         // task lists of the L21 products (all levels)
   int2 *f21 = nullptr, *b21 = nullptr;
+  std::vector<int4> sbf_h, sbb_h;         // task lists of the super-block products
+  int4 *sbf = nullptr, *sbb = nullptr;
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -199,10 +201,13 @@ void build_steps(tem_ctx *c) {
   c->levels.clear();
   c->f21_h.clear();
   c->b21_h.clear();
+  c->sbf_h.clear();
+  c->sbb_h.clear();
   c->max_level_fronts = 0;
   int64_t off = 0;
   for (const Level &L : S.levels) {
     LevelDev lv;
+    lv.h = (int)c->levels.size();
     lv.nf = (int)L.fronts.size();
     lv.fronts = c->levfronts + off;
     off += lv.nf;
@@ -232,6 +237,29 @@ void build_steps(tem_ctx *c) {
     lv.n_b21 = int(c->b21_h.size() - b21_beg);
     lv.f21_tasks = (const int2 *)(uintptr_t)f21_beg;   // offsets until the lists are on the device
     lv.b21_tasks = (const int2 *)(uintptr_t)b21_beg;
+    // super-block products: forward rows of block J against pivots [0, J0);
+    // backward columns of block J against pivot rows [J1, k)
+    const int nsb = div_up(L.max_k, kSB);
+    lv.sb.assign(nsb, LevelDev::SuperBlock());
+    for (int J = 0; J < nsb; J++) {
+      const size_t fb = c->sbf_h.size(), bb = c->sbb_h.size();
+      for (int32_t fi : L.fronts) {
+        const Front &F = S.fronts[fi];
+        const int J0 = J * kSB;
+        if (F.k <= J0) break;
+        const int J1 = std::min(F.k, J0 + kSB);
+        for (int kb = 0; kb < J0; kb += kSplitK)
+          for (int t = 0; t < div_up(J1 - J0, SolveTile<R>::BM); t++)
+            c->sbf_h.push_back(make_int4(fi, t, kb, std::min(J0, kb + kSplitK)));
+        for (int rb = J1; rb < F.k; rb += kSplitK)
+          for (int t = 0; t < div_up(J1 - J0, SolveTile<R>::BN); t++)
+            c->sbb_h.push_back(make_int4(fi, t, rb, std::min(F.k, rb + kSplitK)));
+      }
+      lv.sb[J].n_fwd = int(c->sbf_h.size() - fb);
+      lv.sb[J].n_bwd = int(c->sbb_h.size() - bb);
+      lv.sb[J].fwd = (const int4 *)(uintptr_t)fb;   // offsets until the lists are on the device
+      lv.sb[J].bwd = (const int4 *)(uintptr_t)bb;
+    }
     const int nsteps = div_up(L.max_k, kNB);
     for (int s = 0; s < nsteps; s++) {
       StepDims d{};
@@ -245,8 +273,9 @@ void build_steps(tem_ctx *c) {
         d.panel_tiles = std::max(d.panel_tiles, std::max(1, div_up(below, kPanelRT)));
         const int64_t T = div_up(below, UpdateTile<R>::TM);
         d.update_tiles = (int)std::max<int64_t>(d.update_tiles, std::max<int64_t>(1, T * (T + 1) / 2));
-        d.fwd_tiles = std::max(d.fwd_tiles, std::max(1, div_up(F.k - j0 - nb, SolveTile<R>::RT)));
-        d.bwd_tiles = std::max(d.bwd_tiles, std::max(1, div_up(j0, SolveTile<R>::CT)));
+        const int sb_end = std::min(F.k, (j0 / kSB + 1) * kSB), sb_beg = (j0 / kSB) * kSB;
+        d.fwd_tiles = std::max(d.fwd_tiles, std::max(1, div_up(sb_end - j0 - nb, SolveTile<R>::RT)));
+        d.bwd_tiles = std::max(d.bwd_tiles, std::max(1, div_up(j0 - sb_beg, SolveTile<R>::CT)));
       }
       lv.steps.push_back(d);
     }
@@ -451,9 +480,15 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   else build_steps<float>(c);
   TRY(upload(c, &c->f21, c->f21_h));
   TRY(upload(c, &c->b21, c->b21_h));
+  TRY(upload(c, &c->sbf, c->sbf_h));
+  TRY(upload(c, &c->sbb, c->sbb_h));
   for (LevelDev &lv : c->levels) {
     lv.f21_tasks = c->f21 + (uintptr_t)lv.f21_tasks;
     lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
+    for (auto &sb : lv.sb) {
+      sb.fwd = c->sbf + (uintptr_t)sb.fwd;
+      sb.bwd = c->sbb + (uintptr_t)sb.bwd;
+    }
   }
   for (const LevelDev &lv : c->levels)
     if (lv.nf > 65535) return fail(c, TEM_ERR_MESH, "more than 65535 fronts in one tree level");
@@ -706,8 +741,10 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   o->min_pivot_abs = mp;
   o->nnz_l11 = c->sym.nnz_l11;
   int64_t nl = 0;
-  for (const LevelDev &lv : c->levels)
+  for (const LevelDev &lv : c->levels) {
     nl += 2 * (int64_t)lv.steps.size() + (lv.n_f21 > 0 ? 1 : 0) + (lv.n_b21 > 0 ? 1 : 0);
+    for (const auto &sb : lv.sb) nl += (sb.n_fwd > 0 ? 1 : 0) + (sb.n_bwd > 0 ? 1 : 0);
+  }
   o->n_solve_launch = nl;
   return TEM_OK;
 }
@@ -744,9 +781,11 @@ int tem_export_dofs(tem_ctx *c, int64_t *edge_verts) {
 
 int tem_set_profiling(tem_ctx *c, int kernel_class) {
   if (!c) return TEM_ERR_ARG;
-  if (kernel_class < -1 || kernel_class >= KC_COUNT) return fail(c, TEM_ERR_ARG, "bad kernel class");
+  const int cls = kernel_class < 0 ? -1 : kernel_class % 64, lev = kernel_class < 0 ? -1 : kernel_class / 64 - 1;
+  if (kernel_class < -1 || cls >= KC_COUNT) return fail(c, TEM_ERR_ARG, "bad kernel class");
   c->prof.on = kernel_class >= 0;
-  c->prof.cls = kernel_class;
+  c->prof.cls = cls;
+  c->prof.level = lev;
   c->prof.total_ms = 0;
   c->prof.launches = 0;
   c->prof.used = 0;

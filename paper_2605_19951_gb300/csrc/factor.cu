@@ -353,6 +353,7 @@ void launch_mvals_floor(const int64_t *mc_ptr, const uint32_t *mc_idx, const dou
 template <typename R>
 void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
   const int m = this->m;
+  if (g_prof) g_prof->cur_level = lv.h;
   // 1. zero this level's factor blocks and update blocks
   if (lv.lend > lv.lbeg)
     for (int p = 0; p < m; p++)

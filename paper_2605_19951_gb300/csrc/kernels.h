@@ -11,6 +11,8 @@ namespace tem {
 
 constexpr int kNB = 32;        // pivot block width of the blocked LDL^T and the solves
 constexpr int kPanelRT = 128;  // panel rows per CTA
+constexpr int kSB = 256;       // super-block of the solves' pivot blocks (multiple of kNB)
+constexpr int kSplitK = 512;   // inner-dimension chunk of one super-block product task
 
 template <typename R>
 struct UpdateTile;
@@ -53,6 +55,7 @@ struct StepDims {
 struct LevelDev {
   const int32_t *fronts = nullptr;  // device list, sorted by k descending
   int nf = 0;
+  int h = 0;                        // level index (height in the assembly tree)
   const int2 *f21_tasks = nullptr;  // (front, row tile) of the forward L21 product
   int n_f21 = 0;
   const int2 *b21_tasks = nullptr;  // (front, column tile) of the backward L21 product
@@ -61,6 +64,13 @@ struct LevelDev {
   int64_t lbeg = 0, lend = 0, obeg = 0, oend = 0;
   int64_t ea_beg[2] = {0, 0}, ea_end[2] = {0, 0};
   std::vector<StepDims> steps;
+  struct SuperBlock {
+    const int4 *fwd = nullptr;   // (front, row tile, k begin, k end) of k_fwd_sb
+    int n_fwd = 0;
+    const int4 *bwd = nullptr;   // (front, column tile, row begin, row end) of k_bwd_sb
+    int n_bwd = 0;
+  };
+  std::vector<SuperBlock> sb;
 };
 
 template <typename R>
@@ -160,10 +170,14 @@ void launch_lsqr_kernel(int op, LsqrScalars *sc, double *a, const double *b, con
 void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 
 // Kernel classes that can be timed individually with CUDA events.
-enum KernelClass { KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_COUNT };
+enum KernelClass {
+  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_COUNT
+};
 struct Profiler {
   bool on = false;
   int cls = -1;                        // class being timed
+  int level = -1;                      // tree level being timed (-1: all)
+  int cur_level = -1;                  // level of the launches being issued
   std::vector<cudaEvent_t> pool;       // start/stop pairs
   int used = 0;
   double total_ms = 0;

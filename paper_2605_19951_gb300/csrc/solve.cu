@@ -16,6 +16,10 @@
 //   k_bwd_l21  once: w = D^-1 y - L21^T x_upd (tiled GEMM, no atomics);
 //   k_bwd_l11  reverse pivot steps: x_j = Linv_jj^T w_j, then the pivot
 //              columns left of the block -= L[j rows, c]^T x_j.
+// The pivot blocks are also grouped in super-blocks of kSB pivots: the step
+// kernels only touch rows / columns inside their super-block, and the rest
+// of the pivot-block work of a super-block is one split-K product
+// (k_fwd_sb: y_J -= L[J, 0:J0] x; k_bwd_sb: w_J -= L[J1:k, J]^T x).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -56,9 +60,10 @@ __global__ void __launch_bounds__(256) k_fwd_l11(const cx<R> *__restrict__ L, in
   if (j0 >= f.k) return;
   const int nb = min(NB, f.k - j0);
   const int64_t n = f.n;
-  const int rbeg = j0 + nb;                       // pivot rows below the block: [rbeg, k)
+  const int rbeg = j0 + nb;                       // pivot rows below the block ...
+  const int rend = min(f.k, (j0 / kSB + 1) * kSB);  // ... inside its super-block
   const int tile = blockIdx.x;
-  if (tile > 0 && rbeg + tile * RT >= f.k) return;
+  if (tile > 0 && rbeg + tile * RT >= rend) return;
   const cx<R> *A = L + p * lstride + f.lofs;
   const cx<R> *Iv = Linv + p * istride + (f.inv_off + step) * (NB * NB);
   cx<R> *Yp = Y + p * vstride;
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(256) k_fwd_l11(const cx<R> *__restrict__ L, in
   const int r0 = rbeg + tile * RT;
   for (int idx = threadIdx.x; idx < NB * RT; idx += 256) {
     int c = idx / RT, i = idx % RT;
-    Lt[c][i] = (c < nb && r0 + i < f.k) ? A[(j0 + c) * n + r0 + i] : mk<R>(R(0), R(0));
+    Lt[c][i] = (c < nb && r0 + i < rend) ? A[(j0 + c) * n + r0 + i] : mk<R>(R(0), R(0));
   }
   __syncthreads();
   small_apply<R, NB>(Inv, xs, warp, lane, false);   // y_j = Linv_jj b_j
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(256) k_fwd_l11(const cx<R> *__restrict__ L, in
     for (int i = warp; i < nb; i += 8) Xp[int64_t(f.c0 + j0 + i) * nrhs + rhs] = xs[i][lane];
   for (int i = warp; i < RT; i += 8) {
     const int r = r0 + i;
-    if (r >= f.k) break;
+    if (r >= rend) break;
     cx<R> acc = mk<R>(R(0), R(0));
 #pragma unroll 8
     for (int c = 0; c < NB; c++) cfma(acc, Lt[c][i], xs[c][lane]);
@@ -213,7 +218,8 @@ __global__ void __launch_bounds__(256) k_bwd_l11(const cx<R> *__restrict__ L, in
   if (j0 >= f.k) return;
   const int nb = min(NB, f.k - j0);
   const int tile = blockIdx.x;
-  if (tile > 0 && tile * CT >= j0) return;
+  const int cfirst = (j0 / kSB) * kSB;           // columns left of the block inside its super-block
+  if (tile > 0 && cfirst + tile * CT >= j0) return;
   const int64_t n = f.n;
   const cx<R> *A = L + p * lstride + f.lofs;
   const cx<R> *Iv = Linv + p * istride + (f.inv_off + step) * (NB * NB);
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(256) k_bwd_l11(const cx<R> *__restrict__ L, in
   for (int idx = threadIdx.x; idx < NB * NB; idx += 256) Inv[idx / NB][idx % NB] = Iv[idx];
   for (int i = warp; i < NB; i += 8)
     xs[i][lane] = (ok && i < nb) ? Yp[int64_t(f.c0 + j0 + i) * nrhs + rhs] : mk<R>(R(0), R(0));
-  const int cbeg = tile * CT;
+  const int cbeg = cfirst + tile * CT;
   for (int idx = threadIdx.x; idx < NB * CT; idx += 256) {
     int i = idx % NB, cc = idx / NB;
     Lb[cc][i] = (i < nb && cbeg + cc < j0) ? A[int64_t(cbeg + cc) * n + j0 + i] : mk<R>(R(0), R(0));
@@ -249,10 +255,122 @@ __global__ void __launch_bounds__(256) k_bwd_l11(const cx<R> *__restrict__ L, in
   }
 }
 
+// Super-block products of the pivot blocks (split over the inner dimension,
+// atomically accumulated; every task owns one output tile and one K range).
+// Forward: Y[c0 + r] -= sum_{c in [kb, ke)} L[r][c] X[c0 + c] for the rows r
+// of super-block J (task = front, row tile of BM, K range).
+template <typename R, int BM, int KC>
+__global__ void __launch_bounds__(256) k_fwd_sb(const cx<R> *__restrict__ L, int64_t lstride,
+                                                const FrontDev *__restrict__ F, const int4 *__restrict__ tasks,
+                                                int sb, cx<R> *__restrict__ Y, const cx<R> *__restrict__ X,
+                                                int64_t vstride, int nrhs, int nchunk) {
+  constexpr int RW = BM / 8;
+  const int4 t = tasks[blockIdx.x];
+  const FrontDev f = F[t.x];
+  const int p = blockIdx.y / nchunk, ch = blockIdx.y % nchunk;
+  const int64_t n = f.n;
+  const int rlo = sb * kSB, rhi = min(f.k, rlo + kSB);
+  const int i0 = rlo + t.y * BM;
+  const cx<R> *A = L + p * lstride + f.lofs;
+  const cx<R> *Xp = X + p * vstride;
+  cx<R> *Yp = Y + p * vstride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rhs = ch * 32 + lane;
+  const bool ok = rhs < nrhs;
+  __shared__ cx<R> Ls[KC][BM];
+  __shared__ cx<R> Xs[KC][32];
+  cx<R> acc[RW];
+#pragma unroll
+  for (int q = 0; q < RW; q++) acc[q] = mk<R>(R(0), R(0));
+  for (int c0 = t.z; c0 < t.w; c0 += KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KC * BM; idx += 256) {
+      int c = idx / BM, i = idx % BM;
+      Ls[c][i] = (c0 + c < t.w && i0 + i < rhi) ? A[int64_t(c0 + c) * n + i0 + i] : mk<R>(R(0), R(0));
+    }
+    for (int c = warp; c < KC; c += 8)
+      Xs[c][lane] = (ok && c0 + c < t.w) ? Xp[int64_t(f.c0 + c0 + c) * nrhs + rhs] : mk<R>(R(0), R(0));
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < KC; c++) {
+      const cx<R> x = Xs[c][lane];
+#pragma unroll
+      for (int q = 0; q < RW; q++) cfma(acc[q], Ls[c][warp * RW + q], x);
+    }
+  }
+  if (!ok) return;
+#pragma unroll
+  for (int q = 0; q < RW; q++) {
+    const int i = i0 + warp * RW + q;
+    if (i < rhi) atomic_add_cx(Yp + int64_t(f.c0 + i) * nrhs + rhs, mk<R>(-acc[q].x, -acc[q].y));
+  }
+}
+
+// Backward: W[c0 + c] -= sum_{r in [kb, ke)} L[r][c] X[c0 + r] for the
+// columns c of super-block J (task = front, column tile of BN, K range of rows).
+template <typename R, int BN, int KC>
+__global__ void __launch_bounds__(256) k_bwd_sb(const cx<R> *__restrict__ L, int64_t lstride,
+                                                const FrontDev *__restrict__ F, const int4 *__restrict__ tasks,
+                                                int sb, cx<R> *__restrict__ Y, const cx<R> *__restrict__ X,
+                                                int64_t vstride, int nrhs, int nchunk) {
+  constexpr int CW = BN / 8;
+  const int4 t = tasks[blockIdx.x];
+  const FrontDev f = F[t.x];
+  const int p = blockIdx.y / nchunk, ch = blockIdx.y % nchunk;
+  const int64_t n = f.n;
+  const int clo = sb * kSB, chi = min(f.k, clo + kSB);
+  const int cb = clo + t.y * BN;
+  const cx<R> *A = L + p * lstride + f.lofs;
+  const cx<R> *Xp = X + p * vstride;
+  cx<R> *Yp = Y + p * vstride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rhs = ch * 32 + lane;
+  const bool ok = rhs < nrhs;
+  __shared__ cx<R> Ls[KC][BN + 1];
+  __shared__ cx<R> Xs[KC][32];
+  cx<R> acc[CW];
+#pragma unroll
+  for (int q = 0; q < CW; q++) acc[q] = mk<R>(R(0), R(0));
+  for (int i0 = t.z; i0 < t.w; i0 += KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KC * BN; idx += 256) {
+      int i = idx % KC, c = idx / KC;
+      Ls[i][c] = (i0 + i < t.w && cb + c < chi) ? A[int64_t(cb + c) * n + i0 + i] : mk<R>(R(0), R(0));
+    }
+    for (int i = warp; i < KC; i += 8)
+      Xs[i][lane] = (ok && i0 + i < t.w) ? Xp[int64_t(f.c0 + i0 + i) * nrhs + rhs] : mk<R>(R(0), R(0));
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < KC; i++) {
+      const cx<R> x = Xs[i][lane];
+#pragma unroll
+      for (int q = 0; q < CW; q++) cfma(acc[q], Ls[i][warp * CW + q], x);
+    }
+  }
+  if (!ok) return;
+#pragma unroll
+  for (int q = 0; q < CW; q++) {
+    const int c = cb + warp * CW + q;
+    if (c >= chi) break;
+    atomic_add_cx(Yp + int64_t(f.c0 + c) * nrhs + rhs, mk<R>(-acc[q].x, -acc[q].y));
+  }
+}
+
 template <typename R>
 void SolvePlan<R>::forward_level(const LevelDev &lv, cudaStream_t s) {
+  if (g_prof) g_prof->cur_level = lv.h;
   const int nchunk = (nrhs + 31) / 32;
+  const int per_sb = kSB / kNB;
   for (int step = 0; step < (int)lv.steps.size(); step++) {
+    const int sb = step / per_sb;
+    if (step % per_sb == 0 && sb > 0 && lv.sb[sb].n_fwd > 0) {
+      dim3 g(lv.sb[sb].n_fwd, m * nchunk);
+      if (g_prof) g_prof->begin(KC_FWD_SB, s);
+      tem::count_launch();
+      k_fwd_sb<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].fwd, sb, Y, X,
+                                                                         vstride, nrhs, nchunk);
+      if (g_prof) g_prof->end(KC_FWD_SB, s);
+    }
     const StepDims &sd = lv.steps[step];
     dim3 g(sd.fwd_tiles, sd.nfronts, m * nchunk);
     if (g_prof) g_prof->begin(KC_FWD, s);
@@ -273,7 +391,9 @@ void SolvePlan<R>::forward_level(const LevelDev &lv, cudaStream_t s) {
 
 template <typename R>
 void SolvePlan<R>::backward_level(const LevelDev &lv, cudaStream_t s) {
+  if (g_prof) g_prof->cur_level = lv.h;
   const int nchunk = (nrhs + 31) / 32;
+  const int per_sb = kSB / kNB;
   if (lv.n_b21 > 0) {
     dim3 g(lv.n_b21, m * nchunk);
     if (g_prof) g_prof->begin(KC_BWD_UPD, s);
@@ -283,6 +403,15 @@ void SolvePlan<R>::backward_level(const LevelDev &lv, cudaStream_t s) {
     if (g_prof) g_prof->end(KC_BWD_UPD, s);
   }
   for (int step = (int)lv.steps.size() - 1; step >= 0; step--) {
+    const int sb = step / per_sb;
+    if ((step == (int)lv.steps.size() - 1 || step % per_sb == per_sb - 1) && lv.sb[sb].n_bwd > 0) {
+      dim3 g(lv.sb[sb].n_bwd, m * nchunk);
+      if (g_prof) g_prof->begin(KC_BWD_SB, s);
+      tem::count_launch();
+      k_bwd_sb<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].bwd, sb, Y, X,
+                                                                         vstride, nrhs, nchunk);
+      if (g_prof) g_prof->end(KC_BWD_SB, s);
+    }
     const StepDims &sd = lv.steps[step];
     dim3 g(sd.bwd_tiles, sd.nfronts, m * nchunk);
     if (g_prof) g_prof->begin(KC_BWD, s);
