@@ -78,6 +78,8 @@ typedef struct tem_stats {
   double min_pivot_abs;  /* smallest |d_kk| seen in the last factorisation */
   int64_t nnz_l11;       /* factor entries in the pivot blocks (sum k(k+1)/2) */
   int64_t n_solve_launch;/* kernel launches of one solve (forward + backward sweep) */
+  int64_t pole_solves;   /* poles x (forward + backward sweep) issued so far */
+  int64_t solve_calls;   /* multi-pole solves issued so far (each with its refinement) */
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or
@@ -183,8 +185,19 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
  * whose cells are all floored are eigenvectors of P_i^-1 A_i, every
  * right-hand side of the path is orthogonal to them and no output reads
  * them, so the refined data converge to those of A_i.  The FP64 mode factors
- * A_i itself.  steps in 0..20, floor_tau in [0, 1]. */
-int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau);
+ * A_i itself.  With tol > 0 a pole stops refining once its last correction,
+ * over the unknowns every output reads (edges of parameter cells), is below
+ * tol times the solution there; the remaining sweeps run over the poles still
+ * refining (one host read per step).  steps in 0..20 (the maximum),
+ * floor_tau in [0, 1], tol in [0, 1] (0: always steps corrections). */
+int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau, double tol);
+
+/* TEM_FP32_REFINED mode: run the update-row products of the solves on the
+ * tensor cores (tcgen05, TF32 split into hi + lo parts, three MMAs per
+ * product, FP32 accumulation; default 1) or on the FP32 pipes (0).  A
+ * tensor-core completion wait that gives up makes the call return
+ * TEM_ERR_TIMEOUT.  No effect in TEM_FP64 mode. */
+int tem_set_tensor_cores(tem_ctx *ctx, int enable);
 
 /* Time one class of kernels with CUDA events on the context's stream:
  * 0 trailing update, 1 panel, 2 forward pivot-block step, 3 backward

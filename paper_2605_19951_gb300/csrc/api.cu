@@ -75,6 +75,12 @@ struct tem_ctx {
   int state = 0;
   int refine = 6;
   double floor_tau = 1e-4;   // FP32 mode: conductivity floor of the factored matrix
+  double refine_tol = 0.0;   // FP32 mode: stop a pole's refinement below this progress (0: fixed count)
+  int64_t pole_solves = 0;   // statistics: poles x sweeps pairs issued
+  int64_t solve_calls = 0;
+  uint8_t *earth = nullptr;  // unknowns on edges of parameter cells (what every output reads)
+  int *pmap = nullptr;       // device list of the poles still refining
+  double *prog = nullptr;    // [2m] progress maxima
   int64_t bytes = 0;
   std::vector<void *> allocs;
   Profiler prof;
@@ -88,6 +94,9 @@ struct tem_ctx {
   int2 *f21 = nullptr, *b21 = nullptr;
   std::vector<int4> sbf_h, sbb_h;         // task lists of the super-block products
   int4 *sbf = nullptr, *sbb = nullptr;
+  std::vector<int2> f21tc_h, b21tc_h;     // task lists of the tensor-core L21 products
+  int2 *f21tc = nullptr, *b21tc = nullptr;
+  bool use_tc = true;                     // FP32 mode: L21 products on tcgen05
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -189,6 +198,15 @@ int sync(tem_ctx *c, const char *where) {
   return TEM_OK;
 }
 
+// Status words written by the solve kernels (bounded tensor-core waits).
+int check_solve_status(tem_ctx *c) {
+  DevStatus h{};
+  CK(cudaMemcpyAsync(&h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h.tc_timeout) return fail(c, TEM_ERR_TIMEOUT, "a tensor-core completion wait expired in a solve");
+  return TEM_OK;
+}
+
 struct ProfScope {
   explicit ProfScope(tem_ctx *c) { g_prof = c->prof.on ? &c->prof : nullptr; }
   ~ProfScope() { g_prof = nullptr; }
@@ -203,6 +221,8 @@ void build_steps(tem_ctx *c) {
   c->b21_h.clear();
   c->sbf_h.clear();
   c->sbb_h.clear();
+  c->f21tc_h.clear();
+  c->b21tc_h.clear();
   c->max_level_fronts = 0;
   int64_t off = 0;
   for (const Level &L : S.levels) {
@@ -235,6 +255,19 @@ void build_steps(tem_ctx *c) {
     }
     lv.n_f21 = int(c->f21_h.size() - f21_beg);
     lv.n_b21 = int(c->b21_h.size() - b21_beg);
+    const size_t f21tc_beg = c->f21tc_h.size(), b21tc_beg = c->b21tc_h.size();
+    for (int32_t fi : L.fronts) {
+      const Front &F = S.fronts[fi];
+      const int b = F.n - F.k;
+      if (F.k <= 0) continue;
+      if (b > 0)
+        for (int t = 0; t < div_up(b, 64); t++) c->f21tc_h.push_back(make_int2(fi, t));
+      for (int t = 0; t < div_up(F.k, 64); t++) c->b21tc_h.push_back(make_int2(fi, t));
+    }
+    lv.n_f21tc = int(c->f21tc_h.size() - f21tc_beg);
+    lv.n_b21tc = int(c->b21tc_h.size() - b21tc_beg);
+    lv.f21tc_tasks = (const int2 *)(uintptr_t)f21tc_beg;
+    lv.b21tc_tasks = (const int2 *)(uintptr_t)b21tc_beg;
     lv.f21_tasks = (const int2 *)(uintptr_t)f21_beg;   // offsets until the lists are on the device
     lv.b21_tasks = (const int2 *)(uintptr_t)b21_beg;
     // super-block products: forward rows of block J against pivots [0, J0);
@@ -327,33 +360,62 @@ SolvePlan<R> solve_plan(tem_ctx *c) {
 }
 
 template <typename R>
-void sweeps(tem_ctx *c) {
+void sweeps(tem_ctx *c, const int *pmap, int np) {
   SolvePlan<R> P = solve_plan<R>(c);
+  P.pmap = pmap;
+  P.np = np;
+  P.use_tc = c->use_tc;
+  P.status = c->status;
+  c->pole_solves += np;
   const int H = (int)c->levels.size();
   for (int h = 0; h < H; h++) P.forward_level(c->levels[h], c->stream);
   for (int h = H - 1; h >= 0; h--) P.backward_level(c->levels[h], c->stream);
 }
 
 // x = A_i^-1 b for all poles; b c128 with pole stride bstride (0 = shared).
-void solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
+// FP32 mode: refinement x += P_i^-1 (b - A_i x) with the FP64 residual; with
+// refine_tol > 0 a pole stops once its correction on the unknowns the outputs
+// read (edges of parameter cells) is below refine_tol of the solution there,
+// and later sweeps run over the remaining poles only (a host read per step).
+int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
   const int64_t N = c->mesh.N;
   const int nx = c->n_tx, m = c->m;
   cudaStream_t s = c->stream;
+  c->solve_calls++;
   if (c->precision == TEM_FP64) {
-    launch_rhs_to_work<double>(b, bstride, (c128 *)c->Y, nullptr, m, N, nx, false, s);
-    sweeps<double>(c);
-    launch_accumulate<double>((const c128 *)c->X, nullptr, x, m, N, nx, false, s);
-  } else {
-    launch_rhs_to_work<float>(b, bstride, (c64 *)c->Y, c->colmax, m, N, nx, true, s);
-    sweeps<float>(c);
-    launch_accumulate<float>((const c64 *)c->X, c->colmax, x, m, N, nx, false, s);
-    for (int it = 0; it < c->refine; it++) {
-      launch_residual(c->rp, c->ci, c->kval, c->mval, c->xi, b, bstride, x, c->r, m, N, nx, s);
-      launch_rhs_to_work<float>(c->r, N * nx, (c64 *)c->Y, c->colmax, m, N, nx, true, s);
-      sweeps<float>(c);
-      launch_accumulate<float>((const c64 *)c->X, c->colmax, x, m, N, nx, true, s);
-    }
+    launch_rhs_to_work<double>(b, bstride, (c128 *)c->Y, nullptr, m, nullptr, N, nx, false, s);
+    sweeps<double>(c, nullptr, m);
+    launch_accumulate<double>((const c128 *)c->X, nullptr, x, m, nullptr, N, nx, false, s);
+    return TEM_OK;
   }
+  launch_rhs_to_work<float>(b, bstride, (c64 *)c->Y, c->colmax, m, nullptr, N, nx, true, s);
+  sweeps<float>(c, nullptr, m);
+  launch_accumulate<float>((const c64 *)c->X, c->colmax, x, m, nullptr, N, nx, false, s);
+  const int *pm = nullptr;
+  int np = m;
+  for (int it = 0; it < c->refine; it++) {
+    launch_residual(c->rp, c->ci, c->kval, c->mval, c->xi, b, bstride, x, c->r, np, pm, N, nx, s);
+    launch_rhs_to_work<float>(c->r, N * nx, (c64 *)c->Y, c->colmax, np, pm, N, nx, true, s);
+    sweeps<float>(c, pm, np);
+    launch_accumulate<float>((const c64 *)c->X, c->colmax, x, np, pm, N, nx, true, s);
+    if (c->refine_tol <= 0 || it + 1 == c->refine) continue;
+    CK(cudaMemsetAsync(c->prog, 0, sizeof(double) * 2 * m, s));
+    launch_progress<float>((const c64 *)c->X, c->colmax, x, c->earth, c->prog, c->prog + m, np, pm, N, nx, s);
+    std::vector<double> pr(2 * m);
+    std::vector<int> keep;
+    CK(cudaMemcpyAsync(pr.data(), c->prog, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> cur(np);
+    if (pm) CK(cudaMemcpy(cur.data(), pm, sizeof(int) * np, cudaMemcpyDeviceToHost));
+    else for (int i = 0; i < np; i++) cur[i] = i;
+    for (int p : cur)
+      if (pr[p] > c->refine_tol * pr[m + p]) keep.push_back(p);
+    if (keep.empty()) break;
+    CK(cudaMemcpy(c->pmap, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice));
+    pm = c->pmap;
+    np = (int)keep.size();
+  }
+  return TEM_OK;
 }
 
 int ensure_numeric(tem_ctx *c) {
@@ -387,6 +449,8 @@ int ensure_numeric(tem_ctx *c) {
   TRY(dalloc(c, &c->fb, size_t(N) * nx));
   TRY(dalloc(c, &c->colmax, size_t(m) * nx));
   TRY(dalloc(c, &c->d_cur, size_t(nx) * c->n_rx * c->K));
+  TRY(dalloc(c, &c->pmap, size_t(m)));
+  TRY(dalloc(c, &c->prog, size_t(2 * m)));
   TRY(dalloc(c, &c->m_cur, size_t(std::max<int64_t>(1, c->mesh.P))));
   return TEM_OK;
 }
@@ -451,6 +515,14 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->inc_loc, M.inc_loc));
   TRY(upload(c, &c->tdof, M.tdof));
   TRY(upload(c, &c->pidx, M.pidx));
+  {
+    std::vector<uint8_t> earth(M.N, 0);
+    for (int64_t t = 0; t < M.nt; t++)
+      if (M.is_param[t])
+        for (int a = 0; a < 6; a++)
+          if (M.tdof[6 * t + a] >= 0) earth[M.tdof[6 * t + a]] = 1;
+    TRY(upload(c, &c->earth, earth));
+  }
   TRY(upload(c, &c->ptet, M.ptet));
   std::vector<FrontDev> fd(S.fronts.size());
   int64_t inv = 0;
@@ -482,9 +554,13 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->b21, c->b21_h));
   TRY(upload(c, &c->sbf, c->sbf_h));
   TRY(upload(c, &c->sbb, c->sbb_h));
+  TRY(upload(c, &c->f21tc, c->f21tc_h));
+  TRY(upload(c, &c->b21tc, c->b21tc_h));
   for (LevelDev &lv : c->levels) {
     lv.f21_tasks = c->f21 + (uintptr_t)lv.f21_tasks;
     lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
+    lv.f21tc_tasks = c->f21tc + (uintptr_t)lv.f21tc_tasks;
+    lv.b21tc_tasks = c->b21tc + (uintptr_t)lv.b21tc_tasks;
     for (auto &sb : lv.sb) {
       sb.fwd = c->sbf + (uintptr_t)sb.fwd;
       sb.bwd = c->sbb + (uintptr_t)sb.bwd;
@@ -598,29 +674,32 @@ int tem_forward(tem_ctx *c, double *d) {
   cudaStream_t s = c->stream;
   const int64_t N = c->mesh.N;
   launch_real_to_c128(c->f, c->fb, N * c->n_tx, s);
-  solve_all(c, c->fb, 0, c->g);
+  TRY(solve_all(c, c->fb, 0, c->g));
   launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->g, d, c->m, N, c->n_tx, c->n_rx, c->K, s);
   CK(cudaMemcpyAsync(c->d_cur, d, sizeof(double) * c->n_tx * c->n_rx * c->K, cudaMemcpyDeviceToDevice, s));
   TRY(sync(c, "tem_forward"));
+  TRY(check_solve_status(c));
   c->state |= ST_FORWARD;
   return TEM_OK;
 }
 
 namespace {
-void jvp_async(tem_ctx *c, const double *v, double *jv) {
+int jvp_async(tem_ctx *c, const double *v, double *jv) {
   const int64_t N = c->mesh.N;
   launch_dm_apply(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->pidx, v, c->sigma, c->me1, c->xi, c->g, c->b,
                   c->m, N, c->n_tx, c->stream);
-  solve_all(c, c->b, N * c->n_tx, c->x);
+  TRY(solve_all(c, c->b, N * c->n_tx, c->x));
   launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->n_tx, c->n_rx, c->K, c->stream);
+  return TEM_OK;
 }
-void jtvp_async(tem_ctx *c, const double *w, double *jtw) {
+int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
   const int64_t N = c->mesh.N;
   launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->n_tx,
                 c->n_rx, c->K, c->stream);
-  solve_all(c, c->b, N * c->n_tx, c->x);
+  TRY(solve_all(c, c->b, N * c->n_tx, c->x));
   launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->n_tx,
                   c->stream);
+  return TEM_OK;
 }
 }  // namespace
 
@@ -629,8 +708,9 @@ int tem_jvp(tem_ctx *c, const double *v, double *jv) {
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!v || !jv) return fail(c, TEM_ERR_ARG, "NULL vector");
   ProfScope ps(c);
-  jvp_async(c, v, jv);
-  return sync(c, "tem_jvp");
+  TRY(jvp_async(c, v, jv));
+  TRY(sync(c, "tem_jvp"));
+  return check_solve_status(c);
 }
 
 int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
@@ -638,8 +718,9 @@ int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!w || !jtw) return fail(c, TEM_ERR_ARG, "NULL vector");
   ProfScope ps(c);
-  jtvp_async(c, w, jtw);
-  return sync(c, "tem_jtvp");
+  TRY(jtvp_async(c, w, jtw));
+  TRY(sync(c, "tem_jtvp"));
+  return check_solve_status(c);
 }
 
 int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref, double lambda,
@@ -674,7 +755,7 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
   launch_lsqr_scalars(sc, 0, s);  // beta
   // v = A^T u
   launch_lsqr_kernel(5, sc, c->ls_tmpd, u1, wd, nullptr, nd, s);
-  jtvp_async(c, c->ls_tmpd, c->ls_jtw);
+  TRY(jtvp_async(c, c->ls_tmpd, c->ls_jtw));
   CK(cudaMemcpyAsync(c->ls_v, c->ls_jtw, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
   launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, c->ls_v, P, sl, 1.0, s);
   launch_sumsq(c->ls_v, P, &sc->sumsq, s);
@@ -685,7 +766,7 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
   CK(cudaMemsetAsync(dm, 0, sizeof(double) * P, s));
   for (int it = 0; it < n_iter; it++) {
     // u = A v - alpha u
-    jvp_async(c, c->ls_v, c->ls_jv);
+    TRY(jvp_async(c, c->ls_v, c->ls_jv));
     launch_lsqr_kernel(2, sc, u1, c->ls_jv, wd, nullptr, nd, s);
     launch_csr_mv(c->w_rp, c->w_ci, c->w_val, c->ls_v, c->ls_wv, nf, sl, 0.0, s);
     launch_lsqr_kernel(7, sc, u2, c->ls_wv, nullptr, nullptr, nf, s);  // u2 = sl W v - alpha u2
@@ -694,7 +775,7 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
     launch_lsqr_scalars(sc, 0, s);  // beta
     // v = A^T u - beta v
     launch_lsqr_kernel(5, sc, c->ls_tmpd, u1, wd, nullptr, nd, s);
-    jtvp_async(c, c->ls_tmpd, c->ls_jtw);
+    TRY(jtvp_async(c, c->ls_tmpd, c->ls_jtw));
     launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, c->ls_jtw, P, sl, 1.0, s);
     launch_lsqr_kernel(3, sc, c->ls_v, c->ls_jtw, nullptr, nullptr, P, s);
     launch_sumsq(c->ls_v, P, &sc->sumsq, s);
@@ -703,15 +784,24 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
     launch_lsqr_scalars(sc, 3, s);  // rho, c, s, theta, phi
     launch_lsqr_kernel(4, sc, dm, c->ls_w, c->ls_v, nullptr, P, s);
   }
-  return sync(c, "tem_lsqr");
+  TRY(sync(c, "tem_lsqr"));
+  return check_solve_status(c);
 }
 
-int tem_set_refine(tem_ctx *c, int32_t steps, double floor_tau) {
+int tem_set_tensor_cores(tem_ctx *c, int enable) {
+  if (!c) return TEM_ERR_ARG;
+  c->use_tc = enable != 0;
+  return TEM_OK;
+}
+
+int tem_set_refine(tem_ctx *c, int32_t steps, double floor_tau, double tol) {
   if (!c) return TEM_ERR_ARG;
   if (steps < 0 || steps > 20) return fail(c, TEM_ERR_ARG, "refine steps in 0..20");
   if (!(floor_tau >= 0) || floor_tau > 1.0) return fail(c, TEM_ERR_ARG, "floor_tau in [0, 1]");
+  if (!(tol >= 0) || tol > 1.0) return fail(c, TEM_ERR_ARG, "tol in [0, 1]");
   c->refine = steps;
   c->floor_tau = floor_tau;
+  c->refine_tol = tol;
   return TEM_OK;
 }
 
@@ -740,6 +830,8 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   memcpy(&mp, &c->status_h.min_pivot_bits, sizeof(double));
   o->min_pivot_abs = mp;
   o->nnz_l11 = c->sym.nnz_l11;
+  o->pole_solves = c->pole_solves;
+  o->solve_calls = c->solve_calls;
   int64_t nl = 0;
   for (const LevelDev &lv : c->levels) {
     nl += 2 * (int64_t)lv.steps.size() + (lv.n_f21 > 0 ? 1 : 0) + (lv.n_b21 > 0 ? 1 : 0);
@@ -871,7 +963,7 @@ extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *w
   launch_lsqr_kernel(0, sc, u, nullptr, nullptr, nullptr, nd + nf, s);
   launch_lsqr_scalars(sc, 0, s);
   launch_lsqr_kernel(5, sc, tmpd, u1, wd, nullptr, nd, s);
-  jtvp_async(c, tmpd, jtw);
+  TRY(jtvp_async(c, tmpd, jtw));
   CK(cudaMemcpyAsync(v, jtw, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
   launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, v, P, sl, 1.0, s);
   launch_sumsq(v, P, &sc->sumsq, s);
@@ -881,7 +973,7 @@ extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *w
   CK(cudaMemcpyAsync(w, v, sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(dm, 0, sizeof(double) * P, s));
   for (int it = 0; it < n_iter; it++) {
-    jvp_async(c, v, jv);
+    TRY(jvp_async(c, v, jv));
     launch_lsqr_kernel(2, sc, u1, jv, wd, nullptr, nd, s);
     launch_csr_mv(c->w_rp, c->w_ci, c->w_val, v, wv, nf, sl, 0.0, s);
     launch_lsqr_kernel(7, sc, u2, wv, nullptr, nullptr, nf, s);
@@ -889,7 +981,7 @@ extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *w
     launch_lsqr_kernel(0, sc, u, nullptr, nullptr, nullptr, nd + nf, s);
     launch_lsqr_scalars(sc, 0, s);
     launch_lsqr_kernel(5, sc, tmpd, u1, wd, nullptr, nd, s);
-    jtvp_async(c, tmpd, jtw);
+    TRY(jtvp_async(c, tmpd, jtw));
     launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, u2, jtw, P, sl, 1.0, s);
     launch_lsqr_kernel(3, sc, v, jtw, nullptr, nullptr, P, s);
     launch_sumsq(v, P, &sc->sumsq, s);
@@ -898,5 +990,6 @@ extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *w
     launch_lsqr_scalars(sc, 3, s);
     launch_lsqr_kernel(4, sc, dm, w, v, nullptr, P, s);
   }
-  return sync(c, "tem_lsqr_noalloc");
+  TRY(sync(c, "tem_lsqr_noalloc"));
+  return check_solve_status(c);
 }

@@ -83,9 +83,14 @@ struct FrontDev {
 struct DevStatus {
   int32_t pivot_fail;       // 1 if a pivot underflowed
   int32_t pivot_front;      // front of the first failure
+  int32_t tc_timeout;       // 1 if a tensor-core completion wait gave up
+  int32_t pad_;
   unsigned long long min_pivot_bits;  // bits of the smallest |d_kk| (positive double)
 };
 
 inline int div_up(int64_t a, int64_t b) { return int((a + b - 1) / b); }
+
+// Pole of grid slot i: the identity, or the list of poles still refining.
+__device__ __forceinline__ int pole_of(int i, const int *pmap) { return pmap ? pmap[i] : i; }
 
 }  // namespace tem

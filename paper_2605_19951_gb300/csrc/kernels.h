@@ -60,6 +60,10 @@ struct LevelDev {
   int n_f21 = 0;
   const int2 *b21_tasks = nullptr;  // (front, column tile) of the backward L21 product
   int n_b21 = 0;
+  const int2 *f21tc_tasks = nullptr;  // the same for the tensor-core kernels (64-row / 64-column tiles)
+  int n_f21tc = 0;
+  const int2 *b21tc_tasks = nullptr;
+  int n_b21tc = 0;
   int bwd_upd_tiles = 0;            // ceil(max k / 8)
   int64_t lbeg = 0, lend = 0, obeg = 0, oend = 0;
   int64_t ea_beg[2] = {0, 0}, ea_end[2] = {0, 0};
@@ -110,9 +114,16 @@ struct SolvePlan {
   cx<R> *Y = nullptr;   // [m][N][nrhs] right-hand sides in, work space
   cx<R> *X = nullptr;   // [m][N][nrhs] solution out
   int64_t vstride = 0;  // N * nrhs
+  const int *pmap = nullptr;  // device list of the poles to solve (nullptr: all)
+  int np = 0;                 // poles solved
+  bool use_tc = false;        // FP32: update-row products on the tensor cores
+  DevStatus *status = nullptr;
   void forward_level(const LevelDev &lv, cudaStream_t s);
   void backward_level(const LevelDev &lv, cudaStream_t s);
 };
+
+void launch_fwd_l21_tc(const SolvePlan<float> &P, const LevelDev &lv, DevStatus *st, cudaStream_t s);
+void launch_bwd_l21_tc(const SolvePlan<float> &P, const LevelDev &lv, DevStatus *st, cudaStream_t s);
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s);
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
@@ -124,17 +135,23 @@ void launch_mvals_floor(const int64_t *mc_ptr, const uint32_t *mc_idx, const dou
 // ---- ops.cu ----
 // b (c128, pole stride bstride elements, may be 0) -> Y (R) scaled per (pole, rhs) column
 // by 1/colmax; colmax [m][nrhs] written (FP32 mode).  With scale == false a plain copy.
+// All four take a pole map (device, np entries; nullptr = poles 0..np-1).
 template <typename R>
-void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax, int m, int64_t N,
-                        int nrhs, bool scale, cudaStream_t s);
+void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax, int np, const int *pmap,
+                        int64_t N, int nrhs, bool scale, cudaStream_t s);
 // x (c128) (+)= colmax * X (R)
 template <typename R>
-void launch_accumulate(const cx<R> *X, const double *colmax, c128 *x, int m, int64_t N, int nrhs,
-                       bool add, cudaStream_t s);
+void launch_accumulate(const cx<R> *X, const double *colmax, c128 *x, int np, const int *pmap, int64_t N,
+                       int nrhs, bool add, cudaStream_t s);
 // r = b - (K - xi_p M) x,  FP64
 void launch_residual(const int64_t *rp, const int32_t *ci, const double *kv, const double *mv,
                      const double2 *xi, const c128 *b, int64_t bstride, const c128 *x, c128 *r,
-                     int m, int64_t N, int nrhs, cudaStream_t s);
+                     int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s);
+// Refinement progress of each mapped pole over the masked unknowns:
+// num[p] = max |colmax * X|, den[p] = max |x| (double bits, max-accumulated).
+template <typename R>
+void launch_progress(const cx<R> *X, const double *colmax, const c128 *x, const uint8_t *mask, double *num,
+                     double *den, int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s);
 // F (real [N][nrhs]) -> c128 b
 void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s);
 // d[x][r][j] = 2 Re sum_p alpha_pj coef_p (Q y_p)[r][x]; coef = 1 (forward) or xi_p

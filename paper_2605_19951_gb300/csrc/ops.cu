@@ -16,8 +16,8 @@ namespace tem {
 // lanes per block, shared-memory reduction over the groups, one atomic per
 // block and column.
 __global__ void k_colmax(const c128 *__restrict__ b, int64_t bstride, double *colmax, int64_t N,
-                         int nrhs) {
-  const int p = blockIdx.y;
+                         int nrhs, const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
   const c128 *bp = b + p * bstride;
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   __shared__ double red[8][32];
@@ -42,8 +42,9 @@ __global__ void k_colmax(const c128 *__restrict__ b, int64_t bstride, double *co
 
 template <typename R>
 __global__ void k_rhs_to_work(const c128 *__restrict__ b, int64_t bstride, cx<R> *__restrict__ Y,
-                              const double *__restrict__ colmax, int64_t N, int nrhs) {
-  const int p = blockIdx.y;
+                              const double *__restrict__ colmax, int64_t N, int nrhs,
+                              const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
   const c128 *bp = b + p * bstride;
   cx<R> *yp = Y + p * N * nrhs;
   const int64_t cnt = N * nrhs;
@@ -59,24 +60,31 @@ __global__ void k_rhs_to_work(const c128 *__restrict__ b, int64_t bstride, cx<R>
   }
 }
 
+__global__ void k_zero_colmax(double *colmax, int nrhs, const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.x, pmap);
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) colmax[p * nrhs + r] = 0.0;
+}
+
 template <typename R>
-void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax, int m, int64_t N,
-                        int nrhs, bool scale, cudaStream_t s) {
-  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
+void launch_rhs_to_work(const c128 *b, int64_t bstride, cx<R> *Y, double *colmax, int np, const int *pmap,
+                        int64_t N, int nrhs, bool scale, cudaStream_t s) {
+  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), np);
   if (scale) {
-    cudaMemsetAsync(colmax, 0, sizeof(double) * m * nrhs, s);
-    dim3 gc((unsigned)std::min<int64_t>(div_up(N, 8), 512), m);
     tem::count_launch();
-    k_colmax<<<gc, 256, 0, s>>>(b, bstride, colmax, N, nrhs);
+    k_zero_colmax<<<np, 64, 0, s>>>(colmax, nrhs, pmap);
+    dim3 gc((unsigned)std::min<int64_t>(div_up(N, 8), 512), np);
+    tem::count_launch();
+    k_colmax<<<gc, 256, 0, s>>>(b, bstride, colmax, N, nrhs, pmap);
   }
   tem::count_launch();
-  k_rhs_to_work<R><<<g, 256, 0, s>>>(b, bstride, Y, scale ? colmax : nullptr, N, nrhs);
+  k_rhs_to_work<R><<<g, 256, 0, s>>>(b, bstride, Y, scale ? colmax : nullptr, N, nrhs, pmap);
 }
 
 template <typename R>
 __global__ void k_accumulate(const cx<R> *__restrict__ X, const double *__restrict__ colmax,
-                             c128 *__restrict__ x, int64_t N, int nrhs, int add) {
-  const int p = blockIdx.y;
+                             c128 *__restrict__ x, int64_t N, int nrhs, int add,
+                             const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
   const cx<R> *Xp = X + p * N * nrhs;
   c128 *xp = x + p * N * nrhs;
   const int64_t cnt = N * nrhs;
@@ -94,11 +102,48 @@ __global__ void k_accumulate(const cx<R> *__restrict__ X, const double *__restri
 }
 
 template <typename R>
-void launch_accumulate(const cx<R> *X, const double *colmax, c128 *x, int m, int64_t N, int nrhs,
-                       bool add, cudaStream_t s) {
-  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), m);
+void launch_accumulate(const cx<R> *X, const double *colmax, c128 *x, int np, const int *pmap, int64_t N,
+                       int nrhs, bool add, cudaStream_t s) {
+  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 2048), np);
   tem::count_launch();
-  k_accumulate<R><<<g, 256, 0, s>>>(X, colmax, x, N, nrhs, add ? 1 : 0);
+  k_accumulate<R><<<g, 256, 0, s>>>(X, colmax, x, N, nrhs, add ? 1 : 0, pmap);
+}
+
+// Per pole: max over masked rows and all RHS of |colmax * X| (the correction
+// just added) and of |x| (the refined solution), as double bits.
+template <typename R>
+__global__ void k_progress(const cx<R> *__restrict__ X, const double *__restrict__ colmax,
+                           const c128 *__restrict__ x, const uint8_t *__restrict__ mask, double *num,
+                           double *den, int64_t N, int nrhs, const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
+  const cx<R> *Xp = X + p * N * nrhs;
+  const c128 *xp = x + p * N * nrhs;
+  double a = 0.0, b = 0.0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < N * nrhs;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    if (!mask[e / nrhs]) continue;
+    const double c = colmax ? colmax[p * nrhs + e % nrhs] : 1.0;
+    const cx<R> d = Xp[e];
+    const c128 v = xp[e];
+    a = fmax(a, c * fmax(fabs(double(d.x)), fabs(double(d.y))));
+    b = fmax(b, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (a > 0) atomicMax((unsigned long long *)&num[p], (unsigned long long)__double_as_longlong(a));
+    if (b > 0) atomicMax((unsigned long long *)&den[p], (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+template <typename R>
+void launch_progress(const cx<R> *X, const double *colmax, const c128 *x, const uint8_t *mask, double *num,
+                     double *den, int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s) {
+  dim3 g((unsigned)std::min<int64_t>(div_up(N * nrhs, 256), 1024), np);
+  tem::count_launch();
+  k_progress<R><<<g, 256, 0, s>>>(X, colmax, x, mask, num, den, N, nrhs, pmap);
 }
 
 // r = b - (K - xi_p M) x for every pole; one warp per row, lanes over RHS.
@@ -106,8 +151,8 @@ __global__ void k_residual(const int64_t *__restrict__ rp, const int32_t *__rest
                            const double *__restrict__ kv, const double *__restrict__ mv,
                            const double2 *__restrict__ xi, const c128 *__restrict__ b,
                            int64_t bstride, const c128 *__restrict__ x, c128 *__restrict__ r,
-                           int64_t N, int nrhs) {
-  const int p = blockIdx.y;
+                           int64_t N, int nrhs, const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
   const int lane = threadIdx.x & 31;
   const int64_t row = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= N) return;
@@ -128,10 +173,10 @@ __global__ void k_residual(const int64_t *__restrict__ rp, const int32_t *__rest
 
 void launch_residual(const int64_t *rp, const int32_t *ci, const double *kv, const double *mv,
                      const double2 *xi, const c128 *b, int64_t bstride, const c128 *x, c128 *r,
-                     int m, int64_t N, int nrhs, cudaStream_t s) {
-  dim3 g(div_up(N, 8), m);
+                     int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s) {
+  dim3 g(div_up(N, 8), np);
   tem::count_launch();
-  k_residual<<<g, 256, 0, s>>>(rp, ci, kv, mv, xi, b, bstride, x, r, N, nrhs);
+  k_residual<<<g, 256, 0, s>>>(rp, ci, kv, mv, xi, b, bstride, x, r, N, nrhs, pmap);
 }
 
 __global__ void k_real_to_c128(const double *__restrict__ f, c128 *__restrict__ b, int64_t cnt) {
@@ -444,13 +489,15 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s) {
   k_lsqr_scalars<<<1, 32, 0, s>>>(sc, which);
 }
 
-template void launch_rhs_to_work<float>(const c128 *, int64_t, c64 *, double *, int, int64_t, int, bool,
-                                        cudaStream_t);
-template void launch_rhs_to_work<double>(const c128 *, int64_t, c128 *, double *, int, int64_t, int, bool,
-                                         cudaStream_t);
-template void launch_accumulate<float>(const c64 *, const double *, c128 *, int, int64_t, int, bool,
-                                       cudaStream_t);
-template void launch_accumulate<double>(const c128 *, const double *, c128 *, int, int64_t, int, bool,
-                                        cudaStream_t);
+template void launch_rhs_to_work<float>(const c128 *, int64_t, c64 *, double *, int, const int *, int64_t, int,
+                                        bool, cudaStream_t);
+template void launch_rhs_to_work<double>(const c128 *, int64_t, c128 *, double *, int, const int *, int64_t,
+                                         int, bool, cudaStream_t);
+template void launch_accumulate<float>(const c64 *, const double *, c128 *, int, const int *, int64_t, int,
+                                       bool, cudaStream_t);
+template void launch_accumulate<double>(const c128 *, const double *, c128 *, int, const int *, int64_t, int,
+                                        bool, cudaStream_t);
+template void launch_progress<float>(const c64 *, const double *, const c128 *, const uint8_t *, double *,
+                                     double *, int, const int *, int64_t, int, cudaStream_t);
 
 }  // namespace tem

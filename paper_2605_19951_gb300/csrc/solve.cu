@@ -20,6 +20,8 @@
 // kernels only touch rows / columns inside their super-block, and the rest
 // of the pivot-block work of a super-block is one split-K product
 // (k_fwd_sb: y_J -= L[J, 0:J0] x; k_bwd_sb: w_J -= L[J1:k, J]^T x).
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -53,9 +55,10 @@ __global__ void __launch_bounds__(256) k_fwd_l11(const cx<R> *__restrict__ L, in
                                                  const FrontDev *__restrict__ F,
                                                  const int32_t *__restrict__ lev, int step,
                                                  cx<R> *__restrict__ Y, cx<R> *__restrict__ X,
-                                                 int64_t vstride, int nrhs, int nchunk) {
+                                                 int64_t vstride, int nrhs, int nchunk,
+                                                 const int *__restrict__ pmap) {
   const FrontDev f = F[lev[blockIdx.y]];
-  const int p = blockIdx.z / nchunk, ch = blockIdx.z % nchunk;
+  const int p = pole_of(blockIdx.z / nchunk, pmap), ch = blockIdx.z % nchunk;
   const int j0 = step * NB;
   if (j0 >= f.k) return;
   const int nb = min(NB, f.k - j0);
@@ -105,11 +108,12 @@ __global__ void __launch_bounds__(256) k_fwd_l21(const cx<R> *__restrict__ L, in
                                                  const int2 *__restrict__ tasks,
                                                  const int32_t *__restrict__ rows,
                                                  cx<R> *__restrict__ Y, const cx<R> *__restrict__ X,
-                                                 int64_t vstride, int nrhs, int nchunk) {
+                                                 int64_t vstride, int nrhs, int nchunk,
+                                                 const int *__restrict__ pmap) {
   constexpr int RW = BM / 8;                      // rows per warp
   const int2 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
-  const int p = blockIdx.y / nchunk, ch = blockIdx.y % nchunk;
+  const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
   const int64_t n = f.n;
   const int b = f.n - f.k;
   const int i0 = t.y * BM;                        // first update row of the tile
@@ -158,11 +162,12 @@ __global__ void __launch_bounds__(256) k_bwd_l21(const cx<R> *__restrict__ L, in
                                                  const int2 *__restrict__ tasks,
                                                  const int32_t *__restrict__ rows,
                                                  cx<R> *__restrict__ Y, const cx<R> *__restrict__ X,
-                                                 int64_t vstride, int nrhs, int nchunk) {
+                                                 int64_t vstride, int nrhs, int nchunk,
+                                                 const int *__restrict__ pmap) {
   constexpr int CW = BN / 8;                      // columns per warp
   const int2 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
-  const int p = blockIdx.y / nchunk, ch = blockIdx.y % nchunk;
+  const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
   const int64_t n = f.n;
   const int b = f.n - f.k;
   const int cb = t.y * BN;                        // first pivot column of the tile
@@ -211,9 +216,10 @@ __global__ void __launch_bounds__(256) k_bwd_l11(const cx<R> *__restrict__ L, in
                                                  const FrontDev *__restrict__ F,
                                                  const int32_t *__restrict__ lev, int step,
                                                  cx<R> *__restrict__ Y, cx<R> *__restrict__ X,
-                                                 int64_t vstride, int nrhs, int nchunk) {
+                                                 int64_t vstride, int nrhs, int nchunk,
+                                                 const int *__restrict__ pmap) {
   const FrontDev f = F[lev[blockIdx.y]];
-  const int p = blockIdx.z / nchunk, ch = blockIdx.z % nchunk;
+  const int p = pole_of(blockIdx.z / nchunk, pmap), ch = blockIdx.z % nchunk;
   const int j0 = step * NB;
   if (j0 >= f.k) return;
   const int nb = min(NB, f.k - j0);
@@ -263,11 +269,12 @@ template <typename R, int BM, int KC>
 __global__ void __launch_bounds__(256) k_fwd_sb(const cx<R> *__restrict__ L, int64_t lstride,
                                                 const FrontDev *__restrict__ F, const int4 *__restrict__ tasks,
                                                 int sb, cx<R> *__restrict__ Y, const cx<R> *__restrict__ X,
-                                                int64_t vstride, int nrhs, int nchunk) {
+                                                int64_t vstride, int nrhs, int nchunk,
+                                                 const int *__restrict__ pmap) {
   constexpr int RW = BM / 8;
   const int4 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
-  const int p = blockIdx.y / nchunk, ch = blockIdx.y % nchunk;
+  const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
   const int64_t n = f.n;
   const int rlo = sb * kSB, rhi = min(f.k, rlo + kSB);
   const int i0 = rlo + t.y * BM;
@@ -312,11 +319,12 @@ template <typename R, int BN, int KC>
 __global__ void __launch_bounds__(256) k_bwd_sb(const cx<R> *__restrict__ L, int64_t lstride,
                                                 const FrontDev *__restrict__ F, const int4 *__restrict__ tasks,
                                                 int sb, cx<R> *__restrict__ Y, const cx<R> *__restrict__ X,
-                                                int64_t vstride, int nrhs, int nchunk) {
+                                                int64_t vstride, int nrhs, int nchunk,
+                                                 const int *__restrict__ pmap) {
   constexpr int CW = BN / 8;
   const int4 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
-  const int p = blockIdx.y / nchunk, ch = blockIdx.y % nchunk;
+  const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
   const int64_t n = f.n;
   const int clo = sb * kSB, chi = min(f.k, clo + kSB);
   const int cb = clo + t.y * BN;
@@ -364,27 +372,35 @@ void SolvePlan<R>::forward_level(const LevelDev &lv, cudaStream_t s) {
   for (int step = 0; step < (int)lv.steps.size(); step++) {
     const int sb = step / per_sb;
     if (step % per_sb == 0 && sb > 0 && lv.sb[sb].n_fwd > 0) {
-      dim3 g(lv.sb[sb].n_fwd, m * nchunk);
+      dim3 g(lv.sb[sb].n_fwd, np * nchunk);
       if (g_prof) g_prof->begin(KC_FWD_SB, s);
       tem::count_launch();
       k_fwd_sb<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].fwd, sb, Y, X,
-                                                                         vstride, nrhs, nchunk);
+                                                                         vstride, nrhs, nchunk, pmap);
       if (g_prof) g_prof->end(KC_FWD_SB, s);
     }
     const StepDims &sd = lv.steps[step];
-    dim3 g(sd.fwd_tiles, sd.nfronts, m * nchunk);
+    dim3 g(sd.fwd_tiles, sd.nfronts, np * nchunk);
     if (g_prof) g_prof->begin(KC_FWD, s);
     tem::count_launch();
     k_fwd_l11<R, kNB, SolveTile<R>::RT><<<g, 256, 0, s>>>(L, lstride, Linv, istride, F, lv.fronts, step, Y, X,
-                                                           vstride, nrhs, nchunk);
+                                                           vstride, nrhs, nchunk, pmap);
     if (g_prof) g_prof->end(KC_FWD, s);
   }
+  if constexpr (std::is_same<R, float>::value) {
+    if (use_tc && lv.n_f21tc > 0) {
+      if (g_prof) g_prof->begin(KC_FWD21, s);
+      launch_fwd_l21_tc(*this, lv, status, s);
+      if (g_prof) g_prof->end(KC_FWD21, s);
+      return;
+    }
+  }
   if (lv.n_f21 > 0) {
-    dim3 g(lv.n_f21, m * nchunk);
+    dim3 g(lv.n_f21, np * nchunk);
     if (g_prof) g_prof->begin(KC_FWD21, s);
     tem::count_launch();
     k_fwd_l21<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.f21_tasks, rows, Y, X,
-                                                                        vstride, nrhs, nchunk);
+                                                                        vstride, nrhs, nchunk, pmap);
     if (g_prof) g_prof->end(KC_FWD21, s);
   }
 }
@@ -394,30 +410,39 @@ void SolvePlan<R>::backward_level(const LevelDev &lv, cudaStream_t s) {
   if (g_prof) g_prof->cur_level = lv.h;
   const int nchunk = (nrhs + 31) / 32;
   const int per_sb = kSB / kNB;
-  if (lv.n_b21 > 0) {
-    dim3 g(lv.n_b21, m * nchunk);
+  bool done21 = false;
+  if constexpr (std::is_same<R, float>::value) {
+    if (use_tc && lv.n_b21tc > 0) {
+      if (g_prof) g_prof->begin(KC_BWD_UPD, s);
+      launch_bwd_l21_tc(*this, lv, status, s);
+      if (g_prof) g_prof->end(KC_BWD_UPD, s);
+      done21 = true;
+    }
+  }
+  if (!done21 && lv.n_b21 > 0) {
+    dim3 g(lv.n_b21, np * nchunk);
     if (g_prof) g_prof->begin(KC_BWD_UPD, s);
     tem::count_launch();
     k_bwd_l21<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.b21_tasks, rows, Y, X,
-                                                                        vstride, nrhs, nchunk);
+                                                                        vstride, nrhs, nchunk, pmap);
     if (g_prof) g_prof->end(KC_BWD_UPD, s);
   }
   for (int step = (int)lv.steps.size() - 1; step >= 0; step--) {
     const int sb = step / per_sb;
     if ((step == (int)lv.steps.size() - 1 || step % per_sb == per_sb - 1) && lv.sb[sb].n_bwd > 0) {
-      dim3 g(lv.sb[sb].n_bwd, m * nchunk);
+      dim3 g(lv.sb[sb].n_bwd, np * nchunk);
       if (g_prof) g_prof->begin(KC_BWD_SB, s);
       tem::count_launch();
       k_bwd_sb<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].bwd, sb, Y, X,
-                                                                         vstride, nrhs, nchunk);
+                                                                         vstride, nrhs, nchunk, pmap);
       if (g_prof) g_prof->end(KC_BWD_SB, s);
     }
     const StepDims &sd = lv.steps[step];
-    dim3 g(sd.bwd_tiles, sd.nfronts, m * nchunk);
+    dim3 g(sd.bwd_tiles, sd.nfronts, np * nchunk);
     if (g_prof) g_prof->begin(KC_BWD, s);
     tem::count_launch();
     k_bwd_l11<R, kNB, SolveTile<R>::CT><<<g, 256, 0, s>>>(L, lstride, Linv, istride, F, lv.fronts, step, Y, X,
-                                                           vstride, nrhs, nchunk);
+                                                           vstride, nrhs, nchunk, pmap);
     if (g_prof) g_prof->end(KC_BWD, s);
   }
 }

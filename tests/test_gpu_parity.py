@@ -221,7 +221,7 @@ def test_errors_are_statuses(c1):
             mdl.jvp(_cuda(c1.v))
         assert e.value.code == -6                      # TEM_ERR_STATE
         with pytest.raises(tem.TemError) as e:
-            tem.tem_set_refine(mdl.ctx, 99, 3e-5)
+            tem.tem_set_refine(mdl.ctx, 99, 1e-4, 0.0)
         assert e.value.code == -1
     finally:
         mdl.close()
