@@ -80,6 +80,8 @@ typedef struct tem_stats {
   int64_t n_solve_launch;/* kernel launches of one solve (forward + backward sweep) */
   int64_t pole_solves;   /* poles x (forward + backward sweep) issued so far */
   int64_t solve_calls;   /* multi-pole solves issued so far (each with its refinement) */
+  int32_t tc_ctas_per_sm; /* resident CTAs per SM of the tensor-core product kernel (0 before its first launch) */
+  int32_t reserved_;
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or

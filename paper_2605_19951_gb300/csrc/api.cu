@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/tem.h"
@@ -94,9 +95,18 @@ struct tem_ctx {
   int2 *f21 = nullptr, *b21 = nullptr;
   std::vector<int4> sbf_h, sbb_h;         // task lists of the super-block products
   int4 *sbf = nullptr, *sbb = nullptr;
-  std::vector<int2> f21tc_h, b21tc_h;     // task lists of the tensor-core L21 products
-  int2 *f21tc = nullptr, *b21tc = nullptr;
-  bool use_tc = true;                     // FP32 mode: L21 products on tcgen05
+  std::vector<TcTask> prod_h;             // FP32: front-product tasks (all levels and modes)
+  TcTask *prod = nullptr;
+  std::vector<SimtTask> prod_simt_h;      // the same tiles for the SIMT products
+  SimtTask *prod_simt = nullptr;
+  void *tmaps = nullptr;                  // FP32: tensor maps of the factor blocks
+  void *vmaps = nullptr;                  // FP32: tensor maps of the solve vectors
+  std::vector<InvTask> inv_h;             // FP32: pivot-block inversion tasks
+  InvTask *inv = nullptr;
+  std::vector<int2> invdiag_h;
+  int2 *invdiag = nullptr;
+  int64_t yscr_stride = 0;                // inversion scratch per pole
+  bool use_tc = true;                     // FP32 mode: front products on tcgen05
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -125,6 +135,7 @@ struct tem_ctx {
 
   // numeric
   void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr, *linv = nullptr;
+  void *dinv = nullptr, *yscr = nullptr;   // FP32: inverse pivots, inversion scratch
   DevStatus *status = nullptr;
   c128 *g = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *fb = nullptr;
   double *colmax = nullptr;
@@ -212,6 +223,103 @@ struct ProfScope {
   ~ProfScope() { g_prof = nullptr; }
 };
 
+// FP32 task lists of one level: the four front products of the solves (64-row
+// / 64-column tiles; kernels.h gives each mode's operands) and the merge
+// stages of the pivot-block inversion.  List offsets are stored in the
+// LevelDev pointers until the lists are uploaded.
+void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
+  const auto &S = c->sym;
+  for (int mode = 0; mode < PM_COUNT; mode++) {
+    const size_t beg = c->prod_h.size();
+    for (int32_t fi : L.fronts) {
+      const Front &F = S.fronts[fi];
+      const int k = F.k, b = F.n - F.k;
+      if (k <= 0) continue;
+      // tile with A origin (row x, column y) of the front block
+      auto push = [&](int row, int col, int kdim, int mrows, int bbase, int obase, int mfirst, int kfirst) {
+        TcTask t;
+        t.map = 4 * fi + mode;
+        t.x0 = 2 * row;
+        t.y0 = col;
+        t.kdim = kdim;
+        t.mrows = mrows;
+        t.bbase = bbase;
+        t.obase = obase;
+        t.mfirst = int16_t(mfirst);
+        t.kfirst = int16_t(kfirst);
+        c->prod_h.push_back(t);
+        SimtTask u;
+        u.aoff = F.lofs + int64_t(col) * F.ld + row;
+        u.lda = F.ld;
+        u.kdim = kdim;
+        u.mrows = mrows;
+        u.bbase = bbase;
+        u.obase = obase;
+        u.mfirst = int16_t(mfirst);
+        u.kfirst = int16_t(kfirst);
+        c->prod_simt_h.push_back(u);
+      };
+      const int r0 = k & ~1;   // even origin of the update rows (row k - 1 is padding when k is odd)
+      if (mode == PM_TRI_F)
+        for (int i0 = 0; i0 < k; i0 += 64)
+          push(i0, 0, std::min(k, i0 + 64), std::min(64, k - i0), F.c0, F.c0 + i0, 0, 0);
+      else if (mode == PM_FWD21) {
+        if (b > 0)
+          for (int R = r0; R < F.n; R += 64)
+            push(R, 0, k, std::min(64, F.n - R), F.c0, (int)F.rows_off + R - k, std::max(0, k - R), 0);
+      } else if (mode == PM_BWD21)
+        for (int cb = 0; cb < k; cb += 64)
+          push(r0, cb, b == 0 ? 0 : F.n - r0, std::min(64, k - cb), (int)F.rows_off - (k - r0), F.c0 + cb, 0,
+               k - r0);
+      else
+        for (int cb = 0; cb < k; cb += 64)
+          push(cb, cb, k - cb, std::min(64, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
+    }
+    lv.n_prod[mode] = int(c->prod_h.size() - beg);
+    lv.prod[mode] = (const TcTask *)(uintptr_t)beg;
+    lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg;
+  }
+  // inversion: 32-blocks, then pairwise merges of blocks of 32 * 2^stage
+  const size_t dbeg = c->invdiag_h.size();
+  int kmax = 0;
+  for (int32_t fi : L.fronts) {
+    const Front &F = S.fronts[fi];
+    kmax = std::max(kmax, F.k);
+    for (int J = 0; J * kNB < F.k; J++) c->invdiag_h.push_back(make_int2(fi, J));
+  }
+  lv.n_inv_diag = int(c->invdiag_h.size() - dbeg);
+  lv.inv_diag = (const int2 *)(uintptr_t)dbeg;
+  lv.inv.clear();
+  for (int sz = kNB; sz < kmax; sz *= 2) {
+    LevelDev::InvStage st;
+    const size_t beg = c->inv_h.size();
+    int64_t ybase = 0;
+    for (int32_t fi : L.fronts) {
+      const Front &F = S.fronts[fi];
+      for (int a0 = 0; a0 + sz < F.k; a0 += 2 * sz) {
+        const int sc = std::min(sz, F.k - a0 - sz);
+        for (int ti = 0; ti * 64 < sc; ti++)
+          for (int tj = 0; tj * 64 < sz; tj++) {
+            InvTask t;
+            t.front = fi;
+            t.a0 = a0;
+            t.s = sz;
+            t.sc = sc;
+            t.ti = ti;
+            t.tj = tj;
+            t.ybase = ybase;
+            c->inv_h.push_back(t);
+          }
+        ybase += int64_t(sc) * sz;
+      }
+    }
+    st.n = int(c->inv_h.size() - beg);
+    st.tasks = (const InvTask *)(uintptr_t)beg;
+    c->yscr_stride = std::max(c->yscr_stride, ybase);
+    lv.inv.push_back(st);
+  }
+}
+
 // Grid dimensions of every pivot step (depend on the precision's tile sizes).
 template <typename R>
 void build_steps(tem_ctx *c) {
@@ -221,8 +329,11 @@ void build_steps(tem_ctx *c) {
   c->b21_h.clear();
   c->sbf_h.clear();
   c->sbb_h.clear();
-  c->f21tc_h.clear();
-  c->b21tc_h.clear();
+  c->prod_h.clear();
+  c->prod_simt_h.clear();
+  c->inv_h.clear();
+  c->invdiag_h.clear();
+  c->yscr_stride = 0;
   c->max_level_fronts = 0;
   int64_t off = 0;
   for (const Level &L : S.levels) {
@@ -255,19 +366,7 @@ void build_steps(tem_ctx *c) {
     }
     lv.n_f21 = int(c->f21_h.size() - f21_beg);
     lv.n_b21 = int(c->b21_h.size() - b21_beg);
-    const size_t f21tc_beg = c->f21tc_h.size(), b21tc_beg = c->b21tc_h.size();
-    for (int32_t fi : L.fronts) {
-      const Front &F = S.fronts[fi];
-      const int b = F.n - F.k;
-      if (F.k <= 0) continue;
-      if (b > 0)
-        for (int t = 0; t < div_up(b, 64); t++) c->f21tc_h.push_back(make_int2(fi, t));
-      for (int t = 0; t < div_up(F.k, 64); t++) c->b21tc_h.push_back(make_int2(fi, t));
-    }
-    lv.n_f21tc = int(c->f21tc_h.size() - f21tc_beg);
-    lv.n_b21tc = int(c->b21tc_h.size() - b21tc_beg);
-    lv.f21tc_tasks = (const int2 *)(uintptr_t)f21tc_beg;
-    lv.b21tc_tasks = (const int2 *)(uintptr_t)b21tc_beg;
+    if constexpr (std::is_same<R, float>::value) build_fp32_tasks(c, L, lv);
     lv.f21_tasks = (const int2 *)(uintptr_t)f21_beg;   // offsets until the lists are on the device
     lv.b21_tasks = (const int2 *)(uintptr_t)b21_beg;
     // super-block products: forward rows of block J against pivots [0, J0);
@@ -339,6 +438,10 @@ FactorPlan<R> factor_plan(tem_ctx *c) {
   P.linv = (cx<R> *)c->linv;
   P.istride = c->inv_blocks * kNB * kNB;
   P.status = c->status;
+  P.dinv = (cx<R> *)c->dinv;
+  P.N = c->mesh.N;
+  P.yscr = (cx<R> *)c->yscr;
+  P.yscr_stride = c->yscr_stride;
   return P;
 }
 
@@ -356,6 +459,10 @@ SolvePlan<R> solve_plan(tem_ctx *c) {
   P.Y = (cx<R> *)c->Y;
   P.X = (cx<R> *)c->X;
   P.vstride = c->mesh.N * c->n_tx;
+  P.dinv = (const cx<R> *)c->dinv;
+  P.tmaps = c->tmaps;
+  P.vmaps = c->vmaps;
+  P.N = c->mesh.N;
   return P;
 }
 
@@ -436,11 +543,27 @@ int ensure_numeric(tem_ctx *c) {
   c->Y = p;
   TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
   c->X = p;
+  // the products read whole 16-row chunks of these (finite values past a block)
+  CK(cudaMemset(c->Y, 0, size_t(m) * N * nx * es));
+  CK(cudaMemset(c->X, 0, size_t(m) * N * nx * es));
   TRY(dalloc(c, &c->g, size_t(m) * N * nx));
   TRY(dalloc(c, &c->b, size_t(m) * N * nx));
   TRY(dalloc(c, &c->x, size_t(m) * N * nx));
   if (c->precision != TEM_FP64) {
     TRY(dalloc(c, &c->r, size_t(m) * N * nx));
+    TRY(dalloc(c, (c64 **)&c->dinv, size_t(m) * N));
+    TRY(dalloc(c, (c64 **)&c->yscr, size_t(m) * std::max<int64_t>(1, c->yscr_stride)));
+    std::vector<FrontGeom> geo(c->sym.fronts.size());
+    for (size_t i = 0; i < geo.size(); i++) {
+      const Front &F = c->sym.fronts[i];
+      geo[i] = FrontGeom{F.lofs, F.n, F.k, F.ld};
+    }
+    const std::string e = build_tensor_maps(geo, (const c64 *)c->L, c->sym.ltotal, m, &c->tmaps);
+    if (!e.empty()) return fail(c, TEM_ERR_CUDA, e);
+    c->allocs.push_back(c->tmaps);
+    const std::string e2 = build_vector_maps((const c64 *)c->Y, (const c64 *)c->X, N, nx, m, &c->vmaps);
+    if (!e2.empty()) return fail(c, TEM_ERR_CUDA, e2);
+    if (c->vmaps) c->allocs.push_back(c->vmaps);
     TRY(dalloc(c, &c->mval_fact, size_t(m) * c->mesh.kval.size()));
     std::vector<double> tf(c->mesh.nt);
     for (int64_t t = 0; t < c->mesh.nt; t++) tf[t] = 1.0 / (kMu0 * std::pow(c->mesh.vol[t], 2.0 / 3.0));
@@ -528,7 +651,7 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   int64_t inv = 0;
   for (size_t i = 0; i < S.fronts.size(); i++) {
     const Front &F = S.fronts[i];
-    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, inv, F.n, F.k, F.c0, F.parent};
+    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, inv, F.n, F.k, F.c0, F.parent, F.ld, 0};
     inv += div_up(F.k, kNB);
   }
   c->inv_blocks = inv;
@@ -554,13 +677,19 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->b21, c->b21_h));
   TRY(upload(c, &c->sbf, c->sbf_h));
   TRY(upload(c, &c->sbb, c->sbb_h));
-  TRY(upload(c, &c->f21tc, c->f21tc_h));
-  TRY(upload(c, &c->b21tc, c->b21tc_h));
+  TRY(upload(c, &c->prod, c->prod_h));
+  TRY(upload(c, &c->prod_simt, c->prod_simt_h));
+  TRY(upload(c, &c->inv, c->inv_h));
+  TRY(upload(c, &c->invdiag, c->invdiag_h));
   for (LevelDev &lv : c->levels) {
     lv.f21_tasks = c->f21 + (uintptr_t)lv.f21_tasks;
     lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
-    lv.f21tc_tasks = c->f21tc + (uintptr_t)lv.f21tc_tasks;
-    lv.b21tc_tasks = c->b21tc + (uintptr_t)lv.b21tc_tasks;
+    for (int mode = 0; mode < PM_COUNT; mode++) {
+      lv.prod[mode] = c->prod + (uintptr_t)lv.prod[mode];
+      lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
+    }
+    lv.inv_diag = c->invdiag + (uintptr_t)lv.inv_diag;
+    for (auto &st : lv.inv) st.tasks = c->inv + (uintptr_t)st.tasks;
     for (auto &sb : lv.sb) {
       sb.fwd = c->sbf + (uintptr_t)sb.fwd;
       sb.bwd = c->sbb + (uintptr_t)sb.bwd;
@@ -652,7 +781,10 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
     for (int h = 0; h < H; h++) P.level(h, c->levels[h], s);
   } else {
     FactorPlan<float> P = factor_plan<float>(c);
-    for (int h = 0; h < H; h++) P.level(h, c->levels[h], s);
+    for (int h = 0; h < H; h++) {
+      P.level(h, c->levels[h], s);
+      P.invert_level(c->levels[h], s);
+    }
   }
   CK(cudaMemcpyAsync(&c->status_h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   TRY(sync(c, "tem_factor"));
@@ -834,10 +966,15 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   o->solve_calls = c->solve_calls;
   int64_t nl = 0;
   for (const LevelDev &lv : c->levels) {
-    nl += 2 * (int64_t)lv.steps.size() + (lv.n_f21 > 0 ? 1 : 0) + (lv.n_b21 > 0 ? 1 : 0);
-    for (const auto &sb : lv.sb) nl += (sb.n_fwd > 0 ? 1 : 0) + (sb.n_bwd > 0 ? 1 : 0);
+    if (c->precision == TEM_FP64) {
+      nl += 2 * (int64_t)lv.steps.size() + (lv.n_f21 > 0 ? 1 : 0) + (lv.n_b21 > 0 ? 1 : 0);
+      for (const auto &sb : lv.sb) nl += (sb.n_fwd > 0 ? 1 : 0) + (sb.n_bwd > 0 ? 1 : 0);
+    } else {
+      for (int mode = 0; mode < PM_COUNT; mode++) nl += lv.n_prod[mode] > 0 ? 1 : 0;
+    }
   }
   o->n_solve_launch = nl;
+  o->tc_ctas_per_sm = tc_ctas_per_sm();
   return TEM_OK;
 }
 

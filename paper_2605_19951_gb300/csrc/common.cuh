@@ -71,12 +71,14 @@ __device__ __forceinline__ void atomic_add_cx(cx<R> *p, cx<R> v) {
 
 // Front metadata as seen by the kernels.
 struct FrontDev {
-  int64_t lofs;    // factor block offset (n x k, column-major, ld n)
+  int64_t lofs;    // factor block offset (n x k, column-major, column stride ld)
   int64_t uofs;    // update block offset in the arena (b x b, ld b), -1 if b == 0
   int64_t rows_off;
   int64_t rel_off;
   int64_t inv_off;  // first NB x NB diagonal-block inverse of this front (in blocks)
   int32_t n, k, c0, parent;
+  int32_t ld;       // column stride: n rounded up to even (16-byte aligned columns)
+  int32_t pad_;
 };
 
 // Device status words of one context.

@@ -2,7 +2,8 @@
 // (Algorithm 1: form A_i, factor), all poles batched in the grid's z dimension.
 //
 // Storage (per pole, pole stride lstride / ustride elements):
-//   factor store: front f owns an n x k column-major block at lofs (ld n):
+//   factor store: front f owns an n x k column-major block at lofs (column
+//     stride ld = n rounded up to even, so columns start on 16-byte boundaries):
 //     rows 0..k-1 = L11 (unit lower, D on the diagonal), rows k..n-1 = L21.
 //   update arena: front f owns a b x b column-major block at uofs (ld b)
 //     holding its Schur complement (lower triangle) until the parent has
@@ -106,7 +107,7 @@ __global__ void k_extend_add(cx<R> *__restrict__ L, int64_t lstride, cx<R> *__re
   const int32_t *rl = rel + C.rel_off;
   const int32_t rj = rl[j];
   if (rj < Pf.k) {
-    cx<R> *dst = L + p * lstride + Pf.lofs + int64_t(rj) * Pf.n;
+    cx<R> *dst = L + p * lstride + Pf.lofs + int64_t(rj) * Pf.ld;
     for (int32_t i = j + threadIdx.x; i < bc; i += blockDim.x) {
       cx<R> v = uc[i];
       int32_t ri = rl[i];
@@ -151,14 +152,14 @@ __global__ void __launch_bounds__(RT) k_panel(cx<R> *__restrict__ L, int64_t lst
   const int tile = blockIdx.x;
   if (tile > 0 && rbeg + tile * RT >= f.n) return;
   cx<R> *A = L + p * lstride + f.lofs;
-  const int64_t n = f.n;
+  const int64_t n = f.n, ld = f.ld;
   __shared__ cx<R> Dg[NB][NB + 1];
   __shared__ cx<R> w[NB];
   __shared__ cx<R> inv[NB];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < NB * NB; idx += RT) {
     int r = idx % NB, c = idx / NB;
-    if (r < nb && c < nb && r >= c) Dg[r][c] = A[(j0 + c) * n + j0 + r];
+    if (r < nb && c < nb && r >= c) Dg[r][c] = A[(j0 + c) * ld + j0 + r];
   }
   __syncthreads();
   for (int c = 0; c < nb; c++) {
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(RT) k_panel(cx<R> *__restrict__ L, int64_t lst
     cx<R> wr[NB];
 #pragma unroll
     for (int c = 0; c < NB; c++)
-      if (c < nb) wr[c] = A[(j0 + c) * n + r];
+      if (c < nb) wr[c] = A[(j0 + c) * ld + r];
 #pragma unroll
     for (int c = 0; c < NB; c++) {
       if (c < nb) {
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(RT) k_panel(cx<R> *__restrict__ L, int64_t lst
     }
 #pragma unroll
     for (int c = 0; c < NB; c++)
-      if (c < nb) A[(j0 + c) * n + r] = wr[c] * inv[c];
+      if (c < nb) A[(j0 + c) * ld + r] = wr[c] * inv[c];
   }
 }
 
@@ -251,14 +252,14 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
   const int j0 = step * NB;
   if (j0 >= f.k) return;
   const int nb = min(NB, f.k - j0);
-  const int64_t n = f.n;
+  const int64_t n = f.n, ld = f.ld;
   cx<R> *A = L + p * lstride + f.lofs;
   const int tid = threadIdx.x;
   if (blockIdx.x == 0) {
     const cx<R> *ds = dscr + (int64_t(fi) * gridDim.z + p) * NB * NB;
     for (int idx = tid; idx < NB * NB; idx += 256) {
       int r = idx % NB, c = idx / NB;
-      if (r < nb && c < nb && r >= c) A[(j0 + c) * n + j0 + r] = ds[c * NB + r];
+      if (r < nb && c < nb && r >= c) A[(j0 + c) * ld + j0 + r] = ds[c * NB + r];
     }
   }
   const int64_t pbeg = j0 + nb;
@@ -286,8 +287,8 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
     cx<R> a = mk<R>(R(0), R(0)), b = mk<R>(R(0), R(0));
     if (c < nb) {
       int64_t r = r0 + i, s = s0 + i;
-      if (r < n) a = A[(j0 + c) * n + r];
-      if (s < n) b = A[(j0 + c) * n + s] * Dd[c];
+      if (r < n) a = A[(j0 + c) * ld + r];
+      if (s < n) b = A[(j0 + c) * ld + s] * Dd[c];
     }
     As[c][i] = a;
     Bs[c][i] = b;
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
     const int64_t s = s0 + ty + 16 * j;
     if (s >= n) continue;
     // column s lives in the factor block (s < k) or in the update block
-    cx<R> *col = (s < k) ? (A + s * n) : (U + p * ustride + f.uofs + (s - k) * b);
+    cx<R> *col = (s < k) ? (A + s * ld) : (U + p * ustride + f.uofs + (s - k) * b);
     const int64_t roff = (s < k) ? 0 : k;
 #pragma unroll
     for (int i = 0; i < PT; i++) {

@@ -440,6 +440,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
     Front &F = s.fronts[q];
     F.k = (int32_t)nodes[i].piv.size();
     F.n = F.k + (int32_t)upd[i].size();
+    F.ld = F.n + (F.n & 1);   // even: every column starts on a 16-byte boundary
     F.c0 = node_c0[i];
     F.height = height[i];
     F.nchild = nodes[i].nchild;
@@ -447,7 +448,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
     F.rows_off = (int64_t)s.rows.size();
     s.rows.insert(s.rows.end(), upd[i].begin(), upd[i].end());
     F.lofs = lofs;
-    lofs += int64_t(F.n) * F.k;
+    lofs += int64_t(F.ld) * F.k;
     H = std::max(H, F.height);
     s.max_front = std::max(s.max_front, F.n);
     const int64_t b = F.n - F.k;
@@ -495,7 +496,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
     for (int32_t f : L.fronts) {
       const Front &F = s.fronts[f];
       L.lbeg = std::min(L.lbeg, F.lofs);
-      L.lend = std::max(L.lend, F.lofs + int64_t(F.n) * F.k);
+      L.lend = std::max(L.lend, F.lofs + int64_t(F.ld) * F.k);
       L.max_k = std::max(L.max_k, F.k);
     }
   }
@@ -571,7 +572,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
           if (it == urow + b || *it != r) return "internal: entry outside its front";
           loc = F.k + int32_t(it - urow);
         }
-        int64_t dst = F.lofs + int64_t(c - F.c0) * F.n + loc;
+        int64_t dst = F.lofs + int64_t(c - F.c0) * F.ld + loc;
         per_level[F.height].push_back({z, dst});
       }
     }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -52,6 +53,49 @@ struct StepDims {
   int bwd_tiles;
 };
 
+// One output tile of a front product of the FP32 solves (host-built, per
+// level and mode), tensor-core form.  A is read through the tensor map
+// `map` (3-D: floats along a column, columns, poles; zero outside the block)
+// at coordinates (x0, y0) + the chunk offset: column-major modes step the
+// column y, row-major modes the float x.  B row kk is bbase + kk
+// (contiguous) or rows[bbase + kk] (gathered); outputs are rows obase + m
+// (stores) or rows[obase + m] (atomic subtraction).  Tiles start at even
+// rows: output rows m < mfirst and inner indices kk < kfirst (B zero there)
+// are padding of a front with an odd number of pivots.
+struct TcTask {
+  int32_t map, x0, y0;
+  int32_t kdim;    // inner dimension (0: no product, the epilogue still runs)
+  int32_t mrows;   // rows of the 64-row tile inside the block
+  int32_t bbase;
+  int32_t obase;
+  int16_t mfirst, kfirst;
+};
+static_assert(sizeof(TcTask) == 32, "TcTask is loaded as two 16-byte vectors");
+
+// The same tile for the SIMT kernel: A element (m, kk) at aoff + kk * lda + m
+// (column-major modes) or aoff + m * lda + kk (row-major modes).
+struct SimtTask {
+  int64_t aoff;
+  int32_t lda, kdim, mrows, bbase, obase;
+  int16_t mfirst, kfirst;
+};
+
+// The four front products of the FP32 solves (explicit inverses T11 = L11^-1):
+//   TRI_F  X[c0+i]      = sum_c T11[i][c] Y[c0+c]              (store)
+//   FWD21  Y[rows_i]   -= sum_c L21[i][c] X[c0+c]              (atomic)
+//   BWD21  Y[c0+c]      = Dinv_c X[c0+c] - sum_i L21[i][c] X[rows_i]   (store)
+//   TRI_B  X[c0+c]      = sum_i T11[i][c] Y[c0+i]              (store)
+enum ProdMode { PM_TRI_F = 0, PM_FWD21 = 1, PM_BWD21 = 2, PM_TRI_B = 3, PM_COUNT = 4 };
+
+// One tile task of the in-place inversion of L11 (merge of two diagonal
+// blocks A = [a0, a0+s), C = [a0+s, a0+s+sc)): 64 x 64 tile (ti, tj) of the
+// sc x s block; Y scratch of the pair at ybase (column-major, ld sc).
+struct InvTask {
+  int32_t front, a0, s, sc;
+  int32_t ti, tj;
+  int64_t ybase;
+};
+
 struct LevelDev {
   const int32_t *fronts = nullptr;  // device list, sorted by k descending
   int nf = 0;
@@ -60,10 +104,6 @@ struct LevelDev {
   int n_f21 = 0;
   const int2 *b21_tasks = nullptr;  // (front, column tile) of the backward L21 product
   int n_b21 = 0;
-  const int2 *f21tc_tasks = nullptr;  // the same for the tensor-core kernels (64-row / 64-column tiles)
-  int n_f21tc = 0;
-  const int2 *b21tc_tasks = nullptr;
-  int n_b21tc = 0;
   int bwd_upd_tiles = 0;            // ceil(max k / 8)
   int64_t lbeg = 0, lend = 0, obeg = 0, oend = 0;
   int64_t ea_beg[2] = {0, 0}, ea_end[2] = {0, 0};
@@ -75,6 +115,18 @@ struct LevelDev {
     int n_bwd = 0;
   };
   std::vector<SuperBlock> sb;
+  // FP32 solves: front-product tasks per mode
+  const TcTask *prod[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
+  const SimtTask *prod_simt[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
+  int n_prod[PM_COUNT] = {0, 0, 0, 0};
+  // FP32 factorisation: inversion of L11, per merge stage (block size 32 * 2^stage)
+  struct InvStage {
+    const InvTask *tasks = nullptr;
+    int n = 0;
+  };
+  std::vector<InvStage> inv;
+  const int2 *inv_diag = nullptr;   // (front, 32-block) of every diagonal block
+  int n_inv_diag = 0;
 };
 
 template <typename R>
@@ -98,8 +150,19 @@ struct FactorPlan {
   cx<R> *linv = nullptr;            // [m][inv blocks][NB*NB] diagonal-block inverses (output)
   int64_t istride = 0;
   DevStatus *status = nullptr;
+  // FP32: L11 is replaced by its inverse after each level; D^-1 goes to dinv
+  cx<R> *dinv = nullptr;            // [m][N]
+  int64_t N = 0;
+  cx<R> *yscr = nullptr;            // inversion scratch [m][yscr_stride]
+  int64_t yscr_stride = 0;
   void level(int h, const LevelDev &lv, cudaStream_t s);
+  void invert_level(const LevelDev &lv, cudaStream_t s);
 };
+
+template <>
+void FactorPlan<float>::invert_level(const LevelDev &lv, cudaStream_t s);
+template <>
+void FactorPlan<double>::invert_level(const LevelDev &lv, cudaStream_t s);
 
 template <typename R>
 struct SolvePlan {
@@ -116,14 +179,29 @@ struct SolvePlan {
   int64_t vstride = 0;  // N * nrhs
   const int *pmap = nullptr;  // device list of the poles to solve (nullptr: all)
   int np = 0;                 // poles solved
-  bool use_tc = false;        // FP32: update-row products on the tensor cores
+  bool use_tc = false;        // FP32: front products on the tensor cores
+  const cx<R> *dinv = nullptr;  // FP32: [m][N] inverse pivots
+  const void *tmaps = nullptr;  // FP32: 4 tensor maps per front (one per product mode)
+  const void *vmaps = nullptr;  // FP32: tensor maps of Y and X (nullptr for an odd nrhs)
+  int64_t N = 0;
   DevStatus *status = nullptr;
   void forward_level(const LevelDev &lv, cudaStream_t s);
   void backward_level(const LevelDev &lv, cudaStream_t s);
 };
 
-void launch_fwd_l21_tc(const SolvePlan<float> &P, const LevelDev &lv, DevStatus *st, cudaStream_t s);
-void launch_bwd_l21_tc(const SolvePlan<float> &P, const LevelDev &lv, DevStatus *st, cudaStream_t s);
+// FP32 front products (solve_tc.cu): tensor cores (P.use_tc) or SIMT.
+void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s);
+// Resident CTAs per SM of the tensor-core product kernel (0 before its first launch).
+int tc_ctas_per_sm();
+// Tensor maps of every front's factor block (4 per front, index 4 f + mode)
+// in a new device array (*out, cudaFree by the caller); "" on success.
+struct FrontGeom {
+  int64_t lofs;
+  int32_t n, k, ld;
+};
+std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
+                              void **out);
+std::string build_vector_maps(const c64 *Y, const c64 *X, int64_t N, int nrhs, int m, void **out);
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s);
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
@@ -188,7 +266,8 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 
 // Kernel classes that can be timed individually with CUDA events.
 enum KernelClass {
-  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_COUNT
+  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT,
+  KC_COUNT
 };
 struct Profiler {
   bool on = false;

@@ -1,5 +1,8 @@
 // Multi-right-hand-side supernodal solves with the stored LDL^T factors,
 // A_i X = B for all poles at once (Algorithm 1: solve with the cached factors).
+// This file holds the FP64 path (substitution with the pivot blocks); the
+// FP32 path, whose pivot blocks hold their explicit inverses, runs four front
+// products per level pair (solve_tc.cu).
 //
 // Vectors are [pole][N][nrhs] in the elimination numbering, right-hand sides
 // contiguous.  The grid's z dimension runs over (pole, chunk of 32 RHS); a
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(256) k_fwd_l11(const cx<R> *__restrict__ L, in
   const int j0 = step * NB;
   if (j0 >= f.k) return;
   const int nb = min(NB, f.k - j0);
-  const int64_t n = f.n;
+  const int64_t n = f.ld;   // column stride
   const int rbeg = j0 + nb;                       // pivot rows below the block ...
   const int rend = min(f.k, (j0 / kSB + 1) * kSB);  // ... inside its super-block
   const int tile = blockIdx.x;
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(256) k_fwd_l21(const cx<R> *__restrict__ L, in
   const int2 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
   const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
-  const int64_t n = f.n;
+  const int64_t n = f.ld;   // column stride
   const int b = f.n - f.k;
   const int i0 = t.y * BM;                        // first update row of the tile
   const cx<R> *A = L + p * lstride + f.lofs + f.k;   // L21 rows start at row k
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(256) k_bwd_l21(const cx<R> *__restrict__ L, in
   const int2 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
   const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
-  const int64_t n = f.n;
+  const int64_t n = f.ld;   // column stride
   const int b = f.n - f.k;
   const int cb = t.y * BN;                        // first pivot column of the tile
   const cx<R> *A = L + p * lstride + f.lofs;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(256) k_bwd_l11(const cx<R> *__restrict__ L, in
   const int tile = blockIdx.x;
   const int cfirst = (j0 / kSB) * kSB;           // columns left of the block inside its super-block
   if (tile > 0 && cfirst + tile * CT >= j0) return;
-  const int64_t n = f.n;
+  const int64_t n = f.ld;   // column stride
   const cx<R> *A = L + p * lstride + f.lofs;
   const cx<R> *Iv = Linv + p * istride + (f.inv_off + step) * (NB * NB);
   cx<R> *Yp = Y + p * vstride;
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(256) k_fwd_sb(const cx<R> *__restrict__ L, int
   const int4 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
   const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
-  const int64_t n = f.n;
+  const int64_t n = f.ld;   // column stride
   const int rlo = sb * kSB, rhi = min(f.k, rlo + kSB);
   const int i0 = rlo + t.y * BM;
   const cx<R> *A = L + p * lstride + f.lofs;
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(256) k_bwd_sb(const cx<R> *__restrict__ L, int
   const int4 t = tasks[blockIdx.x];
   const FrontDev f = F[t.x];
   const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
-  const int64_t n = f.n;
+  const int64_t n = f.ld;   // column stride
   const int clo = sb * kSB, chi = min(f.k, clo + kSB);
   const int cb = clo + t.y * BN;
   const cx<R> *A = L + p * lstride + f.lofs;
@@ -367,83 +370,85 @@ __global__ void __launch_bounds__(256) k_bwd_sb(const cx<R> *__restrict__ L, int
 template <typename R>
 void SolvePlan<R>::forward_level(const LevelDev &lv, cudaStream_t s) {
   if (g_prof) g_prof->cur_level = lv.h;
-  const int nchunk = (nrhs + 31) / 32;
-  const int per_sb = kSB / kNB;
-  for (int step = 0; step < (int)lv.steps.size(); step++) {
-    const int sb = step / per_sb;
-    if (step % per_sb == 0 && sb > 0 && lv.sb[sb].n_fwd > 0) {
-      dim3 g(lv.sb[sb].n_fwd, np * nchunk);
-      if (g_prof) g_prof->begin(KC_FWD_SB, s);
-      tem::count_launch();
-      k_fwd_sb<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].fwd, sb, Y, X,
-                                                                         vstride, nrhs, nchunk, pmap);
-      if (g_prof) g_prof->end(KC_FWD_SB, s);
-    }
-    const StepDims &sd = lv.steps[step];
-    dim3 g(sd.fwd_tiles, sd.nfronts, np * nchunk);
-    if (g_prof) g_prof->begin(KC_FWD, s);
-    tem::count_launch();
-    k_fwd_l11<R, kNB, SolveTile<R>::RT><<<g, 256, 0, s>>>(L, lstride, Linv, istride, F, lv.fronts, step, Y, X,
-                                                           vstride, nrhs, nchunk, pmap);
-    if (g_prof) g_prof->end(KC_FWD, s);
-  }
   if constexpr (std::is_same<R, float>::value) {
-    if (use_tc && lv.n_f21tc > 0) {
-      if (g_prof) g_prof->begin(KC_FWD21, s);
-      launch_fwd_l21_tc(*this, lv, status, s);
-      if (g_prof) g_prof->end(KC_FWD21, s);
-      return;
-    }
-  }
-  if (lv.n_f21 > 0) {
-    dim3 g(lv.n_f21, np * nchunk);
+    // explicit pivot-block inverses: two products per level
+    if (g_prof) g_prof->begin(KC_FWD, s);
+    launch_prod(PM_TRI_F, *this, lv, s);
+    if (g_prof) g_prof->end(KC_FWD, s);
     if (g_prof) g_prof->begin(KC_FWD21, s);
-    tem::count_launch();
-    k_fwd_l21<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.f21_tasks, rows, Y, X,
-                                                                        vstride, nrhs, nchunk, pmap);
+    launch_prod(PM_FWD21, *this, lv, s);
     if (g_prof) g_prof->end(KC_FWD21, s);
+  } else {
+    const int nchunk = (nrhs + 31) / 32;
+    const int per_sb = kSB / kNB;
+    for (int step = 0; step < (int)lv.steps.size(); step++) {
+      const int sb = step / per_sb;
+      if (step % per_sb == 0 && sb > 0 && lv.sb[sb].n_fwd > 0) {
+        dim3 g(lv.sb[sb].n_fwd, np * nchunk);
+        if (g_prof) g_prof->begin(KC_FWD_SB, s);
+        tem::count_launch();
+        k_fwd_sb<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].fwd, sb, Y, X,
+                                                                           vstride, nrhs, nchunk, pmap);
+        if (g_prof) g_prof->end(KC_FWD_SB, s);
+      }
+      const StepDims &sd = lv.steps[step];
+      dim3 g(sd.fwd_tiles, sd.nfronts, np * nchunk);
+      if (g_prof) g_prof->begin(KC_FWD, s);
+      tem::count_launch();
+      k_fwd_l11<R, kNB, SolveTile<R>::RT><<<g, 256, 0, s>>>(L, lstride, Linv, istride, F, lv.fronts, step, Y, X,
+                                                             vstride, nrhs, nchunk, pmap);
+      if (g_prof) g_prof->end(KC_FWD, s);
+    }
+    if (lv.n_f21 > 0) {
+      dim3 g(lv.n_f21, np * nchunk);
+      if (g_prof) g_prof->begin(KC_FWD21, s);
+      tem::count_launch();
+      k_fwd_l21<R, SolveTile<R>::BM, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.f21_tasks, rows, Y,
+                                                                          X, vstride, nrhs, nchunk, pmap);
+      if (g_prof) g_prof->end(KC_FWD21, s);
+    }
   }
 }
 
 template <typename R>
 void SolvePlan<R>::backward_level(const LevelDev &lv, cudaStream_t s) {
   if (g_prof) g_prof->cur_level = lv.h;
-  const int nchunk = (nrhs + 31) / 32;
-  const int per_sb = kSB / kNB;
-  bool done21 = false;
   if constexpr (std::is_same<R, float>::value) {
-    if (use_tc && lv.n_b21tc > 0) {
-      if (g_prof) g_prof->begin(KC_BWD_UPD, s);
-      launch_bwd_l21_tc(*this, lv, status, s);
-      if (g_prof) g_prof->end(KC_BWD_UPD, s);
-      done21 = true;
-    }
-  }
-  if (!done21 && lv.n_b21 > 0) {
-    dim3 g(lv.n_b21, np * nchunk);
     if (g_prof) g_prof->begin(KC_BWD_UPD, s);
-    tem::count_launch();
-    k_bwd_l21<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.b21_tasks, rows, Y, X,
-                                                                        vstride, nrhs, nchunk, pmap);
+    launch_prod(PM_BWD21, *this, lv, s);
     if (g_prof) g_prof->end(KC_BWD_UPD, s);
-  }
-  for (int step = (int)lv.steps.size() - 1; step >= 0; step--) {
-    const int sb = step / per_sb;
-    if ((step == (int)lv.steps.size() - 1 || step % per_sb == per_sb - 1) && lv.sb[sb].n_bwd > 0) {
-      dim3 g(lv.sb[sb].n_bwd, np * nchunk);
-      if (g_prof) g_prof->begin(KC_BWD_SB, s);
-      tem::count_launch();
-      k_bwd_sb<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].bwd, sb, Y, X,
-                                                                         vstride, nrhs, nchunk, pmap);
-      if (g_prof) g_prof->end(KC_BWD_SB, s);
-    }
-    const StepDims &sd = lv.steps[step];
-    dim3 g(sd.bwd_tiles, sd.nfronts, np * nchunk);
     if (g_prof) g_prof->begin(KC_BWD, s);
-    tem::count_launch();
-    k_bwd_l11<R, kNB, SolveTile<R>::CT><<<g, 256, 0, s>>>(L, lstride, Linv, istride, F, lv.fronts, step, Y, X,
-                                                           vstride, nrhs, nchunk, pmap);
+    launch_prod(PM_TRI_B, *this, lv, s);
     if (g_prof) g_prof->end(KC_BWD, s);
+  } else {
+    const int nchunk = (nrhs + 31) / 32;
+    const int per_sb = kSB / kNB;
+    if (lv.n_b21 > 0) {
+      dim3 g(lv.n_b21, np * nchunk);
+      if (g_prof) g_prof->begin(KC_BWD_UPD, s);
+      tem::count_launch();
+      k_bwd_l21<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.b21_tasks, rows, Y,
+                                                                          X, vstride, nrhs, nchunk, pmap);
+      if (g_prof) g_prof->end(KC_BWD_UPD, s);
+    }
+    for (int step = (int)lv.steps.size() - 1; step >= 0; step--) {
+      const int sb = step / per_sb;
+      if ((step == (int)lv.steps.size() - 1 || step % per_sb == per_sb - 1) && lv.sb[sb].n_bwd > 0) {
+        dim3 g(lv.sb[sb].n_bwd, np * nchunk);
+        if (g_prof) g_prof->begin(KC_BWD_SB, s);
+        tem::count_launch();
+        k_bwd_sb<R, SolveTile<R>::BN, SolveTile<R>::KC><<<g, 256, 0, s>>>(L, lstride, F, lv.sb[sb].bwd, sb, Y, X,
+                                                                           vstride, nrhs, nchunk, pmap);
+        if (g_prof) g_prof->end(KC_BWD_SB, s);
+      }
+      const StepDims &sd = lv.steps[step];
+      dim3 g(sd.bwd_tiles, sd.nfronts, np * nchunk);
+      if (g_prof) g_prof->begin(KC_BWD, s);
+      tem::count_launch();
+      k_bwd_l11<R, kNB, SolveTile<R>::CT><<<g, 256, 0, s>>>(L, lstride, Linv, istride, F, lv.fronts, step, Y, X,
+                                                             vstride, nrhs, nchunk, pmap);
+      if (g_prof) g_prof->end(KC_BWD, s);
+    }
   }
 }
 

@@ -1,23 +1,41 @@
-// Update-row products of the FP32 solves on the fifth-generation tensor
-// cores (tcgen05.mma kind::tf32, accumulators in TMEM).
+// Front products of the FP32 solves (Algorithm 1: solve with the cached
+// factors).  With the pivot blocks stored as their explicit inverses
+// T11 = L11^-1, every step of both sweeps is a product of a factor block with
+// the 32 right-hand sides of one pole (modes in kernels.h):
+//   forward, per level:  TRI_F (X_piv = T11 Y_piv), FWD21 (Y_upd -= L21 X_piv)
+//   backward, per level: BWD21 (Y_piv = D^-1 X_piv - L21^T X_upd), TRI_B (X_piv = T11^T Y_piv)
 //
-// A complex product C = L X is one real GEMM: the rows of L are viewed as
-// interleaved (re, im) real rows, the 32 complex right-hand sides as 64 real
-// columns, so P = L_real X_real holds P[2i+a][2j+b] = sum L_a(i,.) X_b(.,j)
-// and re C(i,j) = P[2i][2j] - P[2i+1][2j+1], im C(i,j) = P[2i][2j+1] +
-// P[2i+1][2j].  Every operand is split into TF32 hi + lo parts and three
-// MMAs (hi.hi + hi.lo + lo.hi) give FP32 accuracy: a single TF32 pass is not
-// accurate enough for the refinement to converge.
+// Tensor-core kernel (k_tc_prod): a complex product C = A B is one real GEMM
+// with the rows of A interleaved as (re, im) real rows and the 32 complex
+// right-hand sides as 64 real columns: P[2i+a][2j+b] = sum A_a(i,.) B_b(.,j),
+// re C(i,j) = P[2i][2j] - P[2i+1][2j+1], im C(i,j) = P[2i][2j+1] + P[2i+1][2j].
+// Operands are split into TF32 hi + lo parts and three MMAs (hi.hi + hi.lo +
+// lo.hi, kind::tf32, FP32 accumulation) give FP32 accuracy.
 //
-// One CTA computes a 128 x 64 real tile (64 complex rows x 32 RHS) with a
-// warp-specialised pipeline: warps 0-3 load K chunks from global memory,
-// split them and stage them in a ring of NSTAGE shared-memory buffers
-// (K-major, no swizzle) and signal "full"; warp 4 issues the MMAs of a full
-// stage and commits them to the stage's "empty" barrier, which frees it for
-// the producers.  After the last chunk warps 0-3 read the accumulators from
-// TMEM (warp w owns lanes 32w..32w+31) and write the complex results.
-// Every wait is bounded; a wait that gives up raises the CTA's abort flag
-// and the status word, and all warps wind down to the TMEM release.
+// One persistent CTA per SM slot walks a static list of (tile, pole, RHS
+// chunk) items; each item is a 128 x 64 real output tile streamed over its
+// inner dimension in chunks of 16:
+//   warps 0-3  (producers) load the raw chunk into a ring of NRAW shared
+//              slots (NRAW - 1 chunks in flight): A by TMA from the front's
+//              tensor map and contiguous B rows by TMA from the vector's map
+//              (one thread), gathered B rows by 16-byte cp.async (each warp
+//              its own rows), then split it:
+//              A hi/lo -> tensor memory (tcgen05.st, thread = TMEM lane =
+//              real row), B hi/lo -> shared memory (K-major core matrices);
+//   warp 8     issues the MMAs of a chunk (A from TMEM, B from shared) into
+//              one of two TMEM accumulators and commits to the stage's
+//              "empty" barrier and, after an item's last chunk, to "accf";
+//   warps 4-7  (epilogue) read the accumulator of the previous item, release
+//              it ("acce") and combine / store / atomically subtract the
+//              results while the next item accumulates.
+// Every wait is bounded: a wait that gives up raises the CTA's abort flag and
+// the status word, all roles wind down, the MMA issuer drains its
+// outstanding MMAs and the TMEM is released.
+//
+// The SIMT kernel (k_prod_simt) computes the same products on the FP32 pipes.
+#include <cstring>
+#include <cuda.h>   // CUtensorMap and the encoder's signature (called through the runtime's entry point)
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.cuh"
@@ -25,311 +43,718 @@
 namespace tem {
 
 namespace {
-constexpr int TBM = 128;     // real rows per CTA (64 complex)
-constexpr int TBN = 64;      // real columns (32 complex RHS)
-constexpr int TKC = 16;      // K per stage (2 MMA k-steps of 8)
-constexpr int NSTAGE = 3;
-constexpr int NPROD = 128;   // producer / epilogue threads (warps 0-3)
+constexpr int TKC = 32;       // inner dimension per chunk (four MMA k-steps)
+constexpr int NRAW = 3;       // raw ring depth (NRAW - 1 chunks in flight)
+constexpr int NST = 2;        // TMEM A stages / shared B stages
+constexpr int NTHR = 288;     // 4 producer + 4 epilogue + 1 MMA warp
+constexpr int RAWA = 4096;    // floats per raw A slot: 32 x 128 (column-major) or 2 x 64 x 32 (row-major, 128B swizzle)
+constexpr int RAWB = TKC * 64;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t COL_A = 128;   // A stages after the two 64-column accumulators
 constexpr uint32_t kWaitIter = 1u << 26;
+constexpr unsigned kFull = 0xffffffffu;
 
-struct Stage {
-  float A[2][TBM * TKC];   // hi, lo
-  float B[2][TBN * TKC];   // hi, lo
-};
 struct TcShared {
-  Stage st[NSTAGE];
-  uint64_t full[NSTAGE], empty[NSTAGE], done;
+  float rawA[NRAW][RAWA];         // 16 KB slots, 1024-byte aligned (swizzle atoms)
+  float rawB[NRAW][RAWB];
+  float Bs[NST][2][64 * TKC];     // hi, lo (K-major, no swizzle)
+  uint64_t full[NST], empty[NST], accf[2], acce[2], fin;
+  uint64_t rawfull[NRAW], rawempty[NRAW];
+  int kval[NRAW];                 // valid inner indices of the chunk in each raw slot
   uint32_t tmem;
   int abort;
 };
-constexpr size_t kTcSmem = sizeof(TcShared);
+constexpr size_t kTcSmem = sizeof(TcShared) + 1024;   // + alignment slack of the dynamic base
+
+__host__ __device__ constexpr bool row_major(int mode) { return mode == PM_BWD21 || mode == PM_TRI_B; }
+__host__ __device__ constexpr bool gathered_b(int mode) { return mode == PM_BWD21; }
+
+struct ProdArgs {
+  const c64 *L;
+  int64_t lstride;
+  const TcTask *tasks;
+  int ntask;
+  const int32_t *rows;
+  const c64 *B;      // source of the B rows
+  c64 *out;          // destination
+  const c64 *xaux;   // BWD21: X (the D^-1 X term)
+  const c64 *dinv;   // BWD21: [pole][N]
+  const CUtensorMap *tmaps;
+  const CUtensorMap *bmap;   // contiguous B rows by TMA (nullptr: cp.async)
+  int64_t N;
+  int64_t vstride;
+  int nrhs, nchunk, np;
+  const int *pmap;
+  DevStatus *st;
+};
+
+// An item: task of pole p, RHS chunk ch (items are numbered per CTA).
+struct Item {
+  TcTask t;
+  int p, ch, nch;
+  bool valid;
+};
+
+__device__ __forceinline__ Item load_item(const ProdArgs &a, int j) {
+  Item it;
+  const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
+  const int64_t idx = int64_t(blockIdx.x) + int64_t(j) * gridDim.x;
+  it.valid = idx < total;
+  if (!it.valid) {
+    it.nch = 0;
+    it.p = it.ch = 0;
+    it.t = TcTask{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    return it;
+  }
+  const int q = int(idx / a.ntask);
+  const int ti = int(idx - int64_t(q) * a.ntask);
+  const int ps = q / a.nchunk;
+  it.ch = q - ps * a.nchunk;
+  it.p = pole_of(ps, a.pmap);
+  const int4 *src = reinterpret_cast<const int4 *>(a.tasks + ti);
+  const int4 w0 = __ldg(src), w1 = __ldg(src + 1);
+  it.t.map = w0.x;
+  it.t.x0 = w0.y;
+  it.t.y0 = w0.z;
+  it.t.kdim = w0.w;
+  it.t.mrows = w1.x;
+  it.t.bbase = w1.y;
+  it.t.obase = w1.z;
+  it.t.mfirst = int16_t(w1.w & 0xffff);
+  it.t.kfirst = int16_t(uint32_t(w1.w) >> 16);
+  it.nch = (it.t.kdim + TKC - 1) / TKC;
+  return it;
+}
 
 // float offset of element (row r, k c) of a K-major no-swizzle tile with `rows` rows
 __device__ __forceinline__ int kmaj_off(int r, int c, int rows) {
   return (c >> 3) * (rows * 8) + (r >> 3) * 64 + ((c & 7) >> 2) * 32 + (r & 7) * 4 + (c & 3);
 }
 
-// Split four consecutive-k values of one row and store them as 16-byte
-// vectors (a core-matrix row holds exactly 4 consecutive k).
-__device__ __forceinline__ void put4(float *hi, float *lo, int off, float a, float b, float c, float d) {
-  const float4 h = make_float4(tc::to_tf32(a), tc::to_tf32(b), tc::to_tf32(c), tc::to_tf32(d));
+__device__ __forceinline__ void split4(float *hi, float *lo, int off, const float *v) {
+  const float4 h = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
   *reinterpret_cast<float4 *>(hi + off) = h;
-  *reinterpret_cast<float4 *>(lo + off) =
-      make_float4(tc::to_tf32(a - h.x), tc::to_tf32(b - h.y), tc::to_tf32(c - h.z), tc::to_tf32(d - h.w));
+  *reinterpret_cast<float4 *>(lo + off) = make_float4(tc::to_tf32(v[0] - h.x), tc::to_tf32(v[1] - h.y),
+                                                      tc::to_tf32(v[2] - h.z), tc::to_tf32(v[3] - h.w));
 }
 
-// B operand (64 real columns = 32 complex RHS) of a chunk: thread t stages
-// column nn = t % 64 for the 8 consecutive k = 8 (t / 64) + 0..7.
-template <class RowPtr>
-__device__ __forceinline__ void stage_b(Stage &s, const float *X, int k0, int kmax, int nrhs, int ch, int ncols,
-                                        RowPtr row_of, int tid) {
-  const int nn = tid & 63, cb = (tid >> 6) * 8;
-  float v[8];
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const int c = k0 + cb + j;
-    v[j] = (c < kmax && (nn >> 1) < ncols) ? X[2 * (int64_t(row_of(c)) * nrhs + ch * 32) + nn] : 0.f;
-  }
-  put4(s.B[0], s.B[1], kmaj_off(nn, cb, TBN), v[0], v[1], v[2], v[3]);
-  put4(s.B[0], s.B[1], kmaj_off(nn, cb + 4, TBN), v[4], v[5], v[6], v[7]);
+__device__ __forceinline__ bool wait_bar(TcShared &sh, uint64_t *bar, uint32_t parity, DevStatus *st) {
+  if (tc::mbar_wait_or_abort(bar, parity, kWaitIter, &sh.abort)) return true;
+  sh.abort = 1;
+  atomicExch(&st->tc_timeout, 1);
+  return false;
 }
 
-// Forward operand geometry: A = L21 rows i0..i0+63 (real rows 2i+a), K =
-// pivot columns; B = X pivot rows.
-struct FwdOps {
-  const float *A;   // float view of L21 (column c at 2 (c n + i0))
-  const float *X;
-  int64_t n;
-  int i0, b, k, c0, nrhs, ch, ncols;
-  __device__ int kdim() const { return k; }
-  __device__ void stage(Stage &s, int k0, int tid) const {
-    // thread t owns real row r = t for all TKC k of the chunk
-    const int r = tid;
-    const bool rok = i0 + (r >> 1) < b;
-    float v[TKC];
-#pragma unroll
-    for (int c = 0; c < TKC; c++)
-      v[c] = (rok && k0 + c < k) ? A[2 * (int64_t(k0 + c) * n + i0) + r] : 0.f;
-#pragma unroll
-    for (int g = 0; g < TKC; g += 4) put4(s.A[0], s.A[1], kmaj_off(r, g, TBM), v[g], v[g + 1], v[g + 2], v[g + 3]);
-    const int cbase = c0;
-    stage_b(s, X, k0, k, nrhs, ch, ncols, [cbase](int c) { return cbase + c; }, tid);
-  }
-};
+__device__ __forceinline__ bool aborted(TcShared &sh) { return *reinterpret_cast<volatile int *>(&sh.abort) != 0; }
 
-// Backward operand geometry: A = L21 columns cb..cb+63 transposed (real
-// rows 2c+a), K = update rows; B = X at the update rows.
-struct BwdOps {
-  const float *L;   // float view of the front block (column c at 2 c n)
-  const float *X;
-  const int32_t *urow;
-  int64_t n;
-  int cb, b, k, nrhs, ch, ncols;
-  __device__ int kdim() const { return b; }
-  __device__ void stage(Stage &s, int k0, int tid) const {
-    // thread t owns real row r = t = 2c + a for all TKC update rows of the chunk
-    const int r = tid, c = cb + (r >> 1), a = r & 1;
-    const bool cok = c < k;
-    const float *col = L + 2 * (int64_t(c) * n + k) + a;
-    float v[TKC];
-#pragma unroll
-    for (int i = 0; i < TKC; i++) v[i] = (cok && k0 + i < b) ? col[2 * (k0 + i)] : 0.f;
-#pragma unroll
-    for (int g = 0; g < TKC; g += 4) put4(s.A[0], s.A[1], kmaj_off(r, g, TBM), v[g], v[g + 1], v[g + 2], v[g + 3]);
-    const int32_t *ur = urow;
-    stage_b(s, X, k0, b, nrhs, ch, ncols, [ur](int i) { return ur[i]; }, tid);
-  }
-};
+// ---------------------------------------------------------------------------
+// producers (warps 0-3, thread t = real row t of the tile)
 
-// Runs the pipeline; returns true (on the producer threads) when the
-// accumulator in TMEM holds the whole product.
-template <class Ops>
-__device__ bool run_pipeline(TcShared &sh, const Ops &ops, DevStatus *st) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nchunks = (ops.kdim() + TKC - 1) / TKC;
-  if (warp < 4) {
-    for (int c = 0; c < nchunks; c++) {
-      const int s = c % NSTAGE, round = c / NSTAGE;
-      if (round > 0 && !tc::mbar_wait_or_abort(&sh.empty[s], (round - 1) & 1, kWaitIter, &sh.abort)) {
-        sh.abort = 1;
-        atomicExch(&st->tc_timeout, 1);
-        break;
-      }
-      ops.stage(sh.st[s], c * TKC, tid);
-      tc::fence_async_smem();
-      tc::mbar_arrive(&sh.full[s]);
+template <int MODE>
+struct Fetch {
+  Item cur, nxt;
+  int j = 0, c = 0;
+  int32_t ridx[8];   // gathered B rows 8w..8w+7 of the current chunk (BWD21)
+
+  __device__ void prep(const ProdArgs &a, int tid) {
+    if (!gathered_b(MODE) || !cur.valid || c >= cur.nch) return;
+    const int kb = (tid >> 5) * 8, k0 = c * TKC;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int kk = k0 + kb + q;
+      ridx[q] = (kk < cur.t.kdim && kk >= cur.t.kfirst) ? __ldg(a.rows + cur.t.bbase + kk) : 0;
     }
-  } else if (lane == 0) {
-    const uint32_t idesc = tc::idesc_tf32(TBM, TBN);
-    for (int c = 0; c < nchunks; c++) {
-      const int s = c % NSTAGE, round = c / NSTAGE;
-      if (!tc::mbar_wait_or_abort(&sh.full[s], round & 1, kWaitIter, &sh.abort)) {
-        sh.abort = 1;
-        atomicExch(&st->tc_timeout, 1);
+  }
+  // move on to the next item that has chunks (the others need no data)
+  __device__ void settle(const ProdArgs &a, int tid) {
+    while (cur.valid && c >= cur.nch) {
+      cur = nxt;
+      j++;
+      c = 0;
+      nxt = load_item(a, j + 1);
+    }
+    prep(a, tid);
+  }
+  __device__ void start(const ProdArgs &a, int tid) {
+    cur = load_item(a, 0);
+    nxt = load_item(a, 1);
+    settle(a, tid);
+  }
+  __device__ bool active() const { return cur.valid; }
+
+  // Issue the loads of the current chunk (global chunk number `gc`) into raw
+  // slot gc % NRAW, then advance: A (and contiguous B rows) by TMA from
+  // thread 0 once every producer thread has released the slot; gathered B
+  // rows 8w..8w+7 by warp w.
+  __device__ bool issue(const ProdArgs &a, TcShared &sh, int gc, int tid) {
+    const int slot = gc % NRAW;
+    const int k0 = c * TKC;
+    const TcTask &t = cur.t;
+    const void *dummy = a.L;
+    const int w = tid >> 5, l = tid & 31;
+    bool ok = true;
+    const bool tma_b = !gathered_b(MODE) && a.bmap != nullptr;
+    if (tid == 0) {
+      if (gc >= NRAW) ok = wait_bar(sh, &sh.rawempty[slot], ((gc / NRAW) - 1) & 1, a.st);
+      if (ok) {
+        sh.kval[slot] = min(TKC, t.kdim - k0);
+        tc::mbar_arrive_expect_tx(&sh.rawfull[slot], RAWA * 4 + (tma_b ? RAWB * 4 : 0));
+        const CUtensorMap *m = a.tmaps + t.map;
+        if (!row_major(MODE)) {
+          tc::tma_load_3d(sh.rawA[slot], m, t.x0, t.y0 + k0, cur.p, &sh.rawfull[slot]);
+        } else {
+          tc::tma_load_3d(sh.rawA[slot], m, t.x0 + 2 * k0, t.y0, cur.p, &sh.rawfull[slot]);
+          tc::tma_load_3d(sh.rawA[slot] + RAWA / 2, m, t.x0 + 2 * k0 + 32, t.y0, cur.p, &sh.rawfull[slot]);
+        }
+        if (tma_b) tc::tma_load_3d(sh.rawB[slot], a.bmap, 64 * cur.ch, t.bbase + k0, cur.p, &sh.rawfull[slot]);
+      }
+    }
+    if (!tma_b) {
+      // B rows 8w..8w+7: 32 complex each
+      const int ncols = min(32, a.nrhs - cur.ch * 32);
+      const c64 *bp = a.B + int64_t(cur.p) * a.vstride + cur.ch * 32;
+      float *rb = sh.rawB[slot];
+      if ((a.nrhs & 1) == 0) {
+#pragma unroll
+        for (int q4 = 0; q4 < 4; q4++) {
+          const int q = l + 32 * q4;
+          const int r = q >> 4, pc = q & 15;   // r = 2 q4 + (l >> 4)
+          const int kk = k0 + 8 * w + r;
+          const bool rok = kk < t.kdim && kk >= t.kfirst;
+          const int nv = rok ? max(0, min(2, ncols - 2 * pc)) : 0;
+          const int32_t gr = (l >> 4) ? ridx[2 * q4 + 1] : ridx[2 * q4];
+          const int64_t row = gathered_b(MODE) ? int64_t(gr) : int64_t(t.bbase) + kk;
+          const void *src = nv ? static_cast<const void *>(bp + row * a.nrhs + 2 * pc) : dummy;
+          tc::cp_async16(rb + (8 * w + r) * 64 + 4 * pc, src, 8 * nv);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+          const int kk = k0 + 8 * w + r;
+          const bool rok = kk < t.kdim && kk >= t.kfirst && l < ncols;
+          const int64_t row = gathered_b(MODE) ? int64_t(ridx[r]) : int64_t(t.bbase) + kk;
+          const void *src = rok ? static_cast<const void *>(bp + row * a.nrhs + l) : dummy;
+          tc::cp_async8(rb + (8 * w + r) * 64 + 2 * l, src, rok);
+        }
+      }
+    }
+    c++;
+    settle(a, tid);
+    return ok;
+  }
+};
+
+// A values kk0..kk0+15 of row `tid` of the chunk in raw slot `slot`.
+template <int MODE>
+__device__ __forceinline__ void load_a16(const TcShared &sh, int slot, int tid, int kk0, float *v) {
+  if (!row_major(MODE)) {
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) v[kk] = sh.rawA[slot][(kk0 + kk) * 128 + tid];
+  } else {
+    // row c of a 64 x 32-float box (16 complex of the inner dimension), 16-byte
+    // chunks swizzled by c & 7; inner indices 16..31 are in the second box
+    const int cc = tid >> 1, sw = cc & 7;
+    const float *src = sh.rawA[slot] + (kk0 >> 4) * (RAWA / 2) + cc * 32 + (tid & 1);
+#pragma unroll
+    for (int e = 0; e < 16; e++) v[e] = src[(((e >> 1) ^ sw) << 2) + 2 * (e & 1)];
+  }
+}
+
+template <int MODE>
+__device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
+  Fetch<MODE> f;
+  f.start(a, tid);
+  int issued = 0;
+  bool ok = true;
+  // prologue: NRAW - 1 chunks in flight
+#pragma unroll 1
+  for (int i = 0; i < NRAW - 1; i++) {
+    if (f.active()) {
+      ok = f.issue(a, sh, issued, tid) && ok;
+      issued++;
+    }
+    tc::cp_async_commit();
+  }
+  const int w = tid >> 5, l = tid & 31;
+  ok = __all_sync(kFull, ok);
+  int g = 0;
+  int pend = -1;   // stage whose TMEM / shared stores are in flight, signalled one chunk later
+#pragma unroll 1
+  for (; g < issued && ok; g++) {
+    __syncwarp();   // every lane has read the B slot about to be refilled
+    if (f.active()) {
+      ok = f.issue(a, sh, issued, tid);
+      issued++;
+    }
+    tc::cp_async_commit();
+    tc::cp_async_wait<NRAW - 1>();        // gathered B of chunk g has landed (this warp's copies)
+    __syncwarp();
+    const int slot = g % NRAW;
+    ok = wait_bar(sh, &sh.rawfull[slot], (g / NRAW) & 1, a.st) && ok;   // TMA loads of chunk g
+    if (!__all_sync(kFull, ok)) break;
+    // the previous chunk's stores had this chunk's loads to land
+    if (pend >= 0) {
+      tc::tmem_st_wait();
+      tc::fence_async_smem();
+      tc::fence_before();
+      tc::mbar_arrive(&sh.full[pend]);
+      pend = -1;
+    }
+    // stage s must have been consumed by the MMAs of chunk g - NST
+    const int s = g % NST, use = g / NST;
+    if (use > 0) ok = wait_bar(sh, &sh.empty[s], (use - 1) & 1, a.st);
+    if (!__all_sync(kFull, ok)) break;
+    tc::fence_after();
+    const uint32_t ta = sh.tmem + (uint32_t(w * 32) << 16) + COL_A + 64 * s;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      float v[16], hi[16], lo[16];
+      load_a16<MODE>(sh, slot, tid, 16 * half, v);
+#pragma unroll
+      for (int kk = 0; kk < 16; kk++) {
+        hi[kk] = tc::to_tf32(v[kk]);
+        lo[kk] = tc::to_tf32(v[kk] - hi[kk]);
+      }
+      tc::tmem_st16(ta + 16 * half, hi);
+      tc::tmem_st16(ta + 32 + 16 * half, lo);
+    }
+    // B: columns l and l + 32 of rows 8w..8w+7 (rows past the inner dimension are zero)
+    const int kv = sh.kval[slot];
+#pragma unroll
+    for (int col = 0; col < 64; col += 32) {
+      float bv[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) bv[q] = (8 * w + q < kv) ? sh.rawB[slot][(8 * w + q) * 64 + col + l] : 0.f;
+      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(col + l, 8 * w, 64), bv);
+      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(col + l, 8 * w + 4, 64), bv + 4);
+    }
+    tc::mbar_arrive(&sh.rawempty[slot]);   // every read of this raw slot is done
+    pend = s;
+    if (__any_sync(kFull, aborted(sh))) break;
+  }
+  tc::tmem_st_wait();
+  if (pend >= 0 && ok) {
+    tc::fence_async_smem();
+    tc::fence_before();
+    tc::mbar_arrive(&sh.full[pend]);
+  }
+  tc::cp_async_wait_all();
+  // after an abort: let the TMA loads still in flight land before the CTA exits
+  if (tid == 0)
+    for (int q = g; q < issued; q++) tc::mbar_wait(&sh.rawfull[q % NRAW], (q / NRAW) & 1, kWaitIter);
+}
+
+// ---------------------------------------------------------------------------
+// MMA issuer (one thread of warp 8)
+
+__device__ void mma_issuer(const ProdArgs &a, TcShared &sh) {
+  const uint32_t idesc = tc::idesc_tf32(128, 64);
+  int g = 0;
+  bool ok = true;
+  Item nxt = load_item(a, 0);
+#pragma unroll 1
+  for (int j = 0; ok; j++) {
+    const Item it = nxt;
+    if (!it.valid) break;
+    nxt = load_item(a, j + 1);
+    const int buf = j & 1, use = j >> 1;
+    if (use > 0 && !wait_bar(sh, &sh.acce[buf], (use - 1) & 1, a.st)) break;
+    tc::fence_after();
+    const uint32_t d = sh.tmem + 64 * buf;
+#pragma unroll 1
+    for (int c = 0; c < it.nch; c++, g++) {
+      const int s = g % NST;
+      if (!wait_bar(sh, &sh.full[s], (g / NST) & 1, a.st)) {
+        ok = false;
         break;
       }
       tc::fence_after();
-      Stage &S = sh.st[s];
 #pragma unroll
       for (int ks = 0; ks < TKC / 8; ks++) {
-        const uint64_t ah = tc::desc_kmajor(tc::smem_addr(&S.A[0][ks * TBM * 8]), 128, 256);
-        const uint64_t al = tc::desc_kmajor(tc::smem_addr(&S.A[1][ks * TBM * 8]), 128, 256);
-        const uint64_t bh = tc::desc_kmajor(tc::smem_addr(&S.B[0][ks * TBN * 8]), 128, 256);
-        const uint64_t bl = tc::desc_kmajor(tc::smem_addr(&S.B[1][ks * TBN * 8]), 128, 256);
-        tc::mma_tf32(sh.tmem, ah, bh, idesc, !(c == 0 && ks == 0));
-        tc::mma_tf32(sh.tmem, ah, bl, idesc, true);
-        tc::mma_tf32(sh.tmem, al, bh, idesc, true);
+        const uint32_t ah = sh.tmem + COL_A + 64 * s + 8 * ks, al = ah + 32;
+        const uint64_t bh = tc::desc_kmajor(tc::smem_addr(&sh.Bs[s][0][ks * 64 * 8]), 128, 256);
+        const uint64_t bl = tc::desc_kmajor(tc::smem_addr(&sh.Bs[s][1][ks * 64 * 8]), 128, 256);
+        tc::mma_tf32_ts(d, ah, bh, idesc, c > 0 || ks > 0);
+        tc::mma_tf32_ts(d, ah, bl, idesc, true);
+        tc::mma_tf32_ts(d, al, bh, idesc, true);
       }
       tc::commit(&sh.empty[s]);
     }
-    tc::commit(&sh.done);   // arrives when every MMA issued above has completed
+    if (!ok) break;
+    tc::commit(&sh.accf[buf]);
   }
-  if (warp >= 4) return false;
-  if (nchunks == 0) return false;
-  const bool ok = tc::mbar_wait_or_abort(&sh.done, 0, kWaitIter, &sh.abort) && !sh.abort;
-  if (!ok) atomicExch(&st->tc_timeout, 1);
-  tc::fence_after();
-  return ok;
+  // drain: every MMA issued above has completed once fin arrives
+  tc::commit(&sh.fin);
+  if (!tc::mbar_wait(&sh.fin, 0, kWaitIter)) atomicExch(&a.st->tc_timeout, 1);
 }
 
-__device__ __forceinline__ void setup(TcShared &sh) {
+// ---------------------------------------------------------------------------
+// epilogue (warps 4-7; e = real row of the tile)
+
+template <int MODE>
+__device__ void epilogue(const ProdArgs &a, TcShared &sh, int e) {
+  const int we = e >> 5, half = e & 1;
+  Item nxt = load_item(a, 0);
+#pragma unroll 1
+  for (int j = 0;; j++) {
+    const Item it = nxt;
+    if (!it.valid) break;
+    nxt = load_item(a, j + 1);
+    const int buf = j & 1, use = j >> 1;
+    const bool ok = wait_bar(sh, &sh.accf[buf], use & 1, a.st);
+    if (!__all_sync(kFull, ok)) break;
+    tc::fence_after();
+    float v[64];
+    if (it.nch > 0) {
+      tc::tmem_ld64(sh.tmem + (uint32_t(we * 32) << 16) + 64 * buf, v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 64; q++) v[q] = 0.f;
+    }
+    tc::fence_before();
+    tc::mbar_arrive(&sh.acce[buf]);
+    // lane pair (2i, 2i+1) = (re, im) row of complex row i; lane `half`
+    // finishes right-hand sides 16 half .. 16 half + 15
+    float E[32], O[32];
+#pragma unroll
+    for (int q = 0; q < 32; q++) {
+      const float mine = half ? v[32 + q] : v[q];
+      const float send = half ? v[q] : v[32 + q];
+      const float got = __shfl_xor_sync(kFull, send, 1);
+      E[q] = half ? got : mine;   // row 2i (re part of A)
+      O[q] = half ? mine : got;   // row 2i+1 (im part of A)
+    }
+    const int m = e >> 1;
+    if (m >= it.t.mrows || m < it.t.mfirst) continue;
+    const int ncols = min(32, a.nrhs - it.ch * 32);
+    const int j0 = 16 * half;
+    const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
+    if (MODE == PM_FWD21) {
+      const int32_t g = __ldg(a.rows + it.t.obase + m);
+      float2 *y = reinterpret_cast<float2 *>(a.out + pv + int64_t(g) * a.nrhs);
+      if ((a.nrhs & 1) == 0) {
+        // two right-hand sides per 16-byte atomic (rows start on 16-byte boundaries)
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          if (j0 + q + 1 < ncols)
+            atomicAdd(reinterpret_cast<float4 *>(y + j0 + q),
+                      make_float4(O[2 * q + 1] - E[2 * q], -(E[2 * q + 1] + O[2 * q]), O[2 * q + 3] - E[2 * q + 2],
+                                  -(E[2 * q + 3] + O[2 * q + 2])));
+          else if (j0 + q < ncols)
+            atomicAdd(y + j0 + q, make_float2(O[2 * q + 1] - E[2 * q], -(E[2 * q + 1] + O[2 * q])));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; q++)
+          if (j0 + q < ncols)
+            atomicAdd(y + j0 + q, make_float2(O[2 * q + 1] - E[2 * q], -(E[2 * q + 1] + O[2 * q])));
+      }
+    } else if (MODE == PM_BWD21) {
+      const int64_t row = int64_t(it.t.obase) + m;
+      const c64 di = a.dinv[int64_t(it.p) * a.N + row];
+      const c64 *x = a.xaux + pv + row * a.nrhs;
+      c64 *y = a.out + pv + row * a.nrhs;
+#pragma unroll
+      for (int q = 0; q < 16; q++)
+        if (j0 + q < ncols) {
+          const c64 dx = di * x[j0 + q];
+          y[j0 + q] = mk<float>(dx.x - (E[2 * q] - O[2 * q + 1]), dx.y - (E[2 * q + 1] + O[2 * q]));
+        }
+    } else {
+      c64 *y = a.out + pv + (int64_t(it.t.obase) + m) * a.nrhs;
+#pragma unroll
+      for (int q = 0; q < 16; q++)
+        if (j0 + q < ncols) y[j0 + q] = mk<float>(E[2 * q] - O[2 * q + 1], E[2 * q + 1] + O[2 * q]);
+    }
+  }
+}
+
+}  // namespace
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHR, 2) k_tc_prod(const ProdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TcShared &sh = *reinterpret_cast<TcShared *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 4) tc::tmem_alloc(&sh.tmem, TBN);
+  if (warp == 8) tc::tmem_alloc(&sh.tmem, TMEM_COLS);
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; s++) {
-      tc::mbar_init(&sh.full[s], NPROD);
+    for (int s = 0; s < NST; s++) {
+      tc::mbar_init(&sh.full[s], 128);
       tc::mbar_init(&sh.empty[s], 1);
     }
-    tc::mbar_init(&sh.done, 1);
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&sh.accf[b], 1);
+      tc::mbar_init(&sh.acce[b], 128);
+    }
+    tc::mbar_init(&sh.fin, 1);
+    for (int r = 0; r < NRAW; r++) {
+      tc::mbar_init(&sh.rawfull[r], 1);
+      tc::mbar_init(&sh.rawempty[r], 128);
+    }
     sh.abort = 0;
     tc::fence_async_smem();
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-}
-
-__device__ __forceinline__ void teardown(TcShared &sh) {
+  if (warp < 4) producer<MODE>(a, sh, tid);
+  else if (warp < 8) epilogue<MODE>(a, sh, tid - 128);
+  else if ((tid & 31) == 0) mma_issuer(a, sh);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if ((threadIdx.x >> 5) == 4) tc::tmem_dealloc(sh.tmem, TBN);
+  if (warp == 8) tc::tmem_dealloc(sh.tmem, TMEM_COLS);
 }
 
-// The even lane of each (re, im) row pair gets the complex results of RHS j:
-// cre[j], cim[j] (j < 32).  Executed by whole warps 0-3.
-__device__ __forceinline__ void read_complex(uint32_t tmem, int warp, float *cre, float *cim) {
+// ---------------------------------------------------------------------------
+// SIMT version: one CTA per item, 256 threads, lane = right-hand side,
+// warp w owns complex rows 8w..8w+7 of the 64-row tile.
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtTask *__restrict__ tasks) {
+  constexpr int KC = 32;
+  const int ti = blockIdx.x;
+  const int ps = blockIdx.y / a.nchunk, ch = blockIdx.y % a.nchunk;
+  const int p = pole_of(ps, a.pmap);
+  const SimtTask t = tasks[ti];
+  const c64 *Lp = a.L + int64_t(p) * a.lstride + t.aoff;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rhs = ch * 32 + lane;
+  const bool ok = rhs < a.nrhs;
+  const int64_t pv = int64_t(p) * a.vstride;
+  __shared__ c64 As[KC][65];
+  __shared__ c64 Bs[KC][32];
+  c64 acc[8];
 #pragma unroll
-  for (int cb = 0; cb < TBN; cb += 16) {
-    float v[16];
-    tc::tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + cb, v);
+  for (int q = 0; q < 8; q++) acc[q] = mk<float>(0.f, 0.f);
+  for (int k0 = 0; k0 < t.kdim; k0 += KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KC * 64; idx += 256) {
+      int m, kk;
+      if (!row_major(MODE)) {
+        m = idx % 64;
+        kk = idx / 64;
+      } else {
+        kk = idx % KC;
+        m = idx / KC;
+      }
+      const bool v = m < t.mrows && k0 + kk < t.kdim;
+      const int64_t off = row_major(MODE) ? int64_t(m) * t.lda + k0 + kk : int64_t(k0 + kk) * t.lda + m;
+      As[kk][m] = v ? Lp[off] : mk<float>(0.f, 0.f);
+    }
+    for (int kk = warp; kk < KC; kk += 8) {
+      const int k = k0 + kk;
+      c64 bv = mk<float>(0.f, 0.f);
+      if (ok && k < t.kdim && k >= t.kfirst) {
+        const int64_t row = gathered_b(MODE) ? int64_t(a.rows[t.bbase + k]) : int64_t(t.bbase) + k;
+        bv = a.B[pv + row * a.nrhs + rhs];
+      }
+      Bs[kk][lane] = bv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; kk++) {
+      const c64 bv = Bs[kk][lane];
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const float p0 = v[2 * q], p1 = v[2 * q + 1];            // P[r][2j], P[r][2j+1]
-      const float o0 = __shfl_xor_sync(0xffffffffu, p0, 1);     // partner row (im of L)
-      const float o1 = __shfl_xor_sync(0xffffffffu, p1, 1);
-      const int j = cb / 2 + q;
-      cre[j] = p0 - o1;
-      cim[j] = p1 + o0;
+      for (int q = 0; q < 8; q++) cfma(acc[q], As[kk][warp * 8 + q], bv);
     }
   }
-}
-}  // namespace
-
-// Forward: Y[rows_i] -= sum_c L21[i][c] X[c0 + c] for 64 update rows i.
-__global__ void __launch_bounds__(160) k_fwd_l21_tc(const c64 *__restrict__ L, int64_t lstride,
-                                                    const FrontDev *__restrict__ F,
-                                                    const int2 *__restrict__ tasks,
-                                                    const int32_t *__restrict__ rows, c64 *__restrict__ Y,
-                                                    const c64 *__restrict__ X, int64_t vstride, int nrhs,
-                                                    int nchunk, const int *__restrict__ pmap,
-                                                    DevStatus *st) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  TcShared &sh = *reinterpret_cast<TcShared *>(smem_raw);
-  const int2 t = tasks[blockIdx.x];
-  const FrontDev f = F[t.x];
-  const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
-  FwdOps ops;
-  ops.A = reinterpret_cast<const float *>(L + p * lstride + f.lofs + f.k);
-  ops.X = reinterpret_cast<const float *>(X + p * vstride);
-  ops.n = f.n;
-  ops.i0 = t.y * (TBM / 2);
-  ops.b = f.n - f.k;
-  ops.k = f.k;
-  ops.c0 = f.c0;
-  ops.nrhs = nrhs;
-  ops.ch = ch;
-  ops.ncols = min(32, nrhs - ch * 32);
-  setup(sh);
-  const bool ok = run_pipeline(sh, ops, st);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (ok) {
-    float cre[32], cim[32];
-    read_complex(sh.tmem, warp, cre, cim);
-    const int r = warp * 32 + lane;
-    const int i = ops.i0 + (r >> 1);
-    if ((r & 1) == 0 && i < ops.b) {
-      const int32_t g = rows[f.rows_off + i];
-      c64 *y = Y + p * vstride + int64_t(g) * nrhs + ch * 32;
-      for (int j = 0; j < ops.ncols; j++) atomic_add_cx(y + j, mk<float>(-cre[j], -cim[j]));
-    }
-  }
-  teardown(sh);
-}
-
-// Backward: W[c0 + c] = X[c0 + c] / D_c - sum_i L21[i][c] X[rows_i] for 64 pivot columns c.
-__global__ void __launch_bounds__(160) k_bwd_l21_tc(const c64 *__restrict__ L, int64_t lstride,
-                                                    const FrontDev *__restrict__ F,
-                                                    const int2 *__restrict__ tasks,
-                                                    const int32_t *__restrict__ rows, c64 *__restrict__ Y,
-                                                    const c64 *__restrict__ X, int64_t vstride, int nrhs,
-                                                    int nchunk, const int *__restrict__ pmap,
-                                                    DevStatus *st) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  TcShared &sh = *reinterpret_cast<TcShared *>(smem_raw);
-  const int2 t = tasks[blockIdx.x];
-  const FrontDev f = F[t.x];
-  const int p = pole_of(blockIdx.y / nchunk, pmap), ch = blockIdx.y % nchunk;
-  const c64 *Lp = L + p * lstride + f.lofs;
-  BwdOps ops;
-  ops.L = reinterpret_cast<const float *>(Lp);
-  ops.X = reinterpret_cast<const float *>(X + p * vstride);
-  ops.urow = rows + f.rows_off;
-  ops.n = f.n;
-  ops.cb = t.y * (TBM / 2);
-  ops.b = f.n - f.k;
-  ops.k = f.k;
-  ops.nrhs = nrhs;
-  ops.ch = ch;
-  ops.ncols = min(32, nrhs - ch * 32);
-  setup(sh);
-  const bool ok = run_pipeline(sh, ops, st);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp < 4 && (ok || ops.b == 0) && !sh.abort) {
-    float cre[32], cim[32];
-    if (ops.b > 0) {
-      read_complex(sh.tmem, warp, cre, cim);
+  if (!ok) return;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int m = warp * 8 + q;
+    if (m >= t.mrows) break;
+    if (m < t.mfirst) continue;
+    if (MODE == PM_FWD21) {
+      const int64_t g = a.rows[t.obase + m];
+      atomic_add_cx(a.out + pv + g * a.nrhs + rhs, mk<float>(-acc[q].x, -acc[q].y));
+    } else if (MODE == PM_BWD21) {
+      const int64_t row = int64_t(t.obase) + m;
+      const int64_t at = pv + row * a.nrhs + rhs;
+      a.out[at] = a.dinv[int64_t(p) * a.N + row] * a.xaux[at] - acc[q];
     } else {
-#pragma unroll
-      for (int j = 0; j < 32; j++) cre[j] = cim[j] = 0.f;
-    }
-    const int r = warp * 32 + lane;
-    const int c = ops.cb + (r >> 1);
-    if ((r & 1) == 0 && c < f.k) {
-      const c64 dinv = crecip(Lp[int64_t(c) * f.n + c]);
-      const int64_t at = p * vstride + int64_t(f.c0 + c) * nrhs + ch * 32;
-      for (int j = 0; j < ops.ncols; j++) Y[at + j] = X[at + j] * dinv - mk<float>(cre[j], cim[j]);
+      a.out[pv + (int64_t(t.obase) + m) * a.nrhs + rhs] = acc[q];
     }
   }
-  teardown(sh);
 }
 
 namespace {
-void set_smem_once() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_fwd_l21_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
-  cudaFuncSetAttribute(k_bwd_l21_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
-  done = true;
+int g_tc_occupancy = 0;
+
+template <int MODE>
+void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t s) {
+  if (use_tc) {
+    static int grid_max = 0;
+    if (grid_max == 0) {
+      int dev = 0, sms = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaFuncSetAttribute(k_tc_prod<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
+      // all of the unified L1 / shared storage as shared memory: two CTAs per SM
+      cudaFuncSetAttribute(k_tc_prod<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      // Two CTAs per SM: 256 of the 512 TMEM columns, under half of the shared
+      // memory and 2 x 288 x 96 registers each.  (The occupancy calculator
+      // reports one for this 9-warp block; two are resident, as measured by
+      // counting CTAs per SM.)
+      static_assert(2 * (kTcSmem + 1024) <= 228 * 1024, "two CTAs per SM must fit in shared memory");
+      occ = 2;
+      g_tc_occupancy = occ;
+      grid_max = occ * (sms > 0 ? sms : 1);
+    }
+    const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
+    const int grid = int(total < grid_max ? total : grid_max);
+    tem::count_launch();
+    k_tc_prod<MODE><<<grid, NTHR, kTcSmem, s>>>(a);
+  } else {
+    dim3 g(a.ntask, a.np * a.nchunk);
+    tem::count_launch();
+    k_prod_simt<MODE><<<g, 256, 0, s>>>(a, simt);
+  }
 }
 }  // namespace
 
-void launch_fwd_l21_tc(const SolvePlan<float> &P, const LevelDev &lv, DevStatus *st, cudaStream_t s) {
-  set_smem_once();
-  const int nchunk = (P.nrhs + 31) / 32;
-  dim3 g(lv.n_f21tc, P.np * nchunk);
-  tem::count_launch();
-  k_fwd_l21_tc<<<g, 160, kTcSmem, s>>>(P.L, P.lstride, P.F, lv.f21tc_tasks, P.rows, P.Y, P.X, P.vstride, P.nrhs,
-                                        nchunk, P.pmap, st);
+int tc_ctas_per_sm() { return g_tc_occupancy; }
+
+void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
+  if (lv.n_prod[mode] == 0 || P.np == 0) return;
+  ProdArgs a;
+  a.L = P.L;
+  a.lstride = P.lstride;
+  a.tasks = lv.prod[mode];
+  a.ntask = lv.n_prod[mode];
+  a.rows = P.rows;
+  a.N = P.N;
+  a.vstride = P.vstride;
+  a.nrhs = P.nrhs;
+  a.nchunk = (P.nrhs + 31) / 32;
+  a.np = P.np;
+  a.pmap = P.pmap;
+  a.st = P.status;
+  a.dinv = P.dinv;
+  a.tmaps = static_cast<const CUtensorMap *>(P.tmaps);
+  const CUtensorMap *vm = static_cast<const CUtensorMap *>(P.vmaps);   // [0] Y, [1] X (nullptr: odd nrhs)
+  a.bmap = nullptr;
+  a.xaux = nullptr;
+  switch (mode) {
+    case PM_TRI_F:
+      a.bmap = vm ? vm : nullptr;
+      a.B = P.Y;
+      a.out = P.X;
+      run_mode<PM_TRI_F>(a, lv.prod_simt[mode], P.use_tc, s);
+      break;
+    case PM_FWD21:
+      a.bmap = vm ? vm + 1 : nullptr;
+      a.B = P.X;
+      a.out = P.Y;
+      run_mode<PM_FWD21>(a, lv.prod_simt[mode], P.use_tc, s);
+      break;
+    case PM_BWD21:
+      a.B = P.X;
+      a.out = P.Y;
+      a.xaux = P.X;
+      run_mode<PM_BWD21>(a, lv.prod_simt[mode], P.use_tc, s);
+      break;
+    default:
+      a.bmap = vm ? vm : nullptr;
+      a.B = P.Y;
+      a.out = P.X;
+      run_mode<PM_TRI_B>(a, lv.prod_simt[mode], P.use_tc, s);
+      break;
+  }
 }
 
-void launch_bwd_l21_tc(const SolvePlan<float> &P, const LevelDev &lv, DevStatus *st, cudaStream_t s) {
-  set_smem_once();
-  const int nchunk = (P.nrhs + 31) / 32;
-  dim3 g(lv.n_b21tc, P.np * nchunk);
-  tem::count_launch();
-  k_bwd_l21_tc<<<g, 160, kTcSmem, s>>>(P.L, P.lstride, P.F, lv.b21tc_tasks, P.rows, P.Y, P.X, P.vstride, P.nrhs,
-                                        nchunk, P.pmap, st);
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}  // namespace
+
+// Per front, four maps over its factor block viewed as floats: dim 0 runs
+// along a column (2 floats per complex entry; rows k..n-1 excluded for the
+// pivot-block maps 0 and 3), dim 1 over the k columns, dim 2 over the poles.
+// Maps 0/1 (column-major tiles) load 32 columns x 64 complex rows; maps 2/3
+// (row-major tiles) load 64 columns x 16 complex rows with the 128-byte
+// swizzle (two boxes per chunk of 32).  Entries outside the dims read as zero.
+std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
+                              void **out) {
+  *out = nullptr;
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return "cuTensorMapEncodeTiled is not available from the driver";
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  std::vector<CUtensorMap> maps(4 * fronts.size());
+  memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+  for (size_t i = 0; i < fronts.size(); i++) {
+    const FrontGeom &f = fronts[i];
+    if (f.k <= 0) continue;
+    for (int kind = 0; kind < 4; kind++) {
+      const bool tri = (kind == PM_TRI_F || kind == PM_TRI_B);
+      const bool colmaj = !row_major(kind);
+      const cuuint64_t dims[3] = {cuuint64_t(2) * (tri ? f.k : f.n), cuuint64_t(f.k), cuuint64_t(m)};
+      const cuuint64_t strides[2] = {cuuint64_t(f.ld) * sizeof(c64), cuuint64_t(lstride) * sizeof(c64)};
+      const cuuint32_t box[3] = {colmaj ? 128u : 32u, colmaj ? 32u : 64u, 1u};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      const CUresult r =
+          encode(&maps[4 * i + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(L + f.lofs), dims,
+                 strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 colmaj ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed for front " + std::to_string(i);
+    }
+  }
+  void *d = nullptr;
+  if (cudaMalloc(&d, maps.size() * sizeof(CUtensorMap) + 64) != cudaSuccess) return "cudaMalloc of tensor maps failed";
+  if (cudaMemcpy(d, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return "copy of tensor maps failed";
+  }
+  *out = d;
+  return "";
+}
+
+// Maps over the two solve vectors Y, X ([pole][N][nrhs] complex) viewed as
+// floats: rows of 2 nrhs floats, N rows, m poles; a box is 32 rows x 32
+// right-hand sides.  Needs an even nrhs (16-byte row stride); *out = nullptr
+// otherwise (the kernels then copy B rows with cp.async).
+std::string build_vector_maps(const c64 *Y, const c64 *X, int64_t N, int nrhs, int m, void **out) {
+  *out = nullptr;
+  if (nrhs & 1) return "";
+  EncodeTiledFn encode = nullptr;
+  {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return "cuTensorMapEncodeTiled is not available from the driver";
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  CUtensorMap maps[2];
+  const c64 *bases[2] = {Y, X};
+  for (int i = 0; i < 2; i++) {
+    const cuuint64_t dims[3] = {cuuint64_t(2) * nrhs, cuuint64_t(N), cuuint64_t(m)};
+    const cuuint64_t strides[2] = {cuuint64_t(nrhs) * sizeof(c64), cuuint64_t(N) * nrhs * sizeof(c64)};
+    const cuuint32_t box[3] = {64u, 32u, 1u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(bases[i]), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return "cuTensorMapEncodeTiled failed for a solve vector";
+  }
+  void *d = nullptr;
+  if (cudaMalloc(&d, sizeof(maps)) != cudaSuccess) return "cudaMalloc of tensor maps failed";
+  if (cudaMemcpy(d, maps, sizeof(maps), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return "copy of tensor maps failed";
+  }
+  *out = d;
+  return "";
 }
 
 }  // namespace tem

@@ -62,6 +62,19 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B[smem]^T: A is read from tensor memory (row m of
+// the M x 8 tile in lane m, k in consecutive 32-bit columns), B from a
+// K-major shared-memory descriptor.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(uint32_t(accumulate))
+      : "memory");
+}
+
 // The mbarrier tracks completion of this thread's prior tcgen05 operations.
 __device__ __forceinline__ void commit(uint64_t *mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -77,10 +90,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bounded wait for phase `parity` of the mbarrier that also gives up when
-// *abort becomes non-zero: true when the phase completed.
+// *abort becomes non-zero or after max_ns nanoseconds (or max_iter polls):
+// true when the phase completed.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, uint32_t max_iter,
-                                                   volatile int *abort) {
+                                                   volatile int *abort, uint64_t max_ns = 1000000000ull) {
+  uint64_t t0 = 0;
   for (uint32_t it = 0; it < max_iter; it++) {
     uint32_t done;
     asm volatile(
@@ -91,13 +112,21 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t pari
         : "r"(smem_addr(mbar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 255) == 255 && *abort) return false;
+    if ((it & 255) == 255) {
+      if (*abort) return false;
+      const uint64_t t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > max_ns) return false;
+    }
   }
   return false;
 }
 
-// Bounded wait for phase `parity` of the mbarrier: true when it completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_iter) {
+// Bounded wait for phase `parity` of the mbarrier: true when it completed
+// (gives up after max_ns nanoseconds or max_iter polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_iter,
+                                          uint64_t max_ns = 1000000000ull) {
+  uint64_t t0 = 0;
   for (uint32_t it = 0; it < max_iter; it++) {
     uint32_t done;
     asm volatile(
@@ -108,6 +137,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
         : "r"(smem_addr(mbar)), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 255) {
+      const uint64_t t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > max_ns) return false;
+    }
   }
   return false;
 }
@@ -132,6 +166,74 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
+
+// Each thread of a warp writes 16 consecutive 32-bit columns of its TMEM
+// lane; completion is awaited separately (tmem_st_wait).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Four x16 loads (64 columns) and one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    uint32_t *r = reinterpret_cast<uint32_t *>(v + 16 * q);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr + 16 * q));
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Arrive on the mbarrier and add `bytes` to its expected transaction count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// TMA: box of a 3-D tensor map at coordinates (x, y, z) -> shared memory,
+// completion counted in bytes on the mbarrier.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// Asynchronous global -> shared copies (cp.async, L1-allocating).  Bytes
+// past `valid` bytes of the copy are zero-filled (valid = 0: no global read).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+// 16-byte copy (both addresses 16-byte aligned); bytes past `valid` are zero-filled.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(valid)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Round to TF32 (nearest, ties away): hi part; lo = tf32(x - hi).
 __device__ __forceinline__ float to_tf32(float x) {

@@ -13,6 +13,7 @@ constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
 struct Front {
   int32_t k = 0;        // pivots (columns eliminated here)
   int32_t n = 0;        // order of the frontal matrix: k + b
+  int32_t ld = 0;       // column stride of the factor block: n rounded up to even
   int32_t c0 = 0;       // first pivot in the elimination numbering
   int32_t parent = -1;  // parent front (-1 = root)
   int32_t height = 0;   // 0 = leaf

@@ -21,7 +21,7 @@ TEM_FP32_REFINED = 1
 ERRORS = {-1: "TEM_ERR_ARG", -2: "TEM_ERR_OOM", -3: "TEM_ERR_PIVOT", -4: "TEM_ERR_TIMEOUT",
           -5: "TEM_ERR_CUDA", -6: "TEM_ERR_STATE", -7: "TEM_ERR_MESH"}
 KERNEL_CLASSES = {"update": 0, "panel": 1, "fwd": 2, "bwd": 3, "bwd_upd": 4, "extend_add": 5, "fwd21": 6,
-                  "fwd_sb": 7, "bwd_sb": 8}
+                  "fwd_sb": 7, "bwd_sb": 8, "invert": 9}
 
 # C declarations, in include/tem.h order: name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -57,7 +57,7 @@ class TemStats(ctypes.Structure):
                 ("m", _I32), ("n_times", _I32), ("n_tx", _I32), ("n_rx", _I32),
                 ("precision", _I32), ("refine_steps", _I32), ("last_pivot_front", _I32),
                 ("min_pivot_abs", _D), ("nnz_l11", _I64), ("n_solve_launch", _I64),
-                ("pole_solves", _I64), ("solve_calls", _I64)]
+                ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("reserved_", _I32)]
 
 
 class TemError(RuntimeError):

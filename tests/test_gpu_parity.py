@@ -73,9 +73,11 @@ def c2():
     return Case(2, 202)
 
 
-def _check_case(case, prec, leaf=0):
+def _check_case(case, prec, leaf=0, tensor_cores=True):
     mdl = _model(case.s, case.xi, case.al, prec, leaf)
     try:
+        if not tensor_cores:
+            _tem().tem_set_tensor_cores(mdl.ctx, 0)
         mdl.factor(_cuda(case.m0))
         d = mdl.forward().cpu().numpy()
         assert floored_err(d, case.d).max() <= TOL[prec]
@@ -94,11 +96,18 @@ def test_c1(c1, prec):
     _check_case(c1, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
 @pytest.mark.parametrize("leaf", [8, 33, 300])
-def test_c1_leaf_sizes(c1, leaf):
+def test_c1_leaf_sizes(c1, leaf, prec):
     """Different dissection leaves give ragged fronts (k not a multiple of
-    the 32-wide pivot block, single-front trees)."""
-    _check_case(c1, "fp64", leaf)
+    the 32-wide pivot block or the 64-row product tiles, single-front trees)."""
+    _check_case(c1, prec, leaf)
+
+
+def test_c1_fp32_simt_products(c1):
+    """FP32 mode with the front products on the FP32 pipes instead of the
+    tensor cores."""
+    _check_case(c1, "fp32r", tensor_cores=False)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32r"])
