@@ -101,6 +101,10 @@ struct tem_ctx {
   SimtTask *prod_simt = nullptr;
   void *tmaps = nullptr;                  // FP32: tensor maps of the factor blocks
   void *vmaps = nullptr;                  // FP32: tensor maps of the solve vectors
+  std::vector<int2> gather_h;             // FP32: update-row gather tasks (all levels)
+  int2 *gather = nullptr;
+  int64_t gather_rows = 0;                // rows of the gather buffer (max over levels)
+  void *Xg = nullptr;
   std::vector<InvTask> inv_h;             // FP32: pivot-block inversion tasks
   InvTask *inv = nullptr;
   std::vector<int2> invdiag_h;
@@ -136,6 +140,9 @@ struct tem_ctx {
   // numeric
   void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr, *linv = nullptr;
   void *dinv = nullptr, *yscr = nullptr;   // FP32: inverse pivots, inversion scratch
+  float2 *kdf = nullptr, *mdf = nullptr;   // FP32: K and M values as double-float pairs
+  float4 *xdf = nullptr;                   // FP32: refined iterate as pairs [m][N][nrhs]
+  float *colmax_f = nullptr;               // FP32: column scales of the correction solves
   DevStatus *status = nullptr;
   c128 *g = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *fb = nullptr;
   double *colmax = nullptr;
@@ -229,6 +236,23 @@ struct ProfScope {
 // LevelDev pointers until the lists are uploaded.
 void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
   const auto &S = c->sym;
+  // gather buffer offsets of the update rows of this level's fronts
+  std::map<int32_t, int> gofs;
+  {
+    const size_t beg = c->gather_h.size();
+    int64_t rows = 0;
+    for (int32_t fi : L.fronts) {
+      const Front &F = S.fronts[fi];
+      gofs[fi] = (int)rows;
+      if (F.k > 0 && F.n > F.k) {
+        c->gather_h.push_back(make_int2(fi, (int)rows));
+        rows += F.n - F.k;
+      }
+    }
+    c->gather_rows = std::max(c->gather_rows, rows);
+    lv.n_gather = int(c->gather_h.size() - beg);
+    lv.gather = (const int2 *)(uintptr_t)beg;
+  }
   for (int mode = 0; mode < PM_COUNT; mode++) {
     const size_t beg = c->prod_h.size();
     for (int32_t fi : L.fronts) {
@@ -268,9 +292,13 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
           for (int R = r0; R < F.n; R += 64)
             push(R, 0, k, std::min(64, F.n - R), F.c0, (int)F.rows_off + R - k, std::max(0, k - R), 0);
       } else if (mode == PM_BWD21)
-        for (int cb = 0; cb < k; cb += 64)
+        for (int cb = 0; cb < k; cb += 64) {
+          // B rows: the SIMT kernel gathers rows[rows_off + kk - kfirst], the
+          // tensor-core kernel reads the level's gather buffer at its offset
           push(r0, cb, b == 0 ? 0 : F.n - r0, std::min(64, k - cb), (int)F.rows_off - (k - r0), F.c0 + cb, 0,
                k - r0);
+          c->prod_h.back().bbase = gofs[fi] - (k - r0);
+        }
       else
         for (int cb = 0; cb < k; cb += 64)
           push(cb, cb, k - cb, std::min(64, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
@@ -331,6 +359,8 @@ void build_steps(tem_ctx *c) {
   c->sbb_h.clear();
   c->prod_h.clear();
   c->prod_simt_h.clear();
+  c->gather_h.clear();
+  c->gather_rows = 0;
   c->inv_h.clear();
   c->invdiag_h.clear();
   c->yscr_stride = 0;
@@ -462,6 +492,8 @@ SolvePlan<R> solve_plan(tem_ctx *c) {
   P.dinv = (const cx<R> *)c->dinv;
   P.tmaps = c->tmaps;
   P.vmaps = c->vmaps;
+  P.Xg = (cx<R> *)c->Xg;
+  P.gstride = std::max<int64_t>(1, c->gather_rows) * c->n_tx;
   P.N = c->mesh.N;
   return P;
 }
@@ -495,19 +527,24 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
     launch_accumulate<double>((const c128 *)c->X, nullptr, x, m, nullptr, N, nx, false, s);
     return TEM_OK;
   }
-  launch_rhs_to_work<float>(b, bstride, (c64 *)c->Y, c->colmax, m, nullptr, N, nx, true, s);
+  // FP32 mode: b and the iterate as double-float pairs, corrections in FP32
+  float4 *bdf = reinterpret_cast<float4 *>(c->r);   // pairs of b (shared when bstride == 0)
+  const int64_t bsd = bstride ? N * nx : 0;
+  launch_split_cx(b, bdf, (bstride ? int64_t(m) : int64_t(1)) * N * nx, s);
+  c64 *Y = (c64 *)c->Y;
+  launch_scale_to_work<float4>(bdf, bsd, Y, c->colmax_f, m, nullptr, N, nx, s);
   sweeps<float>(c, nullptr, m);
-  launch_accumulate<float>((const c64 *)c->X, c->colmax, x, m, nullptr, N, nx, false, s);
+  launch_accumulate_df((const c64 *)c->X, c->colmax_f, c->xdf, m, nullptr, N, nx, false, s);
   const int *pm = nullptr;
   int np = m;
   for (int it = 0; it < c->refine; it++) {
-    launch_residual(c->rp, c->ci, c->kval, c->mval, c->xi, b, bstride, x, c->r, np, pm, N, nx, s);
-    launch_rhs_to_work<float>(c->r, N * nx, (c64 *)c->Y, c->colmax, np, pm, N, nx, true, s);
+    launch_residual_df(c->rp, c->ci, c->kdf, c->mdf, c->xi, bdf, bsd, c->xdf, Y, np, pm, N, nx, s);
+    launch_scale_to_work<c64>(Y, N * nx, Y, c->colmax_f, np, pm, N, nx, s);
     sweeps<float>(c, pm, np);
-    launch_accumulate<float>((const c64 *)c->X, c->colmax, x, np, pm, N, nx, true, s);
+    launch_accumulate_df((const c64 *)c->X, c->colmax_f, c->xdf, np, pm, N, nx, true, s);
     if (c->refine_tol <= 0 || it + 1 == c->refine) continue;
     CK(cudaMemsetAsync(c->prog, 0, sizeof(double) * 2 * m, s));
-    launch_progress<float>((const c64 *)c->X, c->colmax, x, c->earth, c->prog, c->prog + m, np, pm, N, nx, s);
+    launch_progress_df((const c64 *)c->X, c->colmax_f, c->xdf, c->earth, c->prog, c->prog + m, np, pm, N, nx, s);
     std::vector<double> pr(2 * m);
     std::vector<int> keep;
     CK(cudaMemcpyAsync(pr.data(), c->prog, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s));
@@ -522,6 +559,7 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
     pm = c->pmap;
     np = (int)keep.size();
   }
+  launch_join_cx(c->xdf, x, int64_t(m) * N * nx, s);
   return TEM_OK;
 }
 
@@ -552,6 +590,10 @@ int ensure_numeric(tem_ctx *c) {
   if (c->precision != TEM_FP64) {
     TRY(dalloc(c, &c->r, size_t(m) * N * nx));
     TRY(dalloc(c, (c64 **)&c->dinv, size_t(m) * N));
+    TRY(dalloc(c, &c->kdf, c->mesh.kval.size()));
+    TRY(dalloc(c, &c->mdf, c->mesh.kval.size()));
+    TRY(dalloc(c, &c->xdf, size_t(m) * N * nx));
+    TRY(dalloc(c, &c->colmax_f, size_t(m) * nx));
     TRY(dalloc(c, (c64 **)&c->yscr, size_t(m) * std::max<int64_t>(1, c->yscr_stride)));
     std::vector<FrontGeom> geo(c->sym.fronts.size());
     for (size_t i = 0; i < geo.size(); i++) {
@@ -561,7 +603,11 @@ int ensure_numeric(tem_ctx *c) {
     const std::string e = build_tensor_maps(geo, (const c64 *)c->L, c->sym.ltotal, m, &c->tmaps);
     if (!e.empty()) return fail(c, TEM_ERR_CUDA, e);
     c->allocs.push_back(c->tmaps);
-    const std::string e2 = build_vector_maps((const c64 *)c->Y, (const c64 *)c->X, N, nx, m, &c->vmaps);
+    TRY(dalloc(c, (c64 **)&c->Xg, size_t(m) * std::max<int64_t>(1, c->gather_rows) * nx));
+    CK(cudaMemset(c->Xg, 0, size_t(m) * std::max<int64_t>(1, c->gather_rows) * nx * sizeof(c64)));
+    const std::string e2 = build_vector_maps({VecBuf{(const c64 *)c->Y, N}, VecBuf{(const c64 *)c->X, N},
+                                              VecBuf{(const c64 *)c->Xg, std::max<int64_t>(1, c->gather_rows)}},
+                                             nx, m, &c->vmaps);
     if (!e2.empty()) return fail(c, TEM_ERR_CUDA, e2);
     if (c->vmaps) c->allocs.push_back(c->vmaps);
     TRY(dalloc(c, &c->mval_fact, size_t(m) * c->mesh.kval.size()));
@@ -679,6 +725,7 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->sbb, c->sbb_h));
   TRY(upload(c, &c->prod, c->prod_h));
   TRY(upload(c, &c->prod_simt, c->prod_simt_h));
+  TRY(upload(c, &c->gather, c->gather_h));
   TRY(upload(c, &c->inv, c->inv_h));
   TRY(upload(c, &c->invdiag, c->invdiag_h));
   for (LevelDev &lv : c->levels) {
@@ -688,6 +735,7 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
       lv.prod[mode] = c->prod + (uintptr_t)lv.prod[mode];
       lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
     }
+    lv.gather = c->gather + (uintptr_t)lv.gather;
     lv.inv_diag = c->invdiag + (uintptr_t)lv.inv_diag;
     for (auto &st : lv.inv) st.tasks = c->inv + (uintptr_t)st.tasks;
     for (auto &sb : lv.sb) {
@@ -766,9 +814,13 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
     launch_sigma(log_sigma, c->ptet, M.P, c->sigma, s);
   }
   launch_mvals(c->mc_ptr, c->mc_idx, c->sigma, c->me1, (int64_t)M.kval.size(), c->mval, s);
-  if (c->mval_fact)
+  if (c->mval_fact) {
     launch_mvals_floor(c->mc_ptr, c->mc_idx, c->sigma, c->tetfloor, c->me1, c->xi, c->floor_tau, c->m,
                        (int64_t)M.kval.size(), c->mval_fact, s);
+    // the refinement's residual uses K and the true M as double-float pairs
+    launch_split_real(c->kval, c->kdf, (int64_t)M.kval.size(), s);
+    launch_split_real(c->mval, c->mdf, (int64_t)M.kval.size(), s);
+  }
   DevStatus init{};
   init.pivot_fail = 0;
   init.pivot_front = -1;

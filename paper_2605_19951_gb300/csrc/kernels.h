@@ -127,6 +127,10 @@ struct LevelDev {
   std::vector<InvStage> inv;
   const int2 *inv_diag = nullptr;   // (front, 32-block) of every diagonal block
   int n_inv_diag = 0;
+  // FP32 backward: (front, first row) of each front's update rows in the
+  // gather buffer, for the fronts with update rows
+  const int2 *gather = nullptr;
+  int n_gather = 0;
 };
 
 template <typename R>
@@ -182,7 +186,9 @@ struct SolvePlan {
   bool use_tc = false;        // FP32: front products on the tensor cores
   const cx<R> *dinv = nullptr;  // FP32: [m][N] inverse pivots
   const void *tmaps = nullptr;  // FP32: 4 tensor maps per front (one per product mode)
-  const void *vmaps = nullptr;  // FP32: tensor maps of Y and X (nullptr for an odd nrhs)
+  const void *vmaps = nullptr;  // FP32: tensor maps of Y, X and Xg (nullptr for an odd nrhs)
+  cx<R> *Xg = nullptr;          // FP32: [m][gather rows][nrhs] update rows of X, one level at a time
+  int64_t gstride = 0;          // pole stride of Xg
   int64_t N = 0;
   DevStatus *status = nullptr;
   void forward_level(const LevelDev &lv, cudaStream_t s);
@@ -201,7 +207,12 @@ struct FrontGeom {
 };
 std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
                               void **out);
-std::string build_vector_maps(const c64 *Y, const c64 *X, int64_t N, int nrhs, int m, void **out);
+// Maps over [pole][rows][nrhs] complex vectors (pole stride rows * nrhs), in order.
+struct VecBuf {
+  const c64 *base;
+  int64_t rows;
+};
+std::string build_vector_maps(const std::vector<VecBuf> &bufs, int nrhs, int m, void **out);
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s);
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
@@ -230,6 +241,23 @@ void launch_residual(const int64_t *rp, const int32_t *ci, const double *kv, con
 template <typename R>
 void launch_progress(const cx<R> *X, const double *colmax, const c128 *x, const uint8_t *mask, double *num,
                      double *den, int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s);
+// ---- refine.cu: FP32-mode refinement in double-float pairs ----
+void launch_split_real(const double *v, float2 *out, int64_t n, cudaStream_t s);   // v -> (hi, lo)
+void launch_split_cx(const c128 *v, float4 *out, int64_t n, cudaStream_t s);       // (re.hi, re.lo, im.hi, im.lo)
+void launch_join_cx(const float4 *v, c128 *out, int64_t n, cudaStream_t s);        // hi + lo in FP64
+// r (FP32) = b - K x + xi_p (M x) with b, x, K, M as pairs
+void launch_residual_df(const int64_t *rp, const int32_t *ci, const float2 *kdf, const float2 *mdf,
+                        const double2 *xi, const float4 *bdf, int64_t bstride, const float4 *xdf, c64 *r, int np,
+                        const int *pmap, int64_t N, int nrhs, cudaStream_t s);
+// colmax (FP32) = column maxima of v, Y = v / colmax; v complex FP32 or pairs (hi parts)
+template <typename T>
+void launch_scale_to_work(const T *v, int64_t vstride, c64 *Y, float *colmax, int np, const int *pmap, int64_t N,
+                          int nrhs, cudaStream_t s);
+// x (+)= colmax X in pairs
+void launch_accumulate_df(const c64 *X, const float *colmax, float4 *x, int np, const int *pmap, int64_t N, int nrhs,
+                          bool add, cudaStream_t s);
+void launch_progress_df(const c64 *X, const float *colmax, const float4 *x, const uint8_t *mask, double *num,
+                        double *den, int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s);
 // F (real [N][nrhs]) -> c128 b
 void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s);
 // d[x][r][j] = 2 Re sum_p alpha_pj coef_p (Q y_p)[r][x]; coef = 1 (forward) or xi_p

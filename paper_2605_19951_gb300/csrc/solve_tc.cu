@@ -43,11 +43,11 @@
 namespace tem {
 
 namespace {
-constexpr int TKC = 32;       // inner dimension per chunk (four MMA k-steps)
-constexpr int NRAW = 3;       // raw ring depth (NRAW - 1 chunks in flight)
-constexpr int NST = 2;        // TMEM A stages / shared B stages
+constexpr int TKC = 16;       // inner dimension per chunk (two MMA k-steps)
+constexpr int NRAW = 6;       // raw ring depth (NRAW - 1 chunks in flight)
+constexpr int NST = 4;        // TMEM A stages / shared B stages
 constexpr int NTHR = 288;     // 4 producer + 4 epilogue + 1 MMA warp
-constexpr int RAWA = 4096;    // floats per raw A slot: 32 x 128 (column-major) or 2 x 64 x 32 (row-major, 128B swizzle)
+constexpr int RAWA = 2048;    // floats per raw A slot: 16 x 128 (column-major) or 64 x 32 (row-major, 128B swizzle)
 constexpr int RAWB = TKC * 64;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr uint32_t COL_A = 128;   // A stages after the two 64-column accumulators
@@ -55,18 +55,19 @@ constexpr uint32_t kWaitIter = 1u << 26;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct TcShared {
-  float rawA[NRAW][RAWA];         // 16 KB slots, 1024-byte aligned (swizzle atoms)
+  float rawA[NRAW][RAWA];         // 8 KB slots, 1024-byte aligned (swizzle atoms)
   float rawB[NRAW][RAWB];
   float Bs[NST][2][64 * TKC];     // hi, lo (K-major, no swizzle)
   uint64_t full[NST], empty[NST], accf[2], acce[2], fin;
   uint64_t rawfull[NRAW], rawempty[NRAW];
-  int kval[NRAW];                 // valid inner indices of the chunk in each raw slot
+  int kval[NRAW], kfst[NRAW];     // valid inner indices [kfst, kval) of the chunk in each raw slot
   uint32_t tmem;
   int abort;
 };
 constexpr size_t kTcSmem = sizeof(TcShared) + 1024;   // + alignment slack of the dynamic base
 
 __host__ __device__ constexpr bool row_major(int mode) { return mode == PM_BWD21 || mode == PM_TRI_B; }
+// (the SIMT kernel gathers BWD21's B rows itself; the tensor-core kernel reads them pre-gathered)
 __host__ __device__ constexpr bool gathered_b(int mode) { return mode == PM_BWD21; }
 
 struct ProdArgs {
@@ -82,7 +83,8 @@ struct ProdArgs {
   const CUtensorMap *tmaps;
   const CUtensorMap *bmap;   // contiguous B rows by TMA (nullptr: cp.async)
   int64_t N;
-  int64_t vstride;
+  int64_t vstride;   // pole stride of the outputs (and of B, except BWD21 on the tensor cores)
+  int64_t bstride;   // pole stride of the B rows
   int nrhs, nchunk, np;
   const int *pmap;
   DevStatus *st;
@@ -154,116 +156,69 @@ template <int MODE>
 struct Fetch {
   Item cur, nxt;
   int j = 0, c = 0;
-  int32_t ridx[8];   // gathered B rows 8w..8w+7 of the current chunk (BWD21)
 
-  __device__ void prep(const ProdArgs &a, int tid) {
-    if (!gathered_b(MODE) || !cur.valid || c >= cur.nch) return;
-    const int kb = (tid >> 5) * 8, k0 = c * TKC;
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const int kk = k0 + kb + q;
-      ridx[q] = (kk < cur.t.kdim && kk >= cur.t.kfirst) ? __ldg(a.rows + cur.t.bbase + kk) : 0;
-    }
-  }
   // move on to the next item that has chunks (the others need no data)
-  __device__ void settle(const ProdArgs &a, int tid) {
+  __device__ void settle(const ProdArgs &a) {
     while (cur.valid && c >= cur.nch) {
       cur = nxt;
       j++;
       c = 0;
       nxt = load_item(a, j + 1);
     }
-    prep(a, tid);
   }
-  __device__ void start(const ProdArgs &a, int tid) {
+  __device__ void start(const ProdArgs &a) {
     cur = load_item(a, 0);
     nxt = load_item(a, 1);
-    settle(a, tid);
+    settle(a);
   }
   __device__ bool active() const { return cur.valid; }
 
   // Issue the loads of the current chunk (global chunk number `gc`) into raw
-  // slot gc % NRAW, then advance: A (and contiguous B rows) by TMA from
-  // thread 0 once every producer thread has released the slot; gathered B
-  // rows 8w..8w+7 by warp w.
+  // slot gc % NRAW, then advance.  A and the B rows come by TMA from thread 0
+  // once every producer thread has released the slot; with an odd number of
+  // right-hand sides (no B map) warp w copies B rows 4w..4w+3 by cp.async.
   __device__ bool issue(const ProdArgs &a, TcShared &sh, int gc, int tid) {
     const int slot = gc % NRAW;
     const int k0 = c * TKC;
     const TcTask &t = cur.t;
-    const void *dummy = a.L;
-    const int w = tid >> 5, l = tid & 31;
+    const bool tma_b = a.bmap != nullptr;
     bool ok = true;
-    const bool tma_b = !gathered_b(MODE) && a.bmap != nullptr;
     if (tid == 0) {
       if (gc >= NRAW) ok = wait_bar(sh, &sh.rawempty[slot], ((gc / NRAW) - 1) & 1, a.st);
       if (ok) {
         sh.kval[slot] = min(TKC, t.kdim - k0);
+        sh.kfst[slot] = max(0, int(t.kfirst) - k0);
         tc::mbar_arrive_expect_tx(&sh.rawfull[slot], RAWA * 4 + (tma_b ? RAWB * 4 : 0));
-        const CUtensorMap *m = a.tmaps + t.map;
-        if (!row_major(MODE)) {
-          tc::tma_load_3d(sh.rawA[slot], m, t.x0, t.y0 + k0, cur.p, &sh.rawfull[slot]);
-        } else {
-          tc::tma_load_3d(sh.rawA[slot], m, t.x0 + 2 * k0, t.y0, cur.p, &sh.rawfull[slot]);
-          tc::tma_load_3d(sh.rawA[slot] + RAWA / 2, m, t.x0 + 2 * k0 + 32, t.y0, cur.p, &sh.rawfull[slot]);
-        }
+        const bool colmaj = !row_major(MODE);
+        tc::tma_load_3d(sh.rawA[slot], a.tmaps + t.map, colmaj ? t.x0 : t.x0 + 2 * k0, colmaj ? t.y0 + k0 : t.y0,
+                        cur.p, &sh.rawfull[slot]);
         if (tma_b) tc::tma_load_3d(sh.rawB[slot], a.bmap, 64 * cur.ch, t.bbase + k0, cur.p, &sh.rawfull[slot]);
       }
     }
     if (!tma_b) {
-      // B rows 8w..8w+7: 32 complex each
+      const int w = tid >> 5, l = tid & 31;
       const int ncols = min(32, a.nrhs - cur.ch * 32);
-      const c64 *bp = a.B + int64_t(cur.p) * a.vstride + cur.ch * 32;
+      const c64 *bp = a.B + int64_t(cur.p) * a.bstride + cur.ch * 32;
       float *rb = sh.rawB[slot];
-      if ((a.nrhs & 1) == 0) {
 #pragma unroll
-        for (int q4 = 0; q4 < 4; q4++) {
-          const int q = l + 32 * q4;
-          const int r = q >> 4, pc = q & 15;   // r = 2 q4 + (l >> 4)
-          const int kk = k0 + 8 * w + r;
-          const bool rok = kk < t.kdim && kk >= t.kfirst;
-          const int nv = rok ? max(0, min(2, ncols - 2 * pc)) : 0;
-          const int32_t gr = (l >> 4) ? ridx[2 * q4 + 1] : ridx[2 * q4];
-          const int64_t row = gathered_b(MODE) ? int64_t(gr) : int64_t(t.bbase) + kk;
-          const void *src = nv ? static_cast<const void *>(bp + row * a.nrhs + 2 * pc) : dummy;
-          tc::cp_async16(rb + (8 * w + r) * 64 + 4 * pc, src, 8 * nv);
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < 8; r++) {
-          const int kk = k0 + 8 * w + r;
-          const bool rok = kk < t.kdim && kk >= t.kfirst && l < ncols;
-          const int64_t row = gathered_b(MODE) ? int64_t(ridx[r]) : int64_t(t.bbase) + kk;
-          const void *src = rok ? static_cast<const void *>(bp + row * a.nrhs + l) : dummy;
-          tc::cp_async8(rb + (8 * w + r) * 64 + 2 * l, src, rok);
-        }
+      for (int r = 0; r < 4; r++) {
+        const int kk = k0 + 4 * w + r;
+        const bool rok = kk < t.kdim && kk >= t.kfirst && l < ncols;
+        const void *src = rok ? static_cast<const void *>(bp + (int64_t(t.bbase) + kk) * a.nrhs + l)
+                              : static_cast<const void *>(a.L);
+        tc::cp_async8(rb + (4 * w + r) * 64 + 2 * l, src, rok);
       }
     }
     c++;
-    settle(a, tid);
+    settle(a);
     return ok;
   }
 };
 
-// A values kk0..kk0+15 of row `tid` of the chunk in raw slot `slot`.
-template <int MODE>
-__device__ __forceinline__ void load_a16(const TcShared &sh, int slot, int tid, int kk0, float *v) {
-  if (!row_major(MODE)) {
-#pragma unroll
-    for (int kk = 0; kk < 16; kk++) v[kk] = sh.rawA[slot][(kk0 + kk) * 128 + tid];
-  } else {
-    // row c of a 64 x 32-float box (16 complex of the inner dimension), 16-byte
-    // chunks swizzled by c & 7; inner indices 16..31 are in the second box
-    const int cc = tid >> 1, sw = cc & 7;
-    const float *src = sh.rawA[slot] + (kk0 >> 4) * (RAWA / 2) + cc * 32 + (tid & 1);
-#pragma unroll
-    for (int e = 0; e < 16; e++) v[e] = src[(((e >> 1) ^ sw) << 2) + 2 * (e & 1)];
-  }
-}
-
 template <int MODE>
 __device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
   Fetch<MODE> f;
-  f.start(a, tid);
+  f.start(a);
   int issued = 0;
   bool ok = true;
   // prologue: NRAW - 1 chunks in flight
@@ -281,17 +236,41 @@ __device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
   int pend = -1;   // stage whose TMEM / shared stores are in flight, signalled one chunk later
 #pragma unroll 1
   for (; g < issued && ok; g++) {
-    __syncwarp();   // every lane has read the B slot about to be refilled
+    __syncwarp();   // every lane has read the B slot a cp.async is about to refill
     if (f.active()) {
       ok = f.issue(a, sh, issued, tid);
       issued++;
     }
     tc::cp_async_commit();
-    tc::cp_async_wait<NRAW - 1>();        // gathered B of chunk g has landed (this warp's copies)
+    tc::cp_async_wait<NRAW - 1>();        // cp.async B of chunk g has landed (this warp's copies)
     __syncwarp();
     const int slot = g % NRAW;
     ok = wait_bar(sh, &sh.rawfull[slot], (g / NRAW) & 1, a.st) && ok;   // TMA loads of chunk g
     if (!__all_sync(kFull, ok)) break;
+    // copy the chunk into registers and release the slot at once: A row tid
+    // (16 values) and B columns l, l + 32 of rows 4w..4w+3, zero outside [kfst, kval)
+    float v[TKC], b0[4], b1[4];
+    if (!row_major(MODE)) {
+#pragma unroll
+      for (int kk = 0; kk < TKC; kk++) v[kk] = sh.rawA[slot][kk * 128 + tid];
+    } else {
+      // row c of the 64 x 32-float box, 16-byte chunks swizzled by c & 7
+      const int cc = tid >> 1, sw = cc & 7;
+      const float *src = sh.rawA[slot] + cc * 32 + (tid & 1);
+#pragma unroll
+      for (int e = 0; e < TKC; e++) v[e] = src[(((e >> 1) ^ sw) << 2) + 2 * (e & 1)];
+    }
+    {
+      const int kv = sh.kval[slot], kf = sh.kfst[slot];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int r = 4 * w + q;
+        const bool in = r < kv && r >= kf;
+        b0[q] = in ? sh.rawB[slot][r * 64 + l] : 0.f;
+        b1[q] = in ? sh.rawB[slot][r * 64 + 32 + l] : 0.f;
+      }
+    }
+    tc::mbar_arrive(&sh.rawempty[slot]);
     // the previous chunk's stores had this chunk's loads to land
     if (pend >= 0) {
       tc::tmem_st_wait();
@@ -305,30 +284,20 @@ __device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
     if (use > 0) ok = wait_bar(sh, &sh.empty[s], (use - 1) & 1, a.st);
     if (!__all_sync(kFull, ok)) break;
     tc::fence_after();
-    const uint32_t ta = sh.tmem + (uint32_t(w * 32) << 16) + COL_A + 64 * s;
+    const uint32_t ta = sh.tmem + (uint32_t(w * 32) << 16) + COL_A + 32 * s;
+    {
+      float lo[TKC];
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
-      float v[16], hi[16], lo[16];
-      load_a16<MODE>(sh, slot, tid, 16 * half, v);
-#pragma unroll
-      for (int kk = 0; kk < 16; kk++) {
-        hi[kk] = tc::to_tf32(v[kk]);
-        lo[kk] = tc::to_tf32(v[kk] - hi[kk]);
+      for (int kk = 0; kk < TKC; kk++) {
+        const float h = tc::to_tf32(v[kk]);
+        lo[kk] = tc::to_tf32(v[kk] - h);
+        v[kk] = h;
       }
-      tc::tmem_st16(ta + 16 * half, hi);
-      tc::tmem_st16(ta + 32 + 16 * half, lo);
+      tc::tmem_st16(ta, v);
+      tc::tmem_st16(ta + 16, lo);
     }
-    // B: columns l and l + 32 of rows 8w..8w+7 (rows past the inner dimension are zero)
-    const int kv = sh.kval[slot];
-#pragma unroll
-    for (int col = 0; col < 64; col += 32) {
-      float bv[8];
-#pragma unroll
-      for (int q = 0; q < 8; q++) bv[q] = (8 * w + q < kv) ? sh.rawB[slot][(8 * w + q) * 64 + col + l] : 0.f;
-      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(col + l, 8 * w, 64), bv);
-      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(col + l, 8 * w + 4, 64), bv + 4);
-    }
-    tc::mbar_arrive(&sh.rawempty[slot]);   // every read of this raw slot is done
+    split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l, 4 * w, 64), b0);
+    split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l + 32, 4 * w, 64), b1);
     pend = s;
     if (__any_sync(kFull, aborted(sh))) break;
   }
@@ -371,7 +340,7 @@ __device__ void mma_issuer(const ProdArgs &a, TcShared &sh) {
       tc::fence_after();
 #pragma unroll
       for (int ks = 0; ks < TKC / 8; ks++) {
-        const uint32_t ah = sh.tmem + COL_A + 64 * s + 8 * ks, al = ah + 32;
+        const uint32_t ah = sh.tmem + COL_A + 32 * s + 8 * ks, al = ah + 16;
         const uint64_t bh = tc::desc_kmajor(tc::smem_addr(&sh.Bs[s][0][ks * 64 * 8]), 128, 256);
         const uint64_t bl = tc::desc_kmajor(tc::smem_addr(&sh.Bs[s][1][ks * 64 * 8]), 128, 256);
         tc::mma_tf32_ts(d, ah, bh, idesc, c > 0 || ks > 0);
@@ -578,6 +547,24 @@ __global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtT
   }
 }
 
+// Xg[p][g0 + i] = X[p][rows_i] for the update rows of each front of a level
+// (contiguous B rows for the backward L21 product); one CTA per (front, pole).
+__global__ void k_gather_upd(const c64 *__restrict__ X, int64_t vstride, c64 *__restrict__ Xg, int64_t gstride,
+                             const FrontDev *__restrict__ F, const int32_t *__restrict__ rows,
+                             const int2 *__restrict__ tasks, int nrhs, const int *__restrict__ pmap) {
+  const int2 t = tasks[blockIdx.x];
+  const int p = pole_of(blockIdx.y, pmap);
+  const FrontDev f = F[t.x];
+  const int b = f.n - f.k;
+  const int32_t *ur = rows + f.rows_off;
+  const c64 *xp = X + p * vstride;
+  c64 *gp = Xg + p * gstride + int64_t(t.y) * nrhs;
+  for (int64_t e = threadIdx.x; e < int64_t(b) * nrhs; e += blockDim.x) {
+    const int64_t i = e / nrhs, j = e - i * nrhs;
+    gp[e] = xp[int64_t(ur[i]) * nrhs + j];
+  }
+}
+
 namespace {
 int g_tc_occupancy = 0;
 
@@ -625,6 +612,7 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
   a.rows = P.rows;
   a.N = P.N;
   a.vstride = P.vstride;
+  a.bstride = P.vstride;
   a.nrhs = P.nrhs;
   a.nchunk = (P.nrhs + 31) / 32;
   a.np = P.np;
@@ -652,6 +640,17 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
       a.B = P.X;
       a.out = P.Y;
       a.xaux = P.X;
+      if (P.use_tc) {
+        // the tensor-core kernel reads the update rows pre-gathered
+        if (lv.n_gather > 0) {
+          tem::count_launch();
+          k_gather_upd<<<dim3(lv.n_gather, P.np), 256, 0, s>>>(P.X, P.vstride, P.Xg, P.gstride, P.F, P.rows,
+                                                               lv.gather, P.nrhs, P.pmap);
+        }
+        a.B = P.Xg;
+        a.bstride = P.gstride;
+        a.bmap = vm ? vm + 2 : nullptr;
+      }
       run_mode<PM_BWD21>(a, lv.prod_simt[mode], P.use_tc, s);
       break;
     default:
@@ -672,9 +671,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // Per front, four maps over its factor block viewed as floats: dim 0 runs
 // along a column (2 floats per complex entry; rows k..n-1 excluded for the
 // pivot-block maps 0 and 3), dim 1 over the k columns, dim 2 over the poles.
-// Maps 0/1 (column-major tiles) load 32 columns x 64 complex rows; maps 2/3
+// Maps 0/1 (column-major tiles) load 16 columns x 64 complex rows; maps 2/3
 // (row-major tiles) load 64 columns x 16 complex rows with the 128-byte
-// swizzle (two boxes per chunk of 32).  Entries outside the dims read as zero.
+// swizzle.  Entries outside the dims read as zero.
 std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
                               void **out) {
   *out = nullptr;
@@ -698,7 +697,7 @@ std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L
       const bool colmaj = !row_major(kind);
       const cuuint64_t dims[3] = {cuuint64_t(2) * (tri ? f.k : f.n), cuuint64_t(f.k), cuuint64_t(m)};
       const cuuint64_t strides[2] = {cuuint64_t(f.ld) * sizeof(c64), cuuint64_t(lstride) * sizeof(c64)};
-      const cuuint32_t box[3] = {colmaj ? 128u : 32u, colmaj ? 32u : 64u, 1u};
+      const cuuint32_t box[3] = {colmaj ? 128u : 32u, colmaj ? 16u : 64u, 1u};
       const cuuint32_t estr[3] = {1, 1, 1};
       const CUresult r =
           encode(&maps[4 * i + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(L + f.lofs), dims,
@@ -719,10 +718,10 @@ std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L
 }
 
 // Maps over the two solve vectors Y, X ([pole][N][nrhs] complex) viewed as
-// floats: rows of 2 nrhs floats, N rows, m poles; a box is 32 rows x 32
+// floats: rows of 2 nrhs floats, R rows, m poles; a box is 16 rows x 32
 // right-hand sides.  Needs an even nrhs (16-byte row stride); *out = nullptr
 // otherwise (the kernels then copy B rows with cp.async).
-std::string build_vector_maps(const c64 *Y, const c64 *X, int64_t N, int nrhs, int m, void **out) {
+std::string build_vector_maps(const std::vector<VecBuf> &bufs, int nrhs, int m, void **out) {
   *out = nullptr;
   if (nrhs & 1) return "";
   EncodeTiledFn encode = nullptr;
@@ -735,21 +734,22 @@ std::string build_vector_maps(const c64 *Y, const c64 *X, int64_t N, int nrhs, i
       return "cuTensorMapEncodeTiled is not available from the driver";
     encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
-  CUtensorMap maps[2];
-  const c64 *bases[2] = {Y, X};
-  for (int i = 0; i < 2; i++) {
-    const cuuint64_t dims[3] = {cuuint64_t(2) * nrhs, cuuint64_t(N), cuuint64_t(m)};
-    const cuuint64_t strides[2] = {cuuint64_t(nrhs) * sizeof(c64), cuuint64_t(N) * nrhs * sizeof(c64)};
-    const cuuint32_t box[3] = {64u, 32u, 1u};
+  std::vector<CUtensorMap> maps(bufs.size());
+  for (size_t i = 0; i < bufs.size(); i++) {
+    const int64_t rows = bufs[i].rows > 0 ? bufs[i].rows : 1;
+    const cuuint64_t dims[3] = {cuuint64_t(2) * nrhs, cuuint64_t(rows), cuuint64_t(m)};
+    const cuuint64_t strides[2] = {cuuint64_t(nrhs) * sizeof(c64), cuuint64_t(rows) * nrhs * sizeof(c64)};
+    const cuuint32_t box[3] = {64u, 16u, 1u};
     const cuuint32_t estr[3] = {1, 1, 1};
-    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(bases[i]), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(bufs[i].base), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return "cuTensorMapEncodeTiled failed for a solve vector";
   }
   void *d = nullptr;
-  if (cudaMalloc(&d, sizeof(maps)) != cudaSuccess) return "cudaMalloc of tensor maps failed";
-  if (cudaMemcpy(d, maps, sizeof(maps), cudaMemcpyHostToDevice) != cudaSuccess) {
+  const size_t bytes = maps.size() * sizeof(CUtensorMap);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return "cudaMalloc of tensor maps failed";
+  if (cudaMemcpy(d, maps.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(d);
     return "copy of tensor maps failed";
   }
