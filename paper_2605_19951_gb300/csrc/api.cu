@@ -254,58 +254,69 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
     lv.gather = (const int2 *)(uintptr_t)beg;
   }
   for (int mode = 0; mode < PM_COUNT; mode++) {
-    const size_t beg = c->prod_h.size();
+    const size_t beg = c->prod_h.size(), beg_s = c->prod_simt_h.size();
     for (int32_t fi : L.fronts) {
       const Front &F = S.fronts[fi];
       const int k = F.k, b = F.n - F.k;
       if (k <= 0) continue;
-      // tile with A origin (row x, column y) of the front block
-      auto push = [&](int row, int col, int kdim, int mrows, int bbase, int obase, int mfirst, int kfirst) {
-        TcTask t;
-        t.map = 4 * fi + mode;
-        t.x0 = 2 * row;
-        t.y0 = col;
-        t.kdim = kdim;
-        t.mrows = mrows;
-        t.bbase = bbase;
-        t.obase = obase;
-        t.mfirst = int16_t(mfirst);
-        t.kfirst = int16_t(kfirst);
-        c->prod_h.push_back(t);
-        SimtTask u;
-        u.aoff = F.lofs + int64_t(col) * F.ld + row;
-        u.lda = F.ld;
-        u.kdim = kdim;
-        u.mrows = mrows;
-        u.bbase = bbase;
-        u.obase = obase;
-        u.mfirst = int16_t(mfirst);
-        u.kfirst = int16_t(kfirst);
-        c->prod_simt_h.push_back(u);
+      // tile with A origin (row x, column y) of the front block, for the
+      // tensor-core kernel (tc) and / or the SIMT kernel (simt)
+      auto push = [&](bool tc, bool simt, int row, int col, int kdim, int mrows, int bbase, int obase, int mfirst,
+                      int kfirst) {
+        if (tc) {
+          TcTask t;
+          t.map = 4 * fi + mode;
+          t.x0 = 2 * row;
+          t.y0 = col;
+          t.kdim = kdim;
+          t.mrows = mrows;
+          t.bbase = bbase;
+          t.obase = obase;
+          t.mfirst = int16_t(mfirst);
+          t.kfirst = int16_t(kfirst);
+          c->prod_h.push_back(t);
+        }
+        if (simt) {
+          SimtTask u;
+          u.aoff = F.lofs + int64_t(col) * F.ld + row;
+          u.lda = F.ld;
+          u.kdim = kdim;
+          u.mrows = mrows;
+          u.bbase = bbase;
+          u.obase = obase;
+          u.mfirst = int16_t(mfirst);
+          u.kfirst = int16_t(kfirst);
+          c->prod_simt_h.push_back(u);
+        }
       };
       const int r0 = k & ~1;   // even origin of the update rows (row k - 1 is padding when k is odd)
-      if (mode == PM_TRI_F)
+      if (mode == PM_TRI_F) {
         for (int i0 = 0; i0 < k; i0 += 64)
-          push(i0, 0, std::min(k, i0 + 64), std::min(64, k - i0), F.c0, F.c0 + i0, 0, 0);
-      else if (mode == PM_FWD21) {
+          push(true, true, i0, 0, std::min(k, i0 + 64), std::min(64, k - i0), F.c0, F.c0 + i0, 0, 0);
+      } else if (mode == PM_FWD21) {
         if (b > 0)
           for (int R = r0; R < F.n; R += 64)
-            push(R, 0, k, std::min(64, F.n - R), F.c0, (int)F.rows_off + R - k, std::max(0, k - R), 0);
-      } else if (mode == PM_BWD21)
-        for (int cb = 0; cb < k; cb += 64) {
-          // B rows: the SIMT kernel gathers rows[rows_off + kk - kfirst], the
-          // tensor-core kernel reads the level's gather buffer at its offset
-          push(r0, cb, b == 0 ? 0 : F.n - r0, std::min(64, k - cb), (int)F.rows_off - (k - r0), F.c0 + cb, 0,
-               k - r0);
-          c->prod_h.back().bbase = gofs[fi] - (k - r0);
-        }
-      else
+            push(true, true, R, 0, k, std::min(64, F.n - R), F.c0, (int)F.rows_off + R - k, std::max(0, k - R), 0);
+      } else if (mode == PM_BWD21) {
+        // B rows: the SIMT kernel gathers rows[rows_off + kk - kfirst] (64-column
+        // tiles), the tensor-core kernel reads the level's gather buffer at the
+        // front's offset (128-column tiles)
+        const int kdim = b == 0 ? 0 : F.n - r0;
         for (int cb = 0; cb < k; cb += 64)
-          push(cb, cb, k - cb, std::min(64, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
+          push(false, true, r0, cb, kdim, std::min(64, k - cb), (int)F.rows_off - (k - r0), F.c0 + cb, 0, k - r0);
+        for (int cb = 0; cb < k; cb += 128)
+          push(true, false, r0, cb, kdim, std::min(128, k - cb), gofs[fi] - (k - r0), F.c0 + cb, 0, k - r0);
+      } else {
+        for (int cb = 0; cb < k; cb += 64)
+          push(false, true, cb, cb, k - cb, std::min(64, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
+        for (int cb = 0; cb < k; cb += 128)
+          push(true, false, cb, cb, k - cb, std::min(128, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
+      }
     }
     lv.n_prod[mode] = int(c->prod_h.size() - beg);
+    lv.n_prod_simt[mode] = int(c->prod_simt_h.size() - beg_s);
     lv.prod[mode] = (const TcTask *)(uintptr_t)beg;
-    lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg;
+    lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg_s;
   }
   // inversion: 32-blocks, then pairwise merges of blocks of 32 * 2^stage
   const size_t dbeg = c->invdiag_h.size();

@@ -118,7 +118,8 @@ struct LevelDev {
   // FP32 solves: front-product tasks per mode
   const TcTask *prod[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
   const SimtTask *prod_simt[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
-  int n_prod[PM_COUNT] = {0, 0, 0, 0};
+  int n_prod[PM_COUNT] = {0, 0, 0, 0};        // tensor-core tiles (128 columns wide for BWD21 / TRI_B)
+  int n_prod_simt[PM_COUNT] = {0, 0, 0, 0};   // SIMT tiles (64 wide)
   // FP32 factorisation: inversion of L11, per merge stage (block size 32 * 2^stage)
   struct InvStage {
     const InvTask *tasks = nullptr;

@@ -15,11 +15,11 @@
 // One persistent CTA per SM slot walks a static list of (tile, pole, RHS
 // chunk) items; each item is a 128 x 64 real output tile streamed over its
 // inner dimension in chunks of 16:
-//   warps 0-3  (producers) load the raw chunk into a ring of NRAW shared
-//              slots (NRAW - 1 chunks in flight): A by TMA from the front's
-//              tensor map and contiguous B rows by TMA from the vector's map
-//              (one thread), gathered B rows by 16-byte cp.async (each warp
-//              its own rows), then split it:
+//   warp 8 l1 (loader) issues the TMA loads of each chunk (the A box from
+//              the front's tensor map, the B rows from the vector's map)
+//              into a ring of NRAW shared slots as soon as a slot is released;
+//   warps 0-3  (producers) copy a chunk into registers, release the slot and
+//              split it:
 //              A hi/lo -> tensor memory (tcgen05.st, thread = TMEM lane =
 //              real row), B hi/lo -> shared memory (K-major core matrices);
 //   warp 8     issues the MMAs of a chunk (A from TMEM, B from shared) into
@@ -74,7 +74,8 @@ struct ProdArgs {
   const c64 *L;
   int64_t lstride;
   const TcTask *tasks;
-  int ntask;
+  int ntask;         // tensor-core tiles
+  int ntask_simt;    // SIMT tiles (64 wide)
   const int32_t *rows;
   const c64 *B;      // source of the B rows
   c64 *out;          // destination
@@ -152,154 +153,118 @@ __device__ __forceinline__ bool aborted(TcShared &sh) { return *reinterpret_cast
 // ---------------------------------------------------------------------------
 // producers (warps 0-3, thread t = real row t of the tile)
 
+// Loader (warp 8, lane 1): the TMA loads of every chunk (A box and B rows),
+// in order, into raw slot gc % NRAW once the producers have released it.
 template <int MODE>
-struct Fetch {
-  Item cur, nxt;
-  int j = 0, c = 0;
-
-  // move on to the next item that has chunks (the others need no data)
-  __device__ void settle(const ProdArgs &a) {
-    while (cur.valid && c >= cur.nch) {
-      cur = nxt;
-      j++;
-      c = 0;
-      nxt = load_item(a, j + 1);
-    }
-  }
-  __device__ void start(const ProdArgs &a) {
-    cur = load_item(a, 0);
-    nxt = load_item(a, 1);
-    settle(a);
-  }
-  __device__ bool active() const { return cur.valid; }
-
-  // Issue the loads of the current chunk (global chunk number `gc`) into raw
-  // slot gc % NRAW, then advance.  A and the B rows come by TMA from thread 0
-  // once every producer thread has released the slot; with an odd number of
-  // right-hand sides (no B map) warp w copies B rows 4w..4w+3 by cp.async.
-  __device__ bool issue(const ProdArgs &a, TcShared &sh, int gc, int tid) {
-    const int slot = gc % NRAW;
-    const int k0 = c * TKC;
-    const TcTask &t = cur.t;
-    const bool tma_b = a.bmap != nullptr;
-    bool ok = true;
-    if (tid == 0) {
-      if (gc >= NRAW) ok = wait_bar(sh, &sh.rawempty[slot], ((gc / NRAW) - 1) & 1, a.st);
-      if (ok) {
-        sh.kval[slot] = min(TKC, t.kdim - k0);
-        sh.kfst[slot] = max(0, int(t.kfirst) - k0);
-        tc::mbar_arrive_expect_tx(&sh.rawfull[slot], RAWA * 4 + (tma_b ? RAWB * 4 : 0));
-        const bool colmaj = !row_major(MODE);
-        tc::tma_load_3d(sh.rawA[slot], a.tmaps + t.map, colmaj ? t.x0 : t.x0 + 2 * k0, colmaj ? t.y0 + k0 : t.y0,
-                        cur.p, &sh.rawfull[slot]);
-        if (tma_b) tc::tma_load_3d(sh.rawB[slot], a.bmap, 64 * cur.ch, t.bbase + k0, cur.p, &sh.rawfull[slot]);
+__device__ void loader(const ProdArgs &a, TcShared &sh) {
+  int gc = 0;
+  bool ok = true;
+  Item nxt = load_item(a, 0);
+#pragma unroll 1
+  for (int j = 0; ok; j++) {
+    const Item it = nxt;
+    if (!it.valid) break;
+    nxt = load_item(a, j + 1);
+    const TcTask &t = it.t;
+#pragma unroll 1
+    for (int c = 0; c < it.nch; c++, gc++) {
+      const int slot = gc % NRAW;
+      if (gc >= NRAW && !wait_bar(sh, &sh.rawempty[slot], ((gc / NRAW) - 1) & 1, a.st)) {
+        ok = false;
+        break;
       }
+      const int k0 = c * TKC;
+      sh.kval[slot] = min(TKC, t.kdim - k0);
+      sh.kfst[slot] = max(0, int(t.kfirst) - k0);
+      tc::mbar_arrive_expect_tx(&sh.rawfull[slot], (RAWA + RAWB) * 4);
+      const bool colmaj = !row_major(MODE);
+      tc::tma_load_3d(sh.rawA[slot], a.tmaps + t.map, colmaj ? t.x0 : t.x0 + 2 * k0, colmaj ? t.y0 + k0 : t.y0,
+                      it.p, &sh.rawfull[slot]);
+      tc::tma_load_3d(sh.rawB[slot], a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
     }
-    if (!tma_b) {
-      const int w = tid >> 5, l = tid & 31;
-      const int ncols = min(32, a.nrhs - cur.ch * 32);
-      const c64 *bp = a.B + int64_t(cur.p) * a.bstride + cur.ch * 32;
-      float *rb = sh.rawB[slot];
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const int kk = k0 + 4 * w + r;
-        const bool rok = kk < t.kdim && kk >= t.kfirst && l < ncols;
-        const void *src = rok ? static_cast<const void *>(bp + (int64_t(t.bbase) + kk) * a.nrhs + l)
-                              : static_cast<const void *>(a.L);
-        tc::cp_async8(rb + (4 * w + r) * 64 + 2 * l, src, rok);
-      }
-    }
-    c++;
-    settle(a);
-    return ok;
   }
-};
+  if (!ok)
+    for (int q = max(0, gc - NRAW); q < gc; q++) tc::mbar_wait(&sh.rawfull[q % NRAW], (q / NRAW) & 1, kWaitIter);
+}
 
 template <int MODE>
 __device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
-  Fetch<MODE> f;
-  f.start(a);
-  int issued = 0;
-  bool ok = true;
-  // prologue: NRAW - 1 chunks in flight
-#pragma unroll 1
-  for (int i = 0; i < NRAW - 1; i++) {
-    if (f.active()) {
-      ok = f.issue(a, sh, issued, tid) && ok;
-      issued++;
-    }
-    tc::cp_async_commit();
-  }
   const int w = tid >> 5, l = tid & 31;
-  ok = __all_sync(kFull, ok);
   int g = 0;
   int pend = -1;   // stage whose TMEM / shared stores are in flight, signalled one chunk later
+  bool ok = true;
 #pragma unroll 1
-  for (; g < issued && ok; g++) {
-    __syncwarp();   // every lane has read the B slot a cp.async is about to refill
-    if (f.active()) {
-      ok = f.issue(a, sh, issued, tid);
-      issued++;
-    }
-    tc::cp_async_commit();
-    tc::cp_async_wait<NRAW - 1>();        // cp.async B of chunk g has landed (this warp's copies)
-    __syncwarp();
-    const int slot = g % NRAW;
-    ok = wait_bar(sh, &sh.rawfull[slot], (g / NRAW) & 1, a.st) && ok;   // TMA loads of chunk g
-    if (!__all_sync(kFull, ok)) break;
-    // copy the chunk into registers and release the slot at once: A row tid
-    // (16 values) and B columns l, l + 32 of rows 4w..4w+3, zero outside [kfst, kval)
-    float v[TKC], b0[4], b1[4];
-    if (!row_major(MODE)) {
+  for (int j = 0; ok; j++) {
+    const Item it = load_item(a, j);
+    if (!it.valid) break;
+#pragma unroll 1
+    for (int c = 0; c < it.nch; c++, g++) {
+      const int slot = g % NRAW;
+      ok = wait_bar(sh, &sh.rawfull[slot], (g / NRAW) & 1, a.st);
+      if (!__all_sync(kFull, ok)) {
+        ok = false;
+        break;
+      }
+      // copy the chunk into registers and release the slot at once: A row tid
+      // (16 values) and B columns l, l + 32 of rows 4w..4w+3, zero outside [kfst, kval)
+      float v[TKC], b0[4], b1[4];
+      if (!row_major(MODE)) {
 #pragma unroll
-      for (int kk = 0; kk < TKC; kk++) v[kk] = sh.rawA[slot][kk * 128 + tid];
-    } else {
-      // row c of the 64 x 32-float box, 16-byte chunks swizzled by c & 7
-      const int cc = tid >> 1, sw = cc & 7;
-      const float *src = sh.rawA[slot] + cc * 32 + (tid & 1);
+        for (int kk = 0; kk < TKC; kk++) v[kk] = sh.rawA[slot][kk * 128 + tid];
+      } else {
+        // row c of the 64 x 32-float box, 16-byte chunks swizzled by c & 7
+        const int cc = tid >> 1, sw = cc & 7;
+        const float *src = sh.rawA[slot] + cc * 32 + (tid & 1);
 #pragma unroll
-      for (int e = 0; e < TKC; e++) v[e] = src[(((e >> 1) ^ sw) << 2) + 2 * (e & 1)];
-    }
-    {
-      const int kv = sh.kval[slot], kf = sh.kfst[slot];
+        for (int e = 0; e < TKC; e++) v[e] = src[(((e >> 1) ^ sw) << 2) + 2 * (e & 1)];
+      }
+      {
+        const int kv = sh.kval[slot], kf = sh.kfst[slot];
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int r = 4 * w + q;
-        const bool in = r < kv && r >= kf;
-        b0[q] = in ? sh.rawB[slot][r * 64 + l] : 0.f;
-        b1[q] = in ? sh.rawB[slot][r * 64 + 32 + l] : 0.f;
+        for (int q = 0; q < 4; q++) {
+          const int r = 4 * w + q;
+          const bool in = r < kv && r >= kf;
+          b0[q] = in ? sh.rawB[slot][r * 64 + l] : 0.f;
+          b1[q] = in ? sh.rawB[slot][r * 64 + 32 + l] : 0.f;
+        }
+      }
+      tc::mbar_arrive(&sh.rawempty[slot]);
+      // the previous chunk's stores had this chunk's loads to land
+      if (pend >= 0) {
+        tc::tmem_st_wait();
+        tc::fence_async_smem();
+        tc::fence_before();
+        tc::mbar_arrive(&sh.full[pend]);
+        pend = -1;
+      }
+      // stage s must have been consumed by the MMAs of chunk g - NST
+      const int s = g % NST, use = g / NST;
+      if (use > 0) ok = wait_bar(sh, &sh.empty[s], (use - 1) & 1, a.st);
+      if (!__all_sync(kFull, ok)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      const uint32_t ta = sh.tmem + (uint32_t(w * 32) << 16) + COL_A + 32 * s;
+      {
+        float lo[TKC];
+#pragma unroll
+        for (int kk = 0; kk < TKC; kk++) {
+          const float h = tc::to_tf32(v[kk]);
+          lo[kk] = tc::to_tf32(v[kk] - h);
+          v[kk] = h;
+        }
+        tc::tmem_st16(ta, v);
+        tc::tmem_st16(ta + 16, lo);
+      }
+      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l, 4 * w, 64), b0);
+      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l + 32, 4 * w, 64), b1);
+      pend = s;
+      if (__any_sync(kFull, aborted(sh))) {
+        ok = false;
+        break;
       }
     }
-    tc::mbar_arrive(&sh.rawempty[slot]);
-    // the previous chunk's stores had this chunk's loads to land
-    if (pend >= 0) {
-      tc::tmem_st_wait();
-      tc::fence_async_smem();
-      tc::fence_before();
-      tc::mbar_arrive(&sh.full[pend]);
-      pend = -1;
-    }
-    // stage s must have been consumed by the MMAs of chunk g - NST
-    const int s = g % NST, use = g / NST;
-    if (use > 0) ok = wait_bar(sh, &sh.empty[s], (use - 1) & 1, a.st);
-    if (!__all_sync(kFull, ok)) break;
-    tc::fence_after();
-    const uint32_t ta = sh.tmem + (uint32_t(w * 32) << 16) + COL_A + 32 * s;
-    {
-      float lo[TKC];
-#pragma unroll
-      for (int kk = 0; kk < TKC; kk++) {
-        const float h = tc::to_tf32(v[kk]);
-        lo[kk] = tc::to_tf32(v[kk] - h);
-        v[kk] = h;
-      }
-      tc::tmem_st16(ta, v);
-      tc::tmem_st16(ta + 16, lo);
-    }
-    split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l, 4 * w, 64), b0);
-    split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l + 32, 4 * w, 64), b1);
-    pend = s;
-    if (__any_sync(kFull, aborted(sh))) break;
   }
   tc::tmem_st_wait();
   if (pend >= 0 && ok) {
@@ -307,10 +272,6 @@ __device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
     tc::fence_before();
     tc::mbar_arrive(&sh.full[pend]);
   }
-  tc::cp_async_wait_all();
-  // after an abort: let the TMA loads still in flight land before the CTA exits
-  if (tid == 0)
-    for (int q = g; q < issued; q++) tc::mbar_wait(&sh.rawfull[q % NRAW], (q / NRAW) & 1, kWaitIter);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,10 +430,283 @@ __global__ void __launch_bounds__(NTHR, 2) k_tc_prod(const ProdArgs a) {
   if (warp < 4) producer<MODE>(a, sh, tid);
   else if (warp < 8) epilogue<MODE>(a, sh, tid - 128);
   else if ((tid & 31) == 0) mma_issuer(a, sh);
+  else if ((tid & 31) == 1) loader<MODE>(a, sh);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   if (warp == 8) tc::tmem_dealloc(sh.tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// Transposed-access products (BWD21, TRI_B) with the inner dimension
+// interleaved: a factor column c (pivot column of the tile) is one TMEM lane
+// and its complex rows i give real inner indices (i, re) and (i, im), so the
+// raw TMA box of 128 columns x 16 complex rows (128-byte rows, 128-byte
+// swizzle) is already a K-major operand.  The tensor core reads it directly
+// as the TF32 hi part (it truncates FP32 inputs to TF32, so hi = the raw
+// value and lo = x - trunc(x) exactly); the producers compute only lo (into
+// TMEM) and the B operand X^ of the real embedding:
+//   X^[(i, 0)][(j, re)] = Re X(i,j),  X^[(i, 1)][(j, re)] = -Im X(i,j),
+//   X^[(i, 0)][(j, im)] = Im X(i,j),  X^[(i, 1)][(j, im)] =  Re X(i,j),
+// so that lane c of the accumulator holds (re, im) of sum_i A(i,c) X(i,j)
+// for the 32 right-hand sides j, without a lane-pair combine.
+
+namespace {
+constexpr int KI_K = 16;         // complex inner indices per chunk (32 real, four MMA k-steps)
+constexpr int KI_SLOTS = 3;
+constexpr uint32_t KI_TMEM = 256;
+constexpr uint32_t KI_COL_LO = 128;   // lo stages after the two 64-column accumulators
+
+struct KiSlot {
+  float A[128 * 32];          // raw A box: 128 columns x 32 floats, 128-byte swizzle (16 KB)
+  float Xr[KI_K * 64];        // raw B rows: 16 rows x 64 floats (4 KB)
+  float Bh[64 * 32];          // X^ hi, K-major core matrices (8 KB)
+  float Bl[64 * 32];          // X^ lo
+};
+struct KiShared {
+  KiSlot sl[KI_SLOTS];
+  uint64_t rawfull[KI_SLOTS], full[KI_SLOTS], freeb[KI_SLOTS], accf[2], acce[2], fin;
+  int kval[KI_SLOTS], kfst[KI_SLOTS];
+  uint32_t tmem;
+  int abort;
+};
+constexpr size_t kKiSmem = sizeof(KiShared) + 1024;
+
+__device__ __forceinline__ bool ki_wait(KiShared &sh, uint64_t *bar, uint32_t parity, DevStatus *st) {
+  if (tc::mbar_wait_or_abort(bar, parity, kWaitIter, &sh.abort)) return true;
+  sh.abort = 1;
+  atomicExch(&st->tc_timeout, 1);
+  return false;
+}
+
+__device__ __forceinline__ Item ki_item(const ProdArgs &a, int j) {
+  Item it = load_item(a, j);
+  it.nch = (it.t.kdim + KI_K - 1) / KI_K;
+  return it;
+}
+
+// Loader (warp 8, lane 1): the TMA loads of every chunk, in order, into slot
+// gc % KI_SLOTS as soon as the MMAs of the slot's previous chunk are done.
+__device__ void ki_loader(const ProdArgs &a, KiShared &sh) {
+  int gc = 0;
+  bool ok = true;
+  Item nxt = ki_item(a, 0);
+#pragma unroll 1
+  for (int j = 0; ok; j++) {
+    const Item it = nxt;
+    if (!it.valid) break;
+    nxt = ki_item(a, j + 1);
+    const TcTask &t = it.t;
+#pragma unroll 1
+    for (int c = 0; c < it.nch; c++, gc++) {
+      const int slot = gc % KI_SLOTS;
+      if (gc >= KI_SLOTS && !ki_wait(sh, &sh.freeb[slot], ((gc / KI_SLOTS) - 1) & 1, a.st)) {
+        ok = false;
+        break;
+      }
+      const int k0 = c * KI_K;
+      sh.kval[slot] = min(KI_K, t.kdim - k0);
+      sh.kfst[slot] = max(0, int(t.kfirst) - k0);
+      tc::mbar_arrive_expect_tx(&sh.rawfull[slot], (128 * 32 + KI_K * 64) * 4);
+      tc::tma_load_3d(sh.sl[slot].A, a.tmaps + t.map, t.x0 + 2 * k0, t.y0, it.p, &sh.rawfull[slot]);
+      tc::tma_load_3d(sh.sl[slot].Xr, a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
+    }
+  }
+  // after an abort: let the loads still in flight land before the CTA exits
+  if (!ok)
+    for (int q = max(0, gc - KI_SLOTS); q < gc; q++) tc::mbar_wait(&sh.rawfull[q % KI_SLOTS], (q / KI_SLOTS) & 1, kWaitIter);
+}
+
+template <int MODE>
+__device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
+  const int w = tid >> 5, l = tid & 31;
+  int g = 0;
+  bool ok = true;
+#pragma unroll 1
+  for (int j = 0; ok; j++) {
+    const Item it = ki_item(a, j);
+    if (!it.valid) break;
+#pragma unroll 1
+    for (int c = 0; c < it.nch; c++, g++) {
+      const int slot = g % KI_SLOTS;
+      ok = ki_wait(sh, &sh.rawfull[slot], (g / KI_SLOTS) & 1, a.st);
+      if (!__all_sync(kFull, ok)) {
+        ok = false;
+        break;
+      }
+      KiSlot &S = sh.sl[slot];
+      // lo of factor column tid: its 32 floats, 16-byte chunks swizzled by tid & 7
+      {
+        float v[32];
+        const float4 *row = reinterpret_cast<const float4 *>(S.A + tid * 32);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const float4 x = row[q ^ (tid & 7)];
+          v[4 * q] = x.x;
+          v[4 * q + 1] = x.y;
+          v[4 * q + 2] = x.z;
+          v[4 * q + 3] = x.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 32; q++) {
+          const float h = __uint_as_float(__float_as_uint(v[q]) & 0xffffe000u);   // what the MMA reads of v
+          v[q] = tc::to_tf32(__fsub_rn(v[q], h));
+        }
+        tc::tmem_st32(sh.tmem + (uint32_t(w * 32) << 16) + KI_COL_LO + 32 * slot, v);
+      }
+      // X^ row n = l and n = 32 + l (right-hand side n / 2, re row if n even):
+      // inner indices 8w..8w+7 = complex rows i = 4w..4w+3
+      {
+        const int kv = sh.kval[slot], kf = sh.kfst[slot];
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+          const int n = 32 * half + l, jr = n >> 1;
+          float r[8];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int i = 4 * w + q;
+            const float2 x = *reinterpret_cast<const float2 *>(S.Xr + i * 64 + 2 * jr);
+            const bool in = i < kv && i >= kf;
+            const float re = in ? x.x : 0.f, im = in ? x.y : 0.f;
+            r[2 * q] = (n & 1) ? im : re;
+            r[2 * q + 1] = (n & 1) ? re : -im;
+          }
+          split4(S.Bh, S.Bl, kmaj_off(n, 8 * w, 64), r);
+          split4(S.Bh, S.Bl, kmaj_off(n, 8 * w + 4, 64), r + 4);
+        }
+      }
+      tc::tmem_st_wait();
+      tc::fence_async_smem();
+      tc::fence_before();
+      tc::mbar_arrive(&sh.full[slot]);
+      if (__any_sync(kFull, *reinterpret_cast<volatile int *>(&sh.abort) != 0)) {
+        ok = false;
+        break;
+      }
+    }
+  }
+}
+
+__device__ void ki_mma(const ProdArgs &a, KiShared &sh) {
+  const uint32_t idesc = tc::idesc_tf32(128, 64);
+  int g = 0;
+  bool ok = true;
+  Item nxt = ki_item(a, 0);
+#pragma unroll 1
+  for (int j = 0; ok; j++) {
+    const Item it = nxt;
+    if (!it.valid) break;
+    nxt = ki_item(a, j + 1);
+    const int buf = j & 1, use = j >> 1;
+    if (use > 0 && !ki_wait(sh, &sh.acce[buf], (use - 1) & 1, a.st)) break;
+    tc::fence_after();
+    const uint32_t d = sh.tmem + 64 * buf;
+#pragma unroll 1
+    for (int c = 0; c < it.nch; c++, g++) {
+      const int slot = g % KI_SLOTS;
+      if (!ki_wait(sh, &sh.full[slot], (g / KI_SLOTS) & 1, a.st)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      const KiSlot &S = sh.sl[slot];
+#pragma unroll
+      for (int ks = 0; ks < 4; ks++) {
+        const uint64_t ah = tc::desc_kmajor_sw128(tc::smem_addr(S.A) + 32 * ks, 1024);
+        const uint32_t al = sh.tmem + KI_COL_LO + 32 * slot + 8 * ks;
+        const uint64_t bh = tc::desc_kmajor(tc::smem_addr(&S.Bh[ks * 64 * 8]), 128, 256);
+        const uint64_t bl = tc::desc_kmajor(tc::smem_addr(&S.Bl[ks * 64 * 8]), 128, 256);
+        tc::mma_tf32(d, ah, bh, idesc, c > 0 || ks > 0);
+        tc::mma_tf32(d, ah, bl, idesc, true);
+        tc::mma_tf32_ts(d, al, bh, idesc, true);
+      }
+      tc::commit(&sh.freeb[slot]);   // the slot (and its lo stage) is free once these MMAs are done
+    }
+    if (!ok) break;
+    tc::commit(&sh.accf[buf]);
+  }
+  tc::commit(&sh.fin);
+  if (!tc::mbar_wait(&sh.fin, 0, kWaitIter)) atomicExch(&a.st->tc_timeout, 1);
+}
+
+// lane e = pivot column m of the tile: (re, im) of the 32 right-hand sides
+template <int MODE>
+__device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
+  const int we = e >> 5;
+  Item nxt = ki_item(a, 0);
+#pragma unroll 1
+  for (int j = 0;; j++) {
+    const Item it = nxt;
+    if (!it.valid) break;
+    nxt = ki_item(a, j + 1);
+    const int buf = j & 1, use = j >> 1;
+    const bool ok = ki_wait(sh, &sh.accf[buf], use & 1, a.st);
+    if (!__all_sync(kFull, ok)) break;
+    tc::fence_after();
+    float v[64];
+    if (it.nch > 0) {
+      tc::tmem_ld64(sh.tmem + (uint32_t(we * 32) << 16) + 64 * buf, v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 64; q++) v[q] = 0.f;
+    }
+    tc::fence_before();
+    tc::mbar_arrive(&sh.acce[buf]);
+    const int m = e;
+    if (m >= it.t.mrows) continue;
+    const int ncols = min(32, a.nrhs - it.ch * 32);
+    const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
+    const int64_t row = int64_t(it.t.obase) + m;
+    c64 *y = a.out + pv + row * a.nrhs;
+    if (MODE == PM_BWD21) {
+      const c64 di = a.dinv[int64_t(it.p) * a.N + row];
+      const c64 *x = a.xaux + pv + row * a.nrhs;
+#pragma unroll
+      for (int q = 0; q < 32; q++)
+        if (q < ncols) {
+          const c64 dx = di * x[q];
+          y[q] = mk<float>(dx.x - v[2 * q], dx.y - v[2 * q + 1]);
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; q++)
+        if (q < ncols) y[q] = mk<float>(v[2 * q], v[2 * q + 1]);
+    }
+  }
+}
+}  // namespace
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHR, 2) k_tc_kint(const ProdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  KiShared &sh = *reinterpret_cast<KiShared *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 8) tc::tmem_alloc(&sh.tmem, KI_TMEM);
+  if (tid == 0) {
+    for (int s = 0; s < KI_SLOTS; s++) {
+      tc::mbar_init(&sh.rawfull[s], 1);
+      tc::mbar_init(&sh.full[s], 128);
+      tc::mbar_init(&sh.freeb[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&sh.accf[b], 1);
+      tc::mbar_init(&sh.acce[b], 128);
+    }
+    tc::mbar_init(&sh.fin, 1);
+    sh.abort = 0;
+    tc::fence_async_smem();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp < 4) ki_producer<MODE>(a, sh, tid);
+  else if (warp < 8) ki_epilogue<MODE>(a, sh, tid - 128);
+  else if ((tid & 31) == 0) ki_mma(a, sh);
+  else if ((tid & 31) == 1) ki_loader(a, sh);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 8) tc::tmem_dealloc(sh.tmem, KI_TMEM);
 }
 
 // ---------------------------------------------------------------------------
@@ -579,6 +813,11 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
       cudaFuncSetAttribute(k_tc_prod<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
       // all of the unified L1 / shared storage as shared memory: two CTAs per SM
       cudaFuncSetAttribute(k_tc_prod<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if constexpr (row_major(MODE)) {
+        cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kKiSmem));
+        cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
+      static_assert(2 * (kKiSmem + 1024) <= 228 * 1024, "two CTAs per SM must fit in shared memory");
       // Two CTAs per SM: 256 of the 512 TMEM columns, under half of the shared
       // memory and 2 x 288 x 96 registers each.  (The occupancy calculator
       // reports one for this 9-warp block; two are resident, as measured by
@@ -591,9 +830,12 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
     const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
     const int grid = int(total < grid_max ? total : grid_max);
     tem::count_launch();
-    k_tc_prod<MODE><<<grid, NTHR, kTcSmem, s>>>(a);
+    if constexpr (row_major(MODE))
+      k_tc_kint<MODE><<<grid, NTHR, kKiSmem, s>>>(a);
+    else
+      k_tc_prod<MODE><<<grid, NTHR, kTcSmem, s>>>(a);
   } else {
-    dim3 g(a.ntask, a.np * a.nchunk);
+    dim3 g(a.ntask_simt, a.np * a.nchunk);
     tem::count_launch();
     k_prod_simt<MODE><<<g, 256, 0, s>>>(a, simt);
   }
@@ -603,12 +845,16 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
 int tc_ctas_per_sm() { return g_tc_occupancy; }
 
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
-  if (lv.n_prod[mode] == 0 || P.np == 0) return;
+  // the tensor-core kernels load B rows by TMA, which needs 16-byte rows (an
+  // even number of right-hand sides); otherwise the SIMT kernels run
+  const bool use_tc = P.use_tc && P.vmaps != nullptr;
+  if ((use_tc ? lv.n_prod[mode] : lv.n_prod_simt[mode]) == 0 || P.np == 0) return;
   ProdArgs a;
   a.L = P.L;
   a.lstride = P.lstride;
   a.tasks = lv.prod[mode];
   a.ntask = lv.n_prod[mode];
+  a.ntask_simt = lv.n_prod_simt[mode];
   a.rows = P.rows;
   a.N = P.N;
   a.vstride = P.vstride;
@@ -628,19 +874,19 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
       a.bmap = vm ? vm : nullptr;
       a.B = P.Y;
       a.out = P.X;
-      run_mode<PM_TRI_F>(a, lv.prod_simt[mode], P.use_tc, s);
+      run_mode<PM_TRI_F>(a, lv.prod_simt[mode], use_tc, s);
       break;
     case PM_FWD21:
       a.bmap = vm ? vm + 1 : nullptr;
       a.B = P.X;
       a.out = P.Y;
-      run_mode<PM_FWD21>(a, lv.prod_simt[mode], P.use_tc, s);
+      run_mode<PM_FWD21>(a, lv.prod_simt[mode], use_tc, s);
       break;
     case PM_BWD21:
       a.B = P.X;
       a.out = P.Y;
       a.xaux = P.X;
-      if (P.use_tc) {
+      if (use_tc) {
         // the tensor-core kernel reads the update rows pre-gathered
         if (lv.n_gather > 0) {
           tem::count_launch();
@@ -651,13 +897,13 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
         a.bstride = P.gstride;
         a.bmap = vm ? vm + 2 : nullptr;
       }
-      run_mode<PM_BWD21>(a, lv.prod_simt[mode], P.use_tc, s);
+      run_mode<PM_BWD21>(a, lv.prod_simt[mode], use_tc, s);
       break;
     default:
       a.bmap = vm ? vm : nullptr;
       a.B = P.Y;
       a.out = P.X;
-      run_mode<PM_TRI_B>(a, lv.prod_simt[mode], P.use_tc, s);
+      run_mode<PM_TRI_B>(a, lv.prod_simt[mode], use_tc, s);
       break;
   }
 }
@@ -672,7 +918,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // along a column (2 floats per complex entry; rows k..n-1 excluded for the
 // pivot-block maps 0 and 3), dim 1 over the k columns, dim 2 over the poles.
 // Maps 0/1 (column-major tiles) load 16 columns x 64 complex rows; maps 2/3
-// (row-major tiles) load 64 columns x 16 complex rows with the 128-byte
+// (row-major tiles) load 128 columns x 16 complex rows with the 128-byte
 // swizzle.  Entries outside the dims read as zero.
 std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
                               void **out) {
@@ -697,7 +943,7 @@ std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L
       const bool colmaj = !row_major(kind);
       const cuuint64_t dims[3] = {cuuint64_t(2) * (tri ? f.k : f.n), cuuint64_t(f.k), cuuint64_t(m)};
       const cuuint64_t strides[2] = {cuuint64_t(f.ld) * sizeof(c64), cuuint64_t(lstride) * sizeof(c64)};
-      const cuuint32_t box[3] = {colmaj ? 128u : 32u, colmaj ? 16u : 64u, 1u};
+      const cuuint32_t box[3] = {colmaj ? 128u : 32u, colmaj ? 16u : 128u, 1u};
       const cuuint32_t estr[3] = {1, 1, 1};
       const CUresult r =
           encode(&maps[4 * i + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(L + f.lofs), dims,

@@ -28,6 +28,15 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, uint32_t lbo, ui
   return d;
 }
 
+// K-major descriptor with the 128-byte swizzle: rows of 128 bytes, 8-row
+// atoms of 1024 bytes (sbo apart); the atom base must be 1024-byte aligned,
+// the start may advance inside a row in 32-byte k-steps.
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = desc_kmajor(saddr, 16, sbo);
+  d |= uint64_t(2) << 61;                          // layout type: 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor of tcgen05.mma.kind::tf32: FP32 accumulator, TF32
 // A and B, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
@@ -182,6 +191,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
       : "memory");
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Each thread of a warp writes 32 consecutive 32-bit columns of its TMEM lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+  tmem_st16(taddr, v);
+  tmem_st16(taddr + 16, v + 16);
+}
 
 // Four x16 loads (64 columns) and one wait.
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v) {
