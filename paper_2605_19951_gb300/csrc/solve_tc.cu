@@ -391,10 +391,13 @@ __device__ void epilogue(const ProdArgs &a, TcShared &sh, int e) {
           y[j0 + q] = mk<float>(dx.x - (E[2 * q] - O[2 * q + 1]), dx.y - (E[2 * q + 1] + O[2 * q]));
         }
     } else {
-      c64 *y = a.out + pv + (int64_t(it.t.obase) + m) * a.nrhs;
+      // rows start on 16-byte boundaries (even nrhs on the tensor cores): two right-hand sides per store
+      float4 *y = reinterpret_cast<float4 *>(a.out + pv + (int64_t(it.t.obase) + m) * a.nrhs + j0);
 #pragma unroll
-      for (int q = 0; q < 16; q++)
-        if (j0 + q < ncols) y[j0 + q] = mk<float>(E[2 * q] - O[2 * q + 1], E[2 * q + 1] + O[2 * q]);
+      for (int q = 0; q < 16; q += 2)
+        if (j0 + q < ncols)
+          y[q >> 1] = make_float4(E[2 * q] - O[2 * q + 1], E[2 * q + 1] + O[2 * q], E[2 * q + 2] - O[2 * q + 3],
+                                  E[2 * q + 3] + O[2 * q + 2]);
     }
   }
 }
@@ -657,20 +660,22 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     const int ncols = min(32, a.nrhs - it.ch * 32);
     const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
     const int64_t row = int64_t(it.t.obase) + m;
-    c64 *y = a.out + pv + row * a.nrhs;
+    // rows start on 16-byte boundaries (even nrhs): two right-hand sides per access
+    float4 *y = reinterpret_cast<float4 *>(a.out + pv + row * a.nrhs);
     if (MODE == PM_BWD21) {
       const c64 di = a.dinv[int64_t(it.p) * a.N + row];
-      const c64 *x = a.xaux + pv + row * a.nrhs;
+      const float4 *x = reinterpret_cast<const float4 *>(a.xaux + pv + row * a.nrhs);
 #pragma unroll
-      for (int q = 0; q < 32; q++)
-        if (q < ncols) {
-          const c64 dx = di * x[q];
-          y[q] = mk<float>(dx.x - v[2 * q], dx.y - v[2 * q + 1]);
+      for (int q = 0; q < 16; q++)
+        if (2 * q < ncols) {
+          const float4 xv = x[q];
+          const c64 d0 = di * mk<float>(xv.x, xv.y), d1 = di * mk<float>(xv.z, xv.w);
+          y[q] = make_float4(d0.x - v[4 * q], d0.y - v[4 * q + 1], d1.x - v[4 * q + 2], d1.y - v[4 * q + 3]);
         }
     } else {
 #pragma unroll
-      for (int q = 0; q < 32; q++)
-        if (q < ncols) y[q] = mk<float>(v[2 * q], v[2 * q + 1]);
+      for (int q = 0; q < 16; q++)
+        if (2 * q < ncols) y[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
   }
 }
@@ -782,10 +787,12 @@ __global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtT
 }
 
 // Xg[p][g0 + i] = X[p][rows_i] for the update rows of each front of a level
-// (contiguous B rows for the backward L21 product); one CTA per (front, pole).
-__global__ void k_gather_upd(const c64 *__restrict__ X, int64_t vstride, c64 *__restrict__ Xg, int64_t gstride,
-                             const FrontDev *__restrict__ F, const int32_t *__restrict__ rows,
-                             const int2 *__restrict__ tasks, int nrhs, const int *__restrict__ pmap) {
+// (contiguous B rows for the backward L21 product); one CTA per (front,
+// pole), a warp per row at a time, lanes over right-hand sides.
+__global__ void __launch_bounds__(256) k_gather_upd(const c64 *__restrict__ X, int64_t vstride, c64 *__restrict__ Xg,
+                                                    int64_t gstride, const FrontDev *__restrict__ F,
+                                                    const int32_t *__restrict__ rows, const int2 *__restrict__ tasks,
+                                                    int nrhs, const int *__restrict__ pmap) {
   const int2 t = tasks[blockIdx.x];
   const int p = pole_of(blockIdx.y, pmap);
   const FrontDev f = F[t.x];
@@ -793,9 +800,11 @@ __global__ void k_gather_upd(const c64 *__restrict__ X, int64_t vstride, c64 *__
   const int32_t *ur = rows + f.rows_off;
   const c64 *xp = X + p * vstride;
   c64 *gp = Xg + p * gstride + int64_t(t.y) * nrhs;
-  for (int64_t e = threadIdx.x; e < int64_t(b) * nrhs; e += blockDim.x) {
-    const int64_t i = e / nrhs, j = e - i * nrhs;
-    gp[e] = xp[int64_t(ur[i]) * nrhs + j];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < b; i += 8) {
+    const c64 *src = xp + int64_t(__ldg(ur + i)) * nrhs;
+    c64 *dst = gp + int64_t(i) * nrhs;
+    for (int j = lane; j < nrhs; j += 32) dst[j] = src[j];
   }
 }
 
