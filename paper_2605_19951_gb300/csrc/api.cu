@@ -101,6 +101,12 @@ struct tem_ctx {
   SimtTask *prod_simt = nullptr;
   void *tmaps = nullptr;                  // FP32: tensor maps of the factor blocks
   void *vmaps = nullptr;                  // FP32: tensor maps of the solve vectors
+  std::vector<int4> rcopy_h;              // FP32: row-major copy tasks (all levels)
+  int4 *rcopy = nullptr;
+  std::vector<int64_t> t11r_ofs_h, l21t_ofs_h;   // FP32: per front offsets of the row-major copies
+  int64_t *t11r_ofs = nullptr, *l21t_ofs = nullptr;
+  int64_t t11r_total = 0, l21t_total = 0;
+  void *T11R = nullptr, *L21T = nullptr;
   std::vector<int2> gather_h;             // FP32: update-row gather tasks (all levels)
   int2 *gather = nullptr;
   int64_t gather_rows = 0;                // rows of the gather buffer (max over levels)
@@ -292,11 +298,22 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
       const int r0 = k & ~1;   // even origin of the update rows (row k - 1 is padding when k is odd)
       if (mode == PM_TRI_F) {
         for (int i0 = 0; i0 < k; i0 += 64)
-          push(true, true, i0, 0, std::min(k, i0 + 64), std::min(64, k - i0), F.c0, F.c0 + i0, 0, 0);
+          push(false, true, i0, 0, std::min(k, i0 + 64), std::min(64, k - i0), F.c0, F.c0 + i0, 0, 0);
+        // tensor cores: 128 rows of the row-major T11 copy (run origin x = 0, row origin y = i0)
+        for (int i0 = 0; i0 < k; i0 += 128) {
+          push(true, false, 0, 0, std::min(k, i0 + 128), std::min(128, k - i0), F.c0, F.c0 + i0, 0, 0);
+          c->prod_h.back().y0 = i0;
+        }
       } else if (mode == PM_FWD21) {
-        if (b > 0)
+        if (b > 0) {
           for (int R = r0; R < F.n; R += 64)
-            push(true, true, R, 0, k, std::min(64, F.n - R), F.c0, (int)F.rows_off + R - k, std::max(0, k - R), 0);
+            push(false, true, R, 0, k, std::min(64, F.n - R), F.c0, (int)F.rows_off + R - k, std::max(0, k - R), 0);
+          // tensor cores: 128 rows of the row-major L21 copy
+          for (int i0 = 0; i0 < b; i0 += 128) {
+            push(true, false, 0, 0, k, std::min(128, b - i0), F.c0, (int)F.rows_off + i0, 0, 0);
+            c->prod_h.back().y0 = i0;
+          }
+        }
       } else if (mode == PM_BWD21) {
         // B rows: the SIMT kernel gathers rows[rows_off + kk - kfirst] (64-column
         // tiles), the tensor-core kernel reads the level's gather buffer at the
@@ -317,6 +334,18 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
     lv.n_prod_simt[mode] = int(c->prod_simt_h.size() - beg_s);
     lv.prod[mode] = (const TcTask *)(uintptr_t)beg;
     lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg_s;
+  }
+  // row-major copies of T11 and L21 (after the level's inversion)
+  {
+    const size_t beg = c->rcopy_h.size();
+    for (int32_t fi : L.fronts) {
+      const Front &F = S.fronts[fi];
+      if (F.k <= 0) continue;
+      for (int rb = 0; rb * 32 < F.k; rb++) c->rcopy_h.push_back(make_int4(fi, 0, rb, 0));
+      for (int rb = 0; rb * 32 < F.n - F.k; rb++) c->rcopy_h.push_back(make_int4(fi, 1, rb, 0));
+    }
+    lv.n_rcopy = int(c->rcopy_h.size() - beg);
+    lv.rcopy = (const int4 *)(uintptr_t)beg;
   }
   // inversion: 32-blocks, then pairwise merges of blocks of 32 * 2^stage
   const size_t dbeg = c->invdiag_h.size();
@@ -372,6 +401,19 @@ void build_steps(tem_ctx *c) {
   c->prod_simt_h.clear();
   c->gather_h.clear();
   c->gather_rows = 0;
+  c->rcopy_h.clear();
+  // row-major copy layout: per front k x ld2 (T11) and b x ld2 (L21), ld2 = k rounded up to even
+  c->t11r_ofs_h.assign(S.fronts.size(), 0);
+  c->l21t_ofs_h.assign(S.fronts.size(), 0);
+  c->t11r_total = c->l21t_total = 0;
+  for (size_t f = 0; f < S.fronts.size(); f++) {
+    const Front &F = S.fronts[f];
+    const int64_t ld2 = F.k + (F.k & 1);
+    c->t11r_ofs_h[f] = c->t11r_total;
+    c->l21t_ofs_h[f] = c->l21t_total;
+    c->t11r_total += int64_t(F.k) * ld2;
+    c->l21t_total += int64_t(F.n - F.k) * ld2;
+  }
   c->inv_h.clear();
   c->invdiag_h.clear();
   c->yscr_stride = 0;
@@ -483,6 +525,12 @@ FactorPlan<R> factor_plan(tem_ctx *c) {
   P.N = c->mesh.N;
   P.yscr = (cx<R> *)c->yscr;
   P.yscr_stride = c->yscr_stride;
+  P.T11R = (cx<R> *)c->T11R;
+  P.L21T = (cx<R> *)c->L21T;
+  P.t11r_stride = std::max<int64_t>(1, c->t11r_total);
+  P.l21t_stride = std::max<int64_t>(1, c->l21t_total);
+  P.t11r_ofs = c->t11r_ofs;
+  P.l21t_ofs = c->l21t_ofs;
   return P;
 }
 
@@ -606,12 +654,17 @@ int ensure_numeric(tem_ctx *c) {
     TRY(dalloc(c, &c->xdf, size_t(m) * N * nx));
     TRY(dalloc(c, &c->colmax_f, size_t(m) * nx));
     TRY(dalloc(c, (c64 **)&c->yscr, size_t(m) * std::max<int64_t>(1, c->yscr_stride)));
+    TRY(dalloc(c, (c64 **)&c->T11R, size_t(m) * std::max<int64_t>(1, c->t11r_total)));
+    TRY(dalloc(c, (c64 **)&c->L21T, size_t(m) * std::max<int64_t>(1, c->l21t_total)));
     std::vector<FrontGeom> geo(c->sym.fronts.size());
     for (size_t i = 0; i < geo.size(); i++) {
       const Front &F = c->sym.fronts[i];
-      geo[i] = FrontGeom{F.lofs, F.n, F.k, F.ld};
+      geo[i] = FrontGeom{F.lofs, c->t11r_ofs_h[i], c->l21t_ofs_h[i], F.n, F.k, F.ld, F.k + (F.k & 1)};
     }
-    const std::string e = build_tensor_maps(geo, (const c64 *)c->L, c->sym.ltotal, m, &c->tmaps);
+    const FactorViews views{(const c64 *)c->L, c->sym.ltotal, (const c64 *)c->T11R,
+                            std::max<int64_t>(1, c->t11r_total), (const c64 *)c->L21T,
+                            std::max<int64_t>(1, c->l21t_total)};
+    const std::string e = build_tensor_maps(geo, views, m, &c->tmaps);
     if (!e.empty()) return fail(c, TEM_ERR_CUDA, e);
     c->allocs.push_back(c->tmaps);
     TRY(dalloc(c, (c64 **)&c->Xg, size_t(m) * std::max<int64_t>(1, c->gather_rows) * nx));
@@ -737,6 +790,9 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->prod, c->prod_h));
   TRY(upload(c, &c->prod_simt, c->prod_simt_h));
   TRY(upload(c, &c->gather, c->gather_h));
+  TRY(upload(c, &c->rcopy, c->rcopy_h));
+  TRY(upload(c, &c->t11r_ofs, c->t11r_ofs_h));
+  TRY(upload(c, &c->l21t_ofs, c->l21t_ofs_h));
   TRY(upload(c, &c->inv, c->inv_h));
   TRY(upload(c, &c->invdiag, c->invdiag_h));
   for (LevelDev &lv : c->levels) {
@@ -747,6 +803,7 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
       lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
     }
     lv.gather = c->gather + (uintptr_t)lv.gather;
+    lv.rcopy = c->rcopy + (uintptr_t)lv.rcopy;
     lv.inv_diag = c->invdiag + (uintptr_t)lv.inv_diag;
     for (auto &st : lv.inv) st.tasks = c->inv + (uintptr_t)st.tasks;
     for (auto &sb : lv.sb) {

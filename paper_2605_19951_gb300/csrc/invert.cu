@@ -11,7 +11,9 @@
 // Blocks that are merged are never read again by another pair of the same
 // stage, so each stage is two launches over all fronts of the level.  The
 // diagonal, which still holds D during the merges (read as 1 by the
-// products), is finally moved to dinv = D^-1 and set to 1.
+// products), is finally moved to dinv = D^-1 and set to 1.  Last, T11 and
+// L21 are copied row-major (rows contiguous) for the tensor-core forward
+// products, which read them along rows.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -158,6 +160,42 @@ __global__ void k_inv_finish(c64 *__restrict__ L, int64_t lstride, const FrontDe
   }
 }
 
+// Row-major copies of a level's pivot-block inverses and update rows:
+// T11R[i][c] = T11[i][c] (zero for c > i) and L21T[i][c] = L21[i][c], rows of
+// ld2 = k rounded up to even entries; 32 x 32 tiles through shared memory.
+// Task: (front, 0 = T11 / 1 = L21, 32-row block).
+__global__ void __launch_bounds__(256) k_row_copy(const c64 *__restrict__ L, int64_t lstride, c64 *__restrict__ T11R,
+                                                  int64_t tstride, c64 *__restrict__ L21T, int64_t rstride,
+                                                  const FrontDev *__restrict__ F, const int64_t *__restrict__ t11r_ofs,
+                                                  const int64_t *__restrict__ l21t_ofs, const int4 *__restrict__ tasks) {
+  const int4 t = tasks[blockIdx.x];
+  const int p = blockIdx.y;
+  const FrontDev f = F[t.x];
+  const int k = f.k, ld2 = k + (k & 1);
+  const bool l21 = t.y != 0;
+  const int nrows = l21 ? f.n - k : k, row0 = l21 ? k : 0;
+  const c64 *src = L + p * lstride + f.lofs;
+  c64 *dst = l21 ? L21T + p * rstride + l21t_ofs[t.x] : T11R + p * tstride + t11r_ofs[t.x];
+  __shared__ c64 tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = 32 * t.z + tx;
+  for (int cb = 0; cb < ld2; cb += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int c = cb + ty + 8 * q;
+      const bool ok = c < k && i < nrows && (l21 || c <= i);
+      tile[ty + 8 * q][tx] = ok ? src[int64_t(c) * f.ld + row0 + i] : mk<float>(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int r = 32 * t.z + ty + 8 * q, c = cb + tx;
+      if (r < nrows && c < ld2) dst[int64_t(r) * ld2 + c] = tile[tx][ty + 8 * q];
+    }
+    __syncthreads();
+  }
+}
+
 template <>
 void FactorPlan<float>::invert_level(const LevelDev &lv, cudaStream_t s) {
   if (lv.nf == 0) return;
@@ -175,6 +213,11 @@ void FactorPlan<float>::invert_level(const LevelDev &lv, cudaStream_t s) {
   }
   tem::count_launch();
   k_inv_finish<<<dim3(lv.nf, m), 256, 0, s>>>(L, lstride, F, lv.fronts, dinv, N);
+  if (lv.n_rcopy > 0 && T11R) {
+    tem::count_launch();
+    k_row_copy<<<dim3(lv.n_rcopy, m), 256, 0, s>>>(L, lstride, T11R, t11r_stride, L21T, l21t_stride, F, t11r_ofs,
+                                                   l21t_ofs, lv.rcopy);
+  }
   if (g_prof) g_prof->end(KC_INVERT, s);
 }
 

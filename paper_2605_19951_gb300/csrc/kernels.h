@@ -132,6 +132,9 @@ struct LevelDev {
   // gather buffer, for the fronts with update rows
   const int2 *gather = nullptr;
   int n_gather = 0;
+  // FP32 factorisation: (front, 0 = T11 / 1 = L21, 32-row block) of the row-major copies
+  const int4 *rcopy = nullptr;
+  int n_rcopy = 0;
 };
 
 template <typename R>
@@ -160,6 +163,9 @@ struct FactorPlan {
   int64_t N = 0;
   cx<R> *yscr = nullptr;            // inversion scratch [m][yscr_stride]
   int64_t yscr_stride = 0;
+  cx<R> *T11R = nullptr, *L21T = nullptr;   // row-major copies for the tensor-core products
+  int64_t t11r_stride = 0, l21t_stride = 0;
+  const int64_t *t11r_ofs = nullptr, *l21t_ofs = nullptr;   // per front
   void level(int h, const LevelDev &lv, cudaStream_t s);
   void invert_level(const LevelDev &lv, cudaStream_t s);
 };
@@ -203,11 +209,19 @@ int tc_ctas_per_sm();
 // Tensor maps of every front's factor block (4 per front, index 4 f + mode)
 // in a new device array (*out, cudaFree by the caller); "" on success.
 struct FrontGeom {
-  int64_t lofs;
-  int32_t n, k, ld;
+  int64_t lofs, t11r_ofs, l21t_ofs;
+  int32_t n, k, ld, ld2;
 };
-std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
-                              void **out);
+// The factor store and its row-major copies (FP32 mode), pole strides in elements.
+struct FactorViews {
+  const c64 *L;
+  int64_t lstride;
+  const c64 *T11R;     // per front k x ld2, row i = T11[i][0..k) (zero above the diagonal)
+  int64_t t11r_stride;
+  const c64 *L21T;     // per front b x ld2, row i = L21[i][0..k)
+  int64_t l21t_stride;
+};
+std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const FactorViews &v, int m, void **out);
 // Maps over [pole][rows][nrhs] complex vectors (pole stride rows * nrhs), in order.
 struct VecBuf {
   const c64 *base;

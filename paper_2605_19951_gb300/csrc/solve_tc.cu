@@ -5,32 +5,26 @@
 //   forward, per level:  TRI_F (X_piv = T11 Y_piv), FWD21 (Y_upd -= L21 X_piv)
 //   backward, per level: BWD21 (Y_piv = D^-1 X_piv - L21^T X_upd), TRI_B (X_piv = T11^T Y_piv)
 //
-// Tensor-core kernel (k_tc_prod): a complex product C = A B is one real GEMM
-// with the rows of A interleaved as (re, im) real rows and the 32 complex
-// right-hand sides as 64 real columns: P[2i+a][2j+b] = sum A_a(i,.) B_b(.,j),
-// re C(i,j) = P[2i][2j] - P[2i+1][2j+1], im C(i,j) = P[2i][2j+1] + P[2i+1][2j].
-// Operands are split into TF32 hi + lo parts and three MMAs (hi.hi + hi.lo +
-// lo.hi, kind::tf32, FP32 accumulation) give FP32 accuracy.
-//
-// One persistent CTA per SM slot walks a static list of (tile, pole, RHS
-// chunk) items; each item is a 128 x 64 real output tile streamed over its
-// inner dimension in chunks of 16:
-//   warp 8 l1 (loader) issues the TMA loads of each chunk (the A box from
-//              the front's tensor map, the B rows from the vector's map)
-//              into a ring of NRAW shared slots as soon as a slot is released;
-//   warps 0-3  (producers) copy a chunk into registers, release the slot and
-//              split it:
-//              A hi/lo -> tensor memory (tcgen05.st, thread = TMEM lane =
-//              real row), B hi/lo -> shared memory (K-major core matrices);
-//   warp 8     issues the MMAs of a chunk (A from TMEM, B from shared) into
-//              one of two TMEM accumulators and commits to the stage's
-//              "empty" barrier and, after an item's last chunk, to "accf";
-//   warps 4-7  (epilogue) read the accumulator of the previous item, release
-//              it ("acce") and combine / store / atomically subtract the
-//              results while the next item accumulates.
+// Tensor-core kernel (k_tc_kint): one persistent CTA per SM slot (two per
+// SM) walks a static list of (tile, pole, RHS chunk) items; each item is 128
+// output indices (TMEM lanes) x 32 right-hand sides, streamed over its inner
+// dimension in chunks of 16 complex values.  Both operands are split into
+// TF32 hi + lo parts and three MMAs (hi.hi + hi.lo + lo.hi, kind::tf32, FP32
+// accumulation) give FP32 accuracy; the factor's hi part is the raw FP32
+// value itself (the tensor core truncates its inputs to TF32), so only lo is
+// formed.  Roles:
+//   warp 8 l1 (loader) issues the TMA loads of each chunk (the factor box
+//              from the front's tensor map, the B rows from the vector's map)
+//              into a ring of slots once the MMAs have freed the slot;
+//   warps 0-3  (producers) form the factor's lo part (into TMEM, thread =
+//              lane) and the B operand's hi / lo parts (shared memory);
+//   warp 8 l0  issues the MMAs (factor hi from the slot, lo from TMEM, B
+//              from shared memory) into one of two TMEM accumulators;
+//   warps 4-7  (epilogue) read the accumulator of the previous item and
+//              store / atomically subtract while the next item accumulates.
 // Every wait is bounded: a wait that gives up raises the CTA's abort flag and
 // the status word, all roles wind down, the MMA issuer drains its
-// outstanding MMAs and the TMEM is released.
+// outstanding MMAs, in-flight loads land and the TMEM is released.
 //
 // The SIMT kernel (k_prod_simt) computes the same products on the FP32 pipes.
 #include <cstring>
@@ -43,38 +37,22 @@
 namespace tem {
 
 namespace {
-constexpr int TKC = 16;       // inner dimension per chunk (two MMA k-steps)
-constexpr int NRAW = 6;       // raw ring depth (NRAW - 1 chunks in flight)
-constexpr int NST = 4;        // TMEM A stages / shared B stages
-constexpr int NTHR = 288;     // 4 producer + 4 epilogue + 1 MMA warp
-constexpr int RAWA = 2048;    // floats per raw A slot: 16 x 128 (column-major) or 64 x 32 (row-major, 128B swizzle)
-constexpr int RAWB = TKC * 64;
-constexpr uint32_t TMEM_COLS = 256;
-constexpr uint32_t COL_A = 128;   // A stages after the two 64-column accumulators
+constexpr int NTHR = 288;     // 4 producer + 4 epilogue warps, MMA issuer and loader in warp 8
 constexpr uint32_t kWaitIter = 1u << 26;
 constexpr unsigned kFull = 0xffffffffu;
 
-struct TcShared {
-  float rawA[NRAW][RAWA];         // 8 KB slots, 1024-byte aligned (swizzle atoms)
-  float rawB[NRAW][RAWB];
-  float Bs[NST][2][64 * TKC];     // hi, lo (K-major, no swizzle)
-  uint64_t full[NST], empty[NST], accf[2], acce[2], fin;
-  uint64_t rawfull[NRAW], rawempty[NRAW];
-  int kval[NRAW], kfst[NRAW];     // valid inner indices [kfst, kval) of the chunk in each raw slot
-  uint32_t tmem;
-  int abort;
-};
-constexpr size_t kTcSmem = sizeof(TcShared) + 1024;   // + alignment slack of the dynamic base
-
+// modes whose factor operand is read along its columns in the column-major
+// store (the SIMT kernel; the tensor-core kernel reads the row-major copies
+// for the other two)
 __host__ __device__ constexpr bool row_major(int mode) { return mode == PM_BWD21 || mode == PM_TRI_B; }
-// (the SIMT kernel gathers BWD21's B rows itself; the tensor-core kernel reads them pre-gathered)
+// the SIMT kernel gathers BWD21's B rows itself; the tensor-core kernel reads them pre-gathered
 __host__ __device__ constexpr bool gathered_b(int mode) { return mode == PM_BWD21; }
 
 struct ProdArgs {
   const c64 *L;
   int64_t lstride;
   const TcTask *tasks;
-  int ntask;         // tensor-core tiles
+  int ntask;         // tensor-core tiles (128 wide)
   int ntask_simt;    // SIMT tiles (64 wide)
   const int32_t *rows;
   const c64 *B;      // source of the B rows
@@ -82,7 +60,7 @@ struct ProdArgs {
   const c64 *xaux;   // BWD21: X (the D^-1 X term)
   const c64 *dinv;   // BWD21: [pole][N]
   const CUtensorMap *tmaps;
-  const CUtensorMap *bmap;   // contiguous B rows by TMA (nullptr: cp.async)
+  const CUtensorMap *bmap;   // B rows by TMA
   int64_t N;
   int64_t vstride;   // pole stride of the outputs (and of B, except BWD21 on the tensor cores)
   int64_t bstride;   // pole stride of the B rows
@@ -125,7 +103,7 @@ __device__ __forceinline__ Item load_item(const ProdArgs &a, int j) {
   it.t.obase = w1.z;
   it.t.mfirst = int16_t(w1.w & 0xffff);
   it.t.kfirst = int16_t(uint32_t(w1.w) >> 16);
-  it.nch = (it.t.kdim + TKC - 1) / TKC;
+  it.nch = 0;
   return it;
 }
 
@@ -140,311 +118,16 @@ __device__ __forceinline__ void split4(float *hi, float *lo, int off, const floa
   *reinterpret_cast<float4 *>(lo + off) = make_float4(tc::to_tf32(v[0] - h.x), tc::to_tf32(v[1] - h.y),
                                                       tc::to_tf32(v[2] - h.z), tc::to_tf32(v[3] - h.w));
 }
-
-__device__ __forceinline__ bool wait_bar(TcShared &sh, uint64_t *bar, uint32_t parity, DevStatus *st) {
-  if (tc::mbar_wait_or_abort(bar, parity, kWaitIter, &sh.abort)) return true;
-  sh.abort = 1;
-  atomicExch(&st->tc_timeout, 1);
-  return false;
-}
-
-__device__ __forceinline__ bool aborted(TcShared &sh) { return *reinterpret_cast<volatile int *>(&sh.abort) != 0; }
-
-// ---------------------------------------------------------------------------
-// producers (warps 0-3, thread t = real row t of the tile)
-
-// Loader (warp 8, lane 1): the TMA loads of every chunk (A box and B rows),
-// in order, into raw slot gc % NRAW once the producers have released it.
-template <int MODE>
-__device__ void loader(const ProdArgs &a, TcShared &sh) {
-  int gc = 0;
-  bool ok = true;
-  Item nxt = load_item(a, 0);
-#pragma unroll 1
-  for (int j = 0; ok; j++) {
-    const Item it = nxt;
-    if (!it.valid) break;
-    nxt = load_item(a, j + 1);
-    const TcTask &t = it.t;
-#pragma unroll 1
-    for (int c = 0; c < it.nch; c++, gc++) {
-      const int slot = gc % NRAW;
-      if (gc >= NRAW && !wait_bar(sh, &sh.rawempty[slot], ((gc / NRAW) - 1) & 1, a.st)) {
-        ok = false;
-        break;
-      }
-      const int k0 = c * TKC;
-      sh.kval[slot] = min(TKC, t.kdim - k0);
-      sh.kfst[slot] = max(0, int(t.kfirst) - k0);
-      tc::mbar_arrive_expect_tx(&sh.rawfull[slot], (RAWA + RAWB) * 4);
-      const bool colmaj = !row_major(MODE);
-      tc::tma_load_3d(sh.rawA[slot], a.tmaps + t.map, colmaj ? t.x0 : t.x0 + 2 * k0, colmaj ? t.y0 + k0 : t.y0,
-                      it.p, &sh.rawfull[slot]);
-      tc::tma_load_3d(sh.rawB[slot], a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
-    }
-  }
-  if (!ok)
-    for (int q = max(0, gc - NRAW); q < gc; q++) tc::mbar_wait(&sh.rawfull[q % NRAW], (q / NRAW) & 1, kWaitIter);
-}
-
-template <int MODE>
-__device__ void producer(const ProdArgs &a, TcShared &sh, int tid) {
-  const int w = tid >> 5, l = tid & 31;
-  int g = 0;
-  int pend = -1;   // stage whose TMEM / shared stores are in flight, signalled one chunk later
-  bool ok = true;
-#pragma unroll 1
-  for (int j = 0; ok; j++) {
-    const Item it = load_item(a, j);
-    if (!it.valid) break;
-#pragma unroll 1
-    for (int c = 0; c < it.nch; c++, g++) {
-      const int slot = g % NRAW;
-      ok = wait_bar(sh, &sh.rawfull[slot], (g / NRAW) & 1, a.st);
-      if (!__all_sync(kFull, ok)) {
-        ok = false;
-        break;
-      }
-      // copy the chunk into registers and release the slot at once: A row tid
-      // (16 values) and B columns l, l + 32 of rows 4w..4w+3, zero outside [kfst, kval)
-      float v[TKC], b0[4], b1[4];
-      if (!row_major(MODE)) {
-#pragma unroll
-        for (int kk = 0; kk < TKC; kk++) v[kk] = sh.rawA[slot][kk * 128 + tid];
-      } else {
-        // row c of the 64 x 32-float box, 16-byte chunks swizzled by c & 7
-        const int cc = tid >> 1, sw = cc & 7;
-        const float *src = sh.rawA[slot] + cc * 32 + (tid & 1);
-#pragma unroll
-        for (int e = 0; e < TKC; e++) v[e] = src[(((e >> 1) ^ sw) << 2) + 2 * (e & 1)];
-      }
-      {
-        const int kv = sh.kval[slot], kf = sh.kfst[slot];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int r = 4 * w + q;
-          const bool in = r < kv && r >= kf;
-          b0[q] = in ? sh.rawB[slot][r * 64 + l] : 0.f;
-          b1[q] = in ? sh.rawB[slot][r * 64 + 32 + l] : 0.f;
-        }
-      }
-      tc::mbar_arrive(&sh.rawempty[slot]);
-      // the previous chunk's stores had this chunk's loads to land
-      if (pend >= 0) {
-        tc::tmem_st_wait();
-        tc::fence_async_smem();
-        tc::fence_before();
-        tc::mbar_arrive(&sh.full[pend]);
-        pend = -1;
-      }
-      // stage s must have been consumed by the MMAs of chunk g - NST
-      const int s = g % NST, use = g / NST;
-      if (use > 0) ok = wait_bar(sh, &sh.empty[s], (use - 1) & 1, a.st);
-      if (!__all_sync(kFull, ok)) {
-        ok = false;
-        break;
-      }
-      tc::fence_after();
-      const uint32_t ta = sh.tmem + (uint32_t(w * 32) << 16) + COL_A + 32 * s;
-      {
-        float lo[TKC];
-#pragma unroll
-        for (int kk = 0; kk < TKC; kk++) {
-          const float h = tc::to_tf32(v[kk]);
-          lo[kk] = tc::to_tf32(v[kk] - h);
-          v[kk] = h;
-        }
-        tc::tmem_st16(ta, v);
-        tc::tmem_st16(ta + 16, lo);
-      }
-      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l, 4 * w, 64), b0);
-      split4(sh.Bs[s][0], sh.Bs[s][1], kmaj_off(l + 32, 4 * w, 64), b1);
-      pend = s;
-      if (__any_sync(kFull, aborted(sh))) {
-        ok = false;
-        break;
-      }
-    }
-  }
-  tc::tmem_st_wait();
-  if (pend >= 0 && ok) {
-    tc::fence_async_smem();
-    tc::fence_before();
-    tc::mbar_arrive(&sh.full[pend]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// MMA issuer (one thread of warp 8)
-
-__device__ void mma_issuer(const ProdArgs &a, TcShared &sh) {
-  const uint32_t idesc = tc::idesc_tf32(128, 64);
-  int g = 0;
-  bool ok = true;
-  Item nxt = load_item(a, 0);
-#pragma unroll 1
-  for (int j = 0; ok; j++) {
-    const Item it = nxt;
-    if (!it.valid) break;
-    nxt = load_item(a, j + 1);
-    const int buf = j & 1, use = j >> 1;
-    if (use > 0 && !wait_bar(sh, &sh.acce[buf], (use - 1) & 1, a.st)) break;
-    tc::fence_after();
-    const uint32_t d = sh.tmem + 64 * buf;
-#pragma unroll 1
-    for (int c = 0; c < it.nch; c++, g++) {
-      const int s = g % NST;
-      if (!wait_bar(sh, &sh.full[s], (g / NST) & 1, a.st)) {
-        ok = false;
-        break;
-      }
-      tc::fence_after();
-#pragma unroll
-      for (int ks = 0; ks < TKC / 8; ks++) {
-        const uint32_t ah = sh.tmem + COL_A + 32 * s + 8 * ks, al = ah + 16;
-        const uint64_t bh = tc::desc_kmajor(tc::smem_addr(&sh.Bs[s][0][ks * 64 * 8]), 128, 256);
-        const uint64_t bl = tc::desc_kmajor(tc::smem_addr(&sh.Bs[s][1][ks * 64 * 8]), 128, 256);
-        tc::mma_tf32_ts(d, ah, bh, idesc, c > 0 || ks > 0);
-        tc::mma_tf32_ts(d, ah, bl, idesc, true);
-        tc::mma_tf32_ts(d, al, bh, idesc, true);
-      }
-      tc::commit(&sh.empty[s]);
-    }
-    if (!ok) break;
-    tc::commit(&sh.accf[buf]);
-  }
-  // drain: every MMA issued above has completed once fin arrives
-  tc::commit(&sh.fin);
-  if (!tc::mbar_wait(&sh.fin, 0, kWaitIter)) atomicExch(&a.st->tc_timeout, 1);
-}
-
-// ---------------------------------------------------------------------------
-// epilogue (warps 4-7; e = real row of the tile)
-
-template <int MODE>
-__device__ void epilogue(const ProdArgs &a, TcShared &sh, int e) {
-  const int we = e >> 5, half = e & 1;
-  Item nxt = load_item(a, 0);
-#pragma unroll 1
-  for (int j = 0;; j++) {
-    const Item it = nxt;
-    if (!it.valid) break;
-    nxt = load_item(a, j + 1);
-    const int buf = j & 1, use = j >> 1;
-    const bool ok = wait_bar(sh, &sh.accf[buf], use & 1, a.st);
-    if (!__all_sync(kFull, ok)) break;
-    tc::fence_after();
-    float v[64];
-    if (it.nch > 0) {
-      tc::tmem_ld64(sh.tmem + (uint32_t(we * 32) << 16) + 64 * buf, v);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 64; q++) v[q] = 0.f;
-    }
-    tc::fence_before();
-    tc::mbar_arrive(&sh.acce[buf]);
-    // lane pair (2i, 2i+1) = (re, im) row of complex row i; lane `half`
-    // finishes right-hand sides 16 half .. 16 half + 15
-    float E[32], O[32];
-#pragma unroll
-    for (int q = 0; q < 32; q++) {
-      const float mine = half ? v[32 + q] : v[q];
-      const float send = half ? v[q] : v[32 + q];
-      const float got = __shfl_xor_sync(kFull, send, 1);
-      E[q] = half ? got : mine;   // row 2i (re part of A)
-      O[q] = half ? mine : got;   // row 2i+1 (im part of A)
-    }
-    const int m = e >> 1;
-    if (m >= it.t.mrows || m < it.t.mfirst) continue;
-    const int ncols = min(32, a.nrhs - it.ch * 32);
-    const int j0 = 16 * half;
-    const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
-    if (MODE == PM_FWD21) {
-      const int32_t g = __ldg(a.rows + it.t.obase + m);
-      float2 *y = reinterpret_cast<float2 *>(a.out + pv + int64_t(g) * a.nrhs);
-      if ((a.nrhs & 1) == 0) {
-        // two right-hand sides per 16-byte atomic (rows start on 16-byte boundaries)
-#pragma unroll
-        for (int q = 0; q < 16; q += 2) {
-          if (j0 + q + 1 < ncols)
-            atomicAdd(reinterpret_cast<float4 *>(y + j0 + q),
-                      make_float4(O[2 * q + 1] - E[2 * q], -(E[2 * q + 1] + O[2 * q]), O[2 * q + 3] - E[2 * q + 2],
-                                  -(E[2 * q + 3] + O[2 * q + 2])));
-          else if (j0 + q < ncols)
-            atomicAdd(y + j0 + q, make_float2(O[2 * q + 1] - E[2 * q], -(E[2 * q + 1] + O[2 * q])));
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; q++)
-          if (j0 + q < ncols)
-            atomicAdd(y + j0 + q, make_float2(O[2 * q + 1] - E[2 * q], -(E[2 * q + 1] + O[2 * q])));
-      }
-    } else if (MODE == PM_BWD21) {
-      const int64_t row = int64_t(it.t.obase) + m;
-      const c64 di = a.dinv[int64_t(it.p) * a.N + row];
-      const c64 *x = a.xaux + pv + row * a.nrhs;
-      c64 *y = a.out + pv + row * a.nrhs;
-#pragma unroll
-      for (int q = 0; q < 16; q++)
-        if (j0 + q < ncols) {
-          const c64 dx = di * x[j0 + q];
-          y[j0 + q] = mk<float>(dx.x - (E[2 * q] - O[2 * q + 1]), dx.y - (E[2 * q + 1] + O[2 * q]));
-        }
-    } else {
-      // rows start on 16-byte boundaries (even nrhs on the tensor cores): two right-hand sides per store
-      float4 *y = reinterpret_cast<float4 *>(a.out + pv + (int64_t(it.t.obase) + m) * a.nrhs + j0);
-#pragma unroll
-      for (int q = 0; q < 16; q += 2)
-        if (j0 + q < ncols)
-          y[q >> 1] = make_float4(E[2 * q] - O[2 * q + 1], E[2 * q + 1] + O[2 * q], E[2 * q + 2] - O[2 * q + 3],
-                                  E[2 * q + 3] + O[2 * q + 2]);
-    }
-  }
-}
-
 }  // namespace
 
-template <int MODE>
-__global__ void __launch_bounds__(NTHR, 2) k_tc_prod(const ProdArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcShared &sh = *reinterpret_cast<TcShared *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 8) tc::tmem_alloc(&sh.tmem, TMEM_COLS);
-  if (tid == 0) {
-    for (int s = 0; s < NST; s++) {
-      tc::mbar_init(&sh.full[s], 128);
-      tc::mbar_init(&sh.empty[s], 1);
-    }
-    for (int b = 0; b < 2; b++) {
-      tc::mbar_init(&sh.accf[b], 1);
-      tc::mbar_init(&sh.acce[b], 128);
-    }
-    tc::mbar_init(&sh.fin, 1);
-    for (int r = 0; r < NRAW; r++) {
-      tc::mbar_init(&sh.rawfull[r], 1);
-      tc::mbar_init(&sh.rawempty[r], 128);
-    }
-    sh.abort = 0;
-    tc::fence_async_smem();
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (warp < 4) producer<MODE>(a, sh, tid);
-  else if (warp < 8) epilogue<MODE>(a, sh, tid - 128);
-  else if ((tid & 31) == 0) mma_issuer(a, sh);
-  else if ((tid & 31) == 1) loader<MODE>(a, sh);
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (warp == 8) tc::tmem_dealloc(sh.tmem, TMEM_COLS);
-}
-
 // ---------------------------------------------------------------------------
-// Transposed-access products (BWD21, TRI_B) with the inner dimension
-// interleaved: a factor column c (pivot column of the tile) is one TMEM lane
-// and its complex rows i give real inner indices (i, re) and (i, im), so the
-// raw TMA box of 128 columns x 16 complex rows (128-byte rows, 128-byte
+// Tensor-core products with the inner dimension interleaved.  The operand
+// is read along contiguous runs: BWD21 and TRI_B along a column of the
+// column-major store (their output index is the pivot column), TRI_F and
+// FWD21 along a row of the row-major copies of T11 and L21 (their output
+// index is the row).  One output index is one TMEM lane and its run of
+// complex inner indices i gives real inner indices (i, re) and (i, im), so
+// the raw TMA box of 128 runs x 16 complex values (128-byte rows, 128-byte
 // swizzle) is already a K-major operand.  The tensor core reads it directly
 // as the TF32 hi part (it truncates FP32 inputs to TF32, so hi = the raw
 // value and lo = x - trunc(x) exactly); the producers compute only lo (into
@@ -659,10 +342,14 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     if (m >= it.t.mrows) continue;
     const int ncols = min(32, a.nrhs - it.ch * 32);
     const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
-    const int64_t row = int64_t(it.t.obase) + m;
+    const int64_t row = MODE == PM_FWD21 ? int64_t(__ldg(a.rows + it.t.obase + m)) : int64_t(it.t.obase) + m;
     // rows start on 16-byte boundaries (even nrhs): two right-hand sides per access
     float4 *y = reinterpret_cast<float4 *>(a.out + pv + row * a.nrhs);
-    if (MODE == PM_BWD21) {
+    if (MODE == PM_FWD21) {
+#pragma unroll
+      for (int q = 0; q < 16; q++)
+        if (2 * q < ncols) atomicAdd(y + q, make_float4(-v[4 * q], -v[4 * q + 1], -v[4 * q + 2], -v[4 * q + 3]));
+    } else if (MODE == PM_BWD21) {
       const c64 di = a.dinv[int64_t(it.p) * a.N + row];
       const float4 *x = reinterpret_cast<const float4 *>(a.xaux + pv + row * a.nrhs);
 #pragma unroll
@@ -816,33 +503,24 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
   if (use_tc) {
     static int grid_max = 0;
     if (grid_max == 0) {
-      int dev = 0, sms = 0, occ = 0;
+      int dev = 0, sms = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaFuncSetAttribute(k_tc_prod<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
-      // all of the unified L1 / shared storage as shared memory: two CTAs per SM
-      cudaFuncSetAttribute(k_tc_prod<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      if constexpr (row_major(MODE)) {
-        cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kKiSmem));
-        cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      }
-      static_assert(2 * (kKiSmem + 1024) <= 228 * 1024, "two CTAs per SM must fit in shared memory");
+      cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kKiSmem));
+      // all of the unified L1 / shared storage as shared memory
+      cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       // Two CTAs per SM: 256 of the 512 TMEM columns, under half of the shared
       // memory and 2 x 288 x 96 registers each.  (The occupancy calculator
       // reports one for this 9-warp block; two are resident, as measured by
       // counting CTAs per SM.)
-      static_assert(2 * (kTcSmem + 1024) <= 228 * 1024, "two CTAs per SM must fit in shared memory");
-      occ = 2;
-      g_tc_occupancy = occ;
-      grid_max = occ * (sms > 0 ? sms : 1);
+      static_assert(2 * (kKiSmem + 1024) <= 228 * 1024, "two CTAs per SM must fit in shared memory");
+      g_tc_occupancy = 2;
+      grid_max = 2 * (sms > 0 ? sms : 1);
     }
     const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
     const int grid = int(total < grid_max ? total : grid_max);
     tem::count_launch();
-    if constexpr (row_major(MODE))
-      k_tc_kint<MODE><<<grid, NTHR, kKiSmem, s>>>(a);
-    else
-      k_tc_prod<MODE><<<grid, NTHR, kTcSmem, s>>>(a);
+    k_tc_kint<MODE><<<grid, NTHR, kKiSmem, s>>>(a);
   } else {
     dim3 g(a.ntask_simt, a.np * a.nchunk);
     tem::count_launch();
@@ -923,14 +601,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 }  // namespace
 
-// Per front, four maps over its factor block viewed as floats: dim 0 runs
-// along a column (2 floats per complex entry; rows k..n-1 excluded for the
-// pivot-block maps 0 and 3), dim 1 over the k columns, dim 2 over the poles.
-// Maps 0/1 (column-major tiles) load 16 columns x 64 complex rows; maps 2/3
-// (row-major tiles) load 128 columns x 16 complex rows with the 128-byte
-// swizzle.  Entries outside the dims read as zero.
-std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, int m,
-                              void **out) {
+// Per front, four maps, each 3-D over floats (two per complex entry) with
+// 128 runs x 16 complex values per box and the 128-byte swizzle; entries
+// outside the dims read as zero:
+//   TRI_F: rows of the row-major T11 copy (run = row, k entries, k rows),
+//   FWD21: rows of the row-major L21 copy (b rows of k entries),
+//   BWD21: columns of the column-major store (rows 0..n-1 of each of the k columns),
+//   TRI_B: columns of the column-major store restricted to the pivot rows 0..k-1.
+std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const FactorViews &v, int m, void **out) {
   *out = nullptr;
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
@@ -946,19 +624,26 @@ std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const c64 *L
   memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
   for (size_t i = 0; i < fronts.size(); i++) {
     const FrontGeom &f = fronts[i];
+    const int b = f.n - f.k;
     if (f.k <= 0) continue;
     for (int kind = 0; kind < 4; kind++) {
-      const bool tri = (kind == PM_TRI_F || kind == PM_TRI_B);
-      const bool colmaj = !row_major(kind);
-      const cuuint64_t dims[3] = {cuuint64_t(2) * (tri ? f.k : f.n), cuuint64_t(f.k), cuuint64_t(m)};
-      const cuuint64_t strides[2] = {cuuint64_t(f.ld) * sizeof(c64), cuuint64_t(lstride) * sizeof(c64)};
-      const cuuint32_t box[3] = {colmaj ? 128u : 32u, colmaj ? 16u : 128u, 1u};
+      const c64 *base;
+      cuuint64_t runlen, runs, stride, pstride;
+      if (kind == PM_TRI_F) {
+        base = v.T11R + f.t11r_ofs, runlen = f.k, runs = f.k, stride = f.ld2, pstride = v.t11r_stride;
+      } else if (kind == PM_FWD21) {
+        if (b <= 0) continue;
+        base = v.L21T + f.l21t_ofs, runlen = f.k, runs = b, stride = f.ld2, pstride = v.l21t_stride;
+      } else {
+        base = v.L + f.lofs, runlen = kind == PM_TRI_B ? f.k : f.n, runs = f.k, stride = f.ld, pstride = v.lstride;
+      }
+      const cuuint64_t dims[3] = {2 * runlen, runs, cuuint64_t(m)};
+      const cuuint64_t strides[2] = {stride * sizeof(c64), pstride * sizeof(c64)};
+      const cuuint32_t box[3] = {32u, 128u, 1u};
       const cuuint32_t estr[3] = {1, 1, 1};
-      const CUresult r =
-          encode(&maps[4 * i + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(L + f.lofs), dims,
-                 strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                 colmaj ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      const CUresult r = encode(&maps[4 * i + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(base),
+                                dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed for front " + std::to_string(i);
     }
   }
