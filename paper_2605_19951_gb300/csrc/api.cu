@@ -95,6 +95,8 @@ struct tem_ctx {
   int2 *f21 = nullptr, *b21 = nullptr;
   std::vector<int4> sbf_h, sbb_h;         // task lists of the super-block products
   int4 *sbf = nullptr, *sbb = nullptr;
+  std::vector<int32_t> order_h;           // FP32: tensor-core tasks per level and mode, longest first
+  int32_t *order = nullptr;
   std::vector<TcTask> prod_h;             // FP32: front-product tasks (all levels and modes)
   TcTask *prod = nullptr;
   std::vector<SimtTask> prod_simt_h;      // the same tiles for the SIMT products
@@ -107,8 +109,8 @@ struct tem_ctx {
   int64_t *t11r_ofs = nullptr, *l21t_ofs = nullptr;
   int64_t t11r_total = 0, l21t_total = 0;
   void *T11R = nullptr, *L21T = nullptr;
-  std::vector<int2> gather_h;             // FP32: update-row gather tasks (all levels)
-  int2 *gather = nullptr;
+  std::vector<int32_t> gather_h;          // FP32: source rows of every level's gather buffer
+  int32_t *gather = nullptr;
   int64_t gather_rows = 0;                // rows of the gather buffer (max over levels)
   void *Xg = nullptr;
   std::vector<InvTask> inv_h;             // FP32: pivot-block inversion tasks
@@ -251,13 +253,13 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
       const Front &F = S.fronts[fi];
       gofs[fi] = (int)rows;
       if (F.k > 0 && F.n > F.k) {
-        c->gather_h.push_back(make_int2(fi, (int)rows));
+        for (int32_t i = 0; i < F.n - F.k; i++) c->gather_h.push_back(S.rows[F.rows_off + i]);
         rows += F.n - F.k;
       }
     }
     c->gather_rows = std::max(c->gather_rows, rows);
-    lv.n_gather = int(c->gather_h.size() - beg);
-    lv.gather = (const int2 *)(uintptr_t)beg;
+    lv.n_gather_rows = int(c->gather_h.size() - beg);
+    lv.gather_src = (const int32_t *)(uintptr_t)beg;
   }
   for (int mode = 0; mode < PM_COUNT; mode++) {
     const size_t beg = c->prod_h.size(), beg_s = c->prod_simt_h.size();
@@ -332,6 +334,16 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
     }
     lv.n_prod[mode] = int(c->prod_h.size() - beg);
     lv.n_prod_simt[mode] = int(c->prod_simt_h.size() - beg_s);
+    // tensor-core tasks, longest inner dimension first
+    {
+      std::vector<int32_t> ord(lv.n_prod[mode]);
+      for (int t = 0; t < lv.n_prod[mode]; t++) ord[t] = t;
+      std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+        return c->prod_h[beg + x].kdim > c->prod_h[beg + y].kdim;
+      });
+      lv.order[mode] = (const int32_t *)(uintptr_t)c->order_h.size();
+      c->order_h.insert(c->order_h.end(), ord.begin(), ord.end());
+    }
     lv.prod[mode] = (const TcTask *)(uintptr_t)beg;
     lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg_s;
   }
@@ -399,6 +411,7 @@ void build_steps(tem_ctx *c) {
   c->sbb_h.clear();
   c->prod_h.clear();
   c->prod_simt_h.clear();
+  c->order_h.clear();
   c->gather_h.clear();
   c->gather_rows = 0;
   c->rcopy_h.clear();
@@ -434,6 +447,7 @@ void build_steps(tem_ctx *c) {
       lv.ea_end[s] = L.ea_end[s];
     }
     lv.bwd_upd_tiles = std::max(1, div_up(L.max_k, 8));
+    lv.max_k = L.max_k;
     lv.n_f21 = 0;
     lv.n_b21 = 0;
     const size_t f21_beg = c->f21_h.size(), b21_beg = c->b21_h.size();
@@ -788,6 +802,7 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->sbf, c->sbf_h));
   TRY(upload(c, &c->sbb, c->sbb_h));
   TRY(upload(c, &c->prod, c->prod_h));
+  TRY(upload(c, &c->order, c->order_h));
   TRY(upload(c, &c->prod_simt, c->prod_simt_h));
   TRY(upload(c, &c->gather, c->gather_h));
   TRY(upload(c, &c->rcopy, c->rcopy_h));
@@ -800,9 +815,10 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
     lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
     for (int mode = 0; mode < PM_COUNT; mode++) {
       lv.prod[mode] = c->prod + (uintptr_t)lv.prod[mode];
+      lv.order[mode] = c->order + (uintptr_t)lv.order[mode];
       lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
     }
-    lv.gather = c->gather + (uintptr_t)lv.gather;
+    lv.gather_src = c->gather + (uintptr_t)lv.gather_src;
     lv.rcopy = c->rcopy + (uintptr_t)lv.rcopy;
     lv.inv_diag = c->invdiag + (uintptr_t)lv.inv_diag;
     for (auto &st : lv.inv) st.tasks = c->inv + (uintptr_t)st.tasks;

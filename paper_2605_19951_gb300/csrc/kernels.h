@@ -118,6 +118,8 @@ struct LevelDev {
   // FP32 solves: front-product tasks per mode
   const TcTask *prod[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
   const SimtTask *prod_simt[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
+  // tensor-core task indices of the level, longest inner dimension first
+  const int32_t *order[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
   int n_prod[PM_COUNT] = {0, 0, 0, 0};        // tensor-core tiles (128 columns wide for BWD21 / TRI_B)
   int n_prod_simt[PM_COUNT] = {0, 0, 0, 0};   // SIMT tiles (64 wide)
   // FP32 factorisation: inversion of L11, per merge stage (block size 32 * 2^stage)
@@ -128,13 +130,13 @@ struct LevelDev {
   std::vector<InvStage> inv;
   const int2 *inv_diag = nullptr;   // (front, 32-block) of every diagonal block
   int n_inv_diag = 0;
-  // FP32 backward: (front, first row) of each front's update rows in the
-  // gather buffer, for the fronts with update rows
-  const int2 *gather = nullptr;
-  int n_gather = 0;
+  // FP32 backward: source row (in X) of each row of the level's gather buffer
+  const int32_t *gather_src = nullptr;
+  int n_gather_rows = 0;
   // FP32 factorisation: (front, 0 = T11 / 1 = L21, 32-row block) of the row-major copies
   const int4 *rcopy = nullptr;
   int n_rcopy = 0;
+  int max_k = 0;   // largest pivot count of the level's fronts
 };
 
 template <typename R>

@@ -52,6 +52,7 @@ struct ProdArgs {
   const c64 *L;
   int64_t lstride;
   const TcTask *tasks;
+  const int32_t *order; // task indices, longest first
   int ntask;         // tensor-core tiles (128 wide)
   int ntask_simt;    // SIMT tiles (64 wide)
   const int32_t *rows;
@@ -76,19 +77,27 @@ struct Item {
   bool valid;
 };
 
+// Item j of this CTA.  Items are the (task, pole, RHS chunk) triples with the
+// tasks in decreasing length; the CTAs take them in snake order (round j:
+// position j G + b, or j G + G - 1 - b on odd rounds), which balances items of
+// very different lengths over the grid.
 __device__ __forceinline__ Item load_item(const ProdArgs &a, int j) {
   Item it;
-  const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
-  const int64_t idx = int64_t(blockIdx.x) + int64_t(j) * gridDim.x;
-  it.valid = idx < total;
+  const int64_t G = gridDim.x, per = int64_t(a.np) * a.nchunk;
+  const int64_t pos = int64_t(j) * G + ((j & 1) ? G - 1 - blockIdx.x : blockIdx.x);
+  it.valid = pos < int64_t(a.ntask) * per;
+  int q = 0, ti = 0;
+  if (it.valid) {
+    const int64_t r = pos / per;
+    q = int(pos - r * per);
+    ti = __ldg(a.order + r);
+  }
   if (!it.valid) {
     it.nch = 0;
     it.p = it.ch = 0;
     it.t = TcTask{0, 0, 0, 0, 0, 0, 0, 0, 0};
     return it;
   }
-  const int q = int(idx / a.ntask);
-  const int ti = int(idx - int64_t(q) * a.ntask);
   const int ps = q / a.nchunk;
   it.ch = q - ps * a.nchunk;
   it.p = pole_of(ps, a.pmap);
@@ -473,26 +482,21 @@ __global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtT
   }
 }
 
-// Xg[p][g0 + i] = X[p][rows_i] for the update rows of each front of a level
-// (contiguous B rows for the backward L21 product); one CTA per (front,
-// pole), a warp per row at a time, lanes over right-hand sides.
+// Xg[p][g] = X[p][src[g]] for the g < n gather rows of a level (the update
+// rows of its fronts, front after front); a warp per row, lanes over
+// right-hand sides.
 __global__ void __launch_bounds__(256) k_gather_upd(const c64 *__restrict__ X, int64_t vstride, c64 *__restrict__ Xg,
-                                                    int64_t gstride, const FrontDev *__restrict__ F,
-                                                    const int32_t *__restrict__ rows, const int2 *__restrict__ tasks,
-                                                    int nrhs, const int *__restrict__ pmap) {
-  const int2 t = tasks[blockIdx.x];
-  const int p = pole_of(blockIdx.y, pmap);
-  const FrontDev f = F[t.x];
-  const int b = f.n - f.k;
-  const int32_t *ur = rows + f.rows_off;
-  const c64 *xp = X + p * vstride;
-  c64 *gp = Xg + p * gstride + int64_t(t.y) * nrhs;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < b; i += 8) {
-    const c64 *src = xp + int64_t(__ldg(ur + i)) * nrhs;
-    c64 *dst = gp + int64_t(i) * nrhs;
-    for (int j = lane; j < nrhs; j += 32) dst[j] = src[j];
-  }
+                                                    int64_t gstride, const int32_t *__restrict__ src, int64_t n,
+                                                    int nrhs, int np, const int *__restrict__ pmap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= n * np) return;
+  const int ps = int(w / n);
+  const int64_t g = w - int64_t(ps) * n;
+  const int p = pole_of(ps, pmap);
+  const c64 *from = X + p * vstride + int64_t(__ldg(src + g)) * nrhs;
+  c64 *to = Xg + p * gstride + g * nrhs;
+  for (int j = lane; j < nrhs; j += 32) to[j] = from[j];
 }
 
 namespace {
@@ -532,8 +536,10 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
 int tc_ctas_per_sm() { return g_tc_occupancy; }
 
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
-  // the tensor-core kernels load B rows by TMA, which needs 16-byte rows (an
-  // even number of right-hand sides); otherwise the SIMT kernels run
+  // The tensor-core kernel loads B rows by TMA, which needs 16-byte rows (an
+  // even number of right-hand sides); otherwise the SIMT kernels run.  (It is
+  // also faster than the SIMT kernel on levels of small fronts, where most of
+  // a 128-lane tile is idle.)
   const bool use_tc = P.use_tc && P.vmaps != nullptr;
   if ((use_tc ? lv.n_prod[mode] : lv.n_prod_simt[mode]) == 0 || P.np == 0) return;
   ProdArgs a;
@@ -542,6 +548,7 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
   a.tasks = lv.prod[mode];
   a.ntask = lv.n_prod[mode];
   a.ntask_simt = lv.n_prod_simt[mode];
+  a.order = lv.order[mode];
   a.rows = P.rows;
   a.N = P.N;
   a.vstride = P.vstride;
@@ -575,10 +582,11 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
       a.xaux = P.X;
       if (use_tc) {
         // the tensor-core kernel reads the update rows pre-gathered
-        if (lv.n_gather > 0) {
+        if (lv.n_gather_rows > 0) {
+          const int64_t warps = int64_t(lv.n_gather_rows) * P.np;
           tem::count_launch();
-          k_gather_upd<<<dim3(lv.n_gather, P.np), 256, 0, s>>>(P.X, P.vstride, P.Xg, P.gstride, P.F, P.rows,
-                                                               lv.gather, P.nrhs, P.pmap);
+          k_gather_upd<<<unsigned((warps + 7) / 8), 256, 0, s>>>(P.X, P.vstride, P.Xg, P.gstride, lv.gather_src,
+                                                                 lv.n_gather_rows, P.nrhs, P.np, P.pmap);
         }
         a.B = P.Xg;
         a.bstride = P.gstride;
