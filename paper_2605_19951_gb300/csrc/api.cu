@@ -95,8 +95,6 @@ struct tem_ctx {
   int2 *f21 = nullptr, *b21 = nullptr;
   std::vector<int4> sbf_h, sbb_h;         // task lists of the super-block products
   int4 *sbf = nullptr, *sbb = nullptr;
-  std::vector<int32_t> order_h;           // FP32: tensor-core tasks per level and mode, longest first
-  int32_t *order = nullptr;
   std::vector<TcTask> prod_h;             // FP32: front-product tasks (all levels and modes)
   TcTask *prod = nullptr;
   std::vector<SimtTask> prod_simt_h;      // the same tiles for the SIMT products
@@ -334,16 +332,9 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
     }
     lv.n_prod[mode] = int(c->prod_h.size() - beg);
     lv.n_prod_simt[mode] = int(c->prod_simt_h.size() - beg_s);
-    // tensor-core tasks, longest inner dimension first
-    {
-      std::vector<int32_t> ord(lv.n_prod[mode]);
-      for (int t = 0; t < lv.n_prod[mode]; t++) ord[t] = t;
-      std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
-        return c->prod_h[beg + x].kdim > c->prod_h[beg + y].kdim;
-      });
-      lv.order[mode] = (const int32_t *)(uintptr_t)c->order_h.size();
-      c->order_h.insert(c->order_h.end(), ord.begin(), ord.end());
-    }
+    // tensor-core tasks, longest inner dimension first (the kernel deals them out in this order)
+    std::stable_sort(c->prod_h.begin() + beg, c->prod_h.end(),
+                     [](const TcTask &x, const TcTask &y) { return x.kdim > y.kdim; });
     lv.prod[mode] = (const TcTask *)(uintptr_t)beg;
     lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg_s;
   }
@@ -411,7 +402,6 @@ void build_steps(tem_ctx *c) {
   c->sbb_h.clear();
   c->prod_h.clear();
   c->prod_simt_h.clear();
-  c->order_h.clear();
   c->gather_h.clear();
   c->gather_rows = 0;
   c->rcopy_h.clear();
@@ -802,7 +792,6 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->sbf, c->sbf_h));
   TRY(upload(c, &c->sbb, c->sbb_h));
   TRY(upload(c, &c->prod, c->prod_h));
-  TRY(upload(c, &c->order, c->order_h));
   TRY(upload(c, &c->prod_simt, c->prod_simt_h));
   TRY(upload(c, &c->gather, c->gather_h));
   TRY(upload(c, &c->rcopy, c->rcopy_h));
@@ -815,7 +804,6 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
     lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
     for (int mode = 0; mode < PM_COUNT; mode++) {
       lv.prod[mode] = c->prod + (uintptr_t)lv.prod[mode];
-      lv.order[mode] = c->order + (uintptr_t)lv.order[mode];
       lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
     }
     lv.gather_src = c->gather + (uintptr_t)lv.gather_src;

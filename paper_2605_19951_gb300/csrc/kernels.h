@@ -118,8 +118,6 @@ struct LevelDev {
   // FP32 solves: front-product tasks per mode
   const TcTask *prod[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
   const SimtTask *prod_simt[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
-  // tensor-core task indices of the level, longest inner dimension first
-  const int32_t *order[PM_COUNT] = {nullptr, nullptr, nullptr, nullptr};
   int n_prod[PM_COUNT] = {0, 0, 0, 0};        // tensor-core tiles (128 columns wide for BWD21 / TRI_B)
   int n_prod_simt[PM_COUNT] = {0, 0, 0, 0};   // SIMT tiles (64 wide)
   // FP32 factorisation: inversion of L11, per merge stage (block size 32 * 2^stage)

@@ -13,12 +13,12 @@
 // accumulation) give FP32 accuracy; the factor's hi part is the raw FP32
 // value itself (the tensor core truncates its inputs to TF32), so only lo is
 // formed.  Roles:
-//   warp 8 l1 (loader) issues the TMA loads of each chunk (the factor box
+//   warp 9    (loader) issues the TMA loads of each chunk (the factor box
 //              from the front's tensor map, the B rows from the vector's map)
 //              into a ring of slots once the MMAs have freed the slot;
 //   warps 0-3  (producers) form the factor's lo part (into TMEM, thread =
 //              lane) and the B operand's hi / lo parts (shared memory);
-//   warp 8 l0  issues the MMAs (factor hi from the slot, lo from TMEM, B
+//   warp 8     issues the MMAs (factor hi from the slot, lo from TMEM, B
 //              from shared memory) into one of two TMEM accumulators;
 //   warps 4-7  (epilogue) read the accumulator of the previous item and
 //              store / atomically subtract while the next item accumulates.
@@ -37,7 +37,7 @@
 namespace tem {
 
 namespace {
-constexpr int NTHR = 288;     // 4 producer + 4 epilogue warps, MMA issuer and loader in warp 8
+constexpr int NTHR = 320;     // 4 producer + 4 epilogue warps, MMA issuer (warp 8), TMA loader (warp 9)
 constexpr uint32_t kWaitIter = 1u << 26;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -52,7 +52,6 @@ struct ProdArgs {
   const c64 *L;
   int64_t lstride;
   const TcTask *tasks;
-  const int32_t *order; // task indices, longest first
   int ntask;         // tensor-core tiles (128 wide)
   int ntask_simt;    // SIMT tiles (64 wide)
   const int32_t *rows;
@@ -77,10 +76,10 @@ struct Item {
   bool valid;
 };
 
-// Item j of this CTA.  Items are the (task, pole, RHS chunk) triples with the
-// tasks in decreasing length; the CTAs take them in snake order (round j:
-// position j G + b, or j G + G - 1 - b on odd rounds), which balances items of
-// very different lengths over the grid.
+// Item j of this CTA.  Items are the (task, pole, RHS chunk) triples; a
+// level's tasks are stored in decreasing length, and the CTAs take the items
+// in snake order (round j: position j G + b, or j G + G - 1 - b on odd
+// rounds), which balances items of very different lengths over the grid.
 __device__ __forceinline__ Item load_item(const ProdArgs &a, int j) {
   Item it;
   const int64_t G = gridDim.x, per = int64_t(a.np) * a.nchunk;
@@ -90,7 +89,7 @@ __device__ __forceinline__ Item load_item(const ProdArgs &a, int j) {
   if (it.valid) {
     const int64_t r = pos / per;
     q = int(pos - r * per);
-    ti = __ldg(a.order + r);
+    ti = int(r);
   }
   if (!it.valid) {
     it.nch = 0;
@@ -121,11 +120,20 @@ __device__ __forceinline__ int kmaj_off(int r, int c, int rows) {
   return (c >> 3) * (rows * 8) + (r >> 3) * 64 + ((c & 7) >> 2) * 32 + (r & 7) * 4 + (c & 3);
 }
 
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away
+// from zero, on the integer pipe: adding half a TF32 unit to the magnitude
+// bits carries into bit 13 exactly when the dropped 13 bits are >= half
+// (IEEE-754 binary32 layout; a carry out of the mantissa moves to the next
+// binade).  Finite inputs.
+__device__ __forceinline__ float tf32_rna(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+
 __device__ __forceinline__ void split4(float *hi, float *lo, int off, const float *v) {
-  const float4 h = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
+  const float4 h = make_float4(tf32_rna(v[0]), tf32_rna(v[1]), tf32_rna(v[2]), tf32_rna(v[3]));
   *reinterpret_cast<float4 *>(hi + off) = h;
-  *reinterpret_cast<float4 *>(lo + off) = make_float4(tc::to_tf32(v[0] - h.x), tc::to_tf32(v[1] - h.y),
-                                                      tc::to_tf32(v[2] - h.z), tc::to_tf32(v[3] - h.w));
+  *reinterpret_cast<float4 *>(lo + off) = make_float4(tf32_rna(v[0] - h.x), tf32_rna(v[1] - h.y),
+                                                      tf32_rna(v[2] - h.z), tf32_rna(v[3] - h.w));
 }
 }  // namespace
 
@@ -174,13 +182,18 @@ __device__ __forceinline__ bool ki_wait(KiShared &sh, uint64_t *bar, uint32_t pa
   return false;
 }
 
-__device__ __forceinline__ Item ki_item(const ProdArgs &a, int j) {
-  Item it = load_item(a, j);
+// Every role loads the descriptor of its next item at the start of the
+// current one and takes the chunk count only when the item begins, so the
+// load latency overlaps the current item's work.
+__device__ __forceinline__ Item ki_item(const ProdArgs &a, int j) { return load_item(a, j); }
+__device__ __forceinline__ Item ki_begin(const Item &nxt) {
+  Item it = nxt;
   it.nch = (it.t.kdim + KI_K - 1) / KI_K;
   return it;
 }
 
-// Loader (warp 8, lane 1): the TMA loads of every chunk, in order, into slot
+// Loader (warp 9, lane 0; a warp of its own, so that its waits never hold up
+// the MMA issue): the TMA loads of every chunk, in order, into slot
 // gc % KI_SLOTS as soon as the MMAs of the slot's previous chunk are done.
 __device__ void ki_loader(const ProdArgs &a, KiShared &sh) {
   int gc = 0;
@@ -188,8 +201,8 @@ __device__ void ki_loader(const ProdArgs &a, KiShared &sh) {
   Item nxt = ki_item(a, 0);
 #pragma unroll 1
   for (int j = 0; ok; j++) {
-    const Item it = nxt;
-    if (!it.valid) break;
+    if (!nxt.valid) break;
+    const Item it = ki_begin(nxt);
     nxt = ki_item(a, j + 1);
     const TcTask &t = it.t;
 #pragma unroll 1
@@ -217,10 +230,12 @@ __device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
   const int w = tid >> 5, l = tid & 31;
   int g = 0;
   bool ok = true;
+  Item nxt = ki_item(a, 0);
 #pragma unroll 1
   for (int j = 0; ok; j++) {
-    const Item it = ki_item(a, j);
-    if (!it.valid) break;
+    if (!nxt.valid) break;
+    const Item it = ki_begin(nxt);
+    nxt = ki_item(a, j + 1);
 #pragma unroll 1
     for (int c = 0; c < it.nch; c++, g++) {
       const int slot = g % KI_SLOTS;
@@ -245,7 +260,7 @@ __device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
 #pragma unroll
         for (int q = 0; q < 32; q++) {
           const float h = __uint_as_float(__float_as_uint(v[q]) & 0xffffe000u);   // what the MMA reads of v
-          v[q] = tc::to_tf32(__fsub_rn(v[q], h));
+          v[q] = tf32_rna(__fsub_rn(v[q], h));
         }
         tc::tmem_st32(sh.tmem + (uint32_t(w * 32) << 16) + KI_COL_LO + 32 * slot, v);
       }
@@ -289,8 +304,8 @@ __device__ void ki_mma(const ProdArgs &a, KiShared &sh) {
   Item nxt = ki_item(a, 0);
 #pragma unroll 1
   for (int j = 0; ok; j++) {
-    const Item it = nxt;
-    if (!it.valid) break;
+    if (!nxt.valid) break;
+    const Item it = ki_begin(nxt);
     nxt = ki_item(a, j + 1);
     const int buf = j & 1, use = j >> 1;
     if (use > 0 && !ki_wait(sh, &sh.acce[buf], (use - 1) & 1, a.st)) break;
@@ -331,8 +346,8 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
   Item nxt = ki_item(a, 0);
 #pragma unroll 1
   for (int j = 0;; j++) {
-    const Item it = nxt;
-    if (!it.valid) break;
+    if (!nxt.valid) break;
+    const Item it = ki_begin(nxt);
     nxt = ki_item(a, j + 1);
     const int buf = j & 1, use = j >> 1;
     const bool ok = ki_wait(sh, &sh.accf[buf], use & 1, a.st);
@@ -402,8 +417,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_tc_kint(const ProdArgs a) {
   tc::fence_after();
   if (warp < 4) ki_producer<MODE>(a, sh, tid);
   else if (warp < 8) ki_epilogue<MODE>(a, sh, tid - 128);
-  else if ((tid & 31) == 0) ki_mma(a, sh);
-  else if ((tid & 31) == 1) ki_loader(a, sh);
+  else if (warp == 8 && (tid & 31) == 0) ki_mma(a, sh);
+  else if (warp == 9 && (tid & 31) == 0) ki_loader(a, sh);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -514,7 +529,7 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
       // all of the unified L1 / shared storage as shared memory
       cudaFuncSetAttribute(k_tc_kint<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       // Two CTAs per SM: 256 of the 512 TMEM columns, under half of the shared
-      // memory and 2 x 288 x 96 registers each.  (The occupancy calculator
+      // memory and 2 x 320 x 96 registers each.  (The occupancy calculator
       // reports one for this 9-warp block; two are resident, as measured by
       // counting CTAs per SM.)
       static_assert(2 * (kKiSmem + 1024) <= 228 * 1024, "two CTAs per SM must fit in shared memory");
@@ -548,7 +563,6 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
   a.tasks = lv.prod[mode];
   a.ntask = lv.n_prod[mode];
   a.ntask_simt = lv.n_prod_simt[mode];
-  a.order = lv.order[mode];
   a.rows = P.rows;
   a.N = P.N;
   a.vstride = P.vstride;
