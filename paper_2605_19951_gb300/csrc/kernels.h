@@ -204,6 +204,9 @@ struct SolvePlan {
 
 // FP32 front products (solve_tc.cu): tensor cores (P.use_tc) or SIMT.
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s);
+// Gathers the level's update rows of X into P.Xg for the tensor-core BWD21
+// product (no-op when that product runs on the SIMT kernel).
+void launch_gather(const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s);
 // Resident CTAs per SM of the tensor-core product kernel (0 before its first launch).
 int tc_ctas_per_sm();
 // Tensor maps of every front's factor block (4 per front, index 4 f + mode)
@@ -309,7 +312,7 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 
 // Kernel classes that can be timed individually with CUDA events.
 enum KernelClass {
-  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT,
+  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT, KC_GATHER,
   KC_COUNT
 };
 struct Profiler {

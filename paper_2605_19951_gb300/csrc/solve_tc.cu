@@ -550,6 +550,15 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
 
 int tc_ctas_per_sm() { return g_tc_occupancy; }
 
+void launch_gather(const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
+  const bool use_tc = P.use_tc && P.vmaps != nullptr;
+  if (!use_tc || lv.n_prod[PM_BWD21] == 0 || lv.n_gather_rows == 0 || P.np == 0) return;
+  const int64_t warps = int64_t(lv.n_gather_rows) * P.np;
+  tem::count_launch();
+  k_gather_upd<<<unsigned((warps + 7) / 8), 256, 0, s>>>(P.X, P.vstride, P.Xg, P.gstride, lv.gather_src,
+                                                         lv.n_gather_rows, P.nrhs, P.np, P.pmap);
+}
+
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
   // The tensor-core kernel loads B rows by TMA, which needs 16-byte rows (an
   // even number of right-hand sides); otherwise the SIMT kernels run.  (It is
@@ -595,13 +604,7 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
       a.out = P.Y;
       a.xaux = P.X;
       if (use_tc) {
-        // the tensor-core kernel reads the update rows pre-gathered
-        if (lv.n_gather_rows > 0) {
-          const int64_t warps = int64_t(lv.n_gather_rows) * P.np;
-          tem::count_launch();
-          k_gather_upd<<<unsigned((warps + 7) / 8), 256, 0, s>>>(P.X, P.vstride, P.Xg, P.gstride, lv.gather_src,
-                                                                 lv.n_gather_rows, P.nrhs, P.np, P.pmap);
-        }
+        // the tensor-core kernel reads the update rows pre-gathered (launch_gather)
         a.B = P.Xg;
         a.bstride = P.gstride;
         a.bmap = vm ? vm + 2 : nullptr;
