@@ -107,10 +107,6 @@ struct tem_ctx {
   int64_t *t11r_ofs = nullptr, *l21t_ofs = nullptr;
   int64_t t11r_total = 0, l21t_total = 0;
   void *T11R = nullptr, *L21T = nullptr;
-  std::vector<int32_t> gather_h;          // FP32: source rows of every level's gather buffer
-  int32_t *gather = nullptr;
-  int64_t gather_rows = 0;                // rows of the gather buffer (max over levels)
-  void *Xg = nullptr;
   std::vector<InvTask> inv_h;             // FP32: pivot-block inversion tasks
   InvTask *inv = nullptr;
   std::vector<int2> invdiag_h;
@@ -242,23 +238,6 @@ struct ProfScope {
 // LevelDev pointers until the lists are uploaded.
 void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
   const auto &S = c->sym;
-  // gather buffer offsets of the update rows of this level's fronts
-  std::map<int32_t, int> gofs;
-  {
-    const size_t beg = c->gather_h.size();
-    int64_t rows = 0;
-    for (int32_t fi : L.fronts) {
-      const Front &F = S.fronts[fi];
-      gofs[fi] = (int)rows;
-      if (F.k > 0 && F.n > F.k) {
-        for (int32_t i = 0; i < F.n - F.k; i++) c->gather_h.push_back(S.rows[F.rows_off + i]);
-        rows += F.n - F.k;
-      }
-    }
-    c->gather_rows = std::max(c->gather_rows, rows);
-    lv.n_gather_rows = int(c->gather_h.size() - beg);
-    lv.gather_src = (const int32_t *)(uintptr_t)beg;
-  }
   for (int mode = 0; mode < PM_COUNT; mode++) {
     const size_t beg = c->prod_h.size(), beg_s = c->prod_simt_h.size();
     for (int32_t fi : L.fronts) {
@@ -315,14 +294,14 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
           }
         }
       } else if (mode == PM_BWD21) {
-        // B rows: the SIMT kernel gathers rows[rows_off + kk - kfirst] (64-column
-        // tiles), the tensor-core kernel reads the level's gather buffer at the
-        // front's offset (128-column tiles)
+        // B rows: X[rows[rows_off + kk - kfirst]] for inner index kk >= kfirst,
+        // gathered by the SIMT kernel (64-column tiles) or by TMA row-gather
+        // loads (128-column tiles)
         const int kdim = b == 0 ? 0 : F.n - r0;
         for (int cb = 0; cb < k; cb += 64)
           push(false, true, r0, cb, kdim, std::min(64, k - cb), (int)F.rows_off - (k - r0), F.c0 + cb, 0, k - r0);
         for (int cb = 0; cb < k; cb += 128)
-          push(true, false, r0, cb, kdim, std::min(128, k - cb), gofs[fi] - (k - r0), F.c0 + cb, 0, k - r0);
+          push(true, false, r0, cb, kdim, std::min(128, k - cb), (int)F.rows_off - (k - r0), F.c0 + cb, 0, k - r0);
       } else {
         for (int cb = 0; cb < k; cb += 64)
           push(false, true, cb, cb, k - cb, std::min(64, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
@@ -402,8 +381,6 @@ void build_steps(tem_ctx *c) {
   c->sbb_h.clear();
   c->prod_h.clear();
   c->prod_simt_h.clear();
-  c->gather_h.clear();
-  c->gather_rows = 0;
   c->rcopy_h.clear();
   // row-major copy layout: per front k x ld2 (T11) and b x ld2 (L21), ld2 = k rounded up to even
   c->t11r_ofs_h.assign(S.fronts.size(), 0);
@@ -555,8 +532,6 @@ SolvePlan<R> solve_plan(tem_ctx *c) {
   P.dinv = (const cx<R> *)c->dinv;
   P.tmaps = c->tmaps;
   P.vmaps = c->vmaps;
-  P.Xg = (cx<R> *)c->Xg;
-  P.gstride = std::max<int64_t>(1, c->gather_rows) * c->n_tx;
   P.N = c->mesh.N;
   return P;
 }
@@ -671,11 +646,8 @@ int ensure_numeric(tem_ctx *c) {
     const std::string e = build_tensor_maps(geo, views, m, &c->tmaps);
     if (!e.empty()) return fail(c, TEM_ERR_CUDA, e);
     c->allocs.push_back(c->tmaps);
-    TRY(dalloc(c, (c64 **)&c->Xg, size_t(m) * std::max<int64_t>(1, c->gather_rows) * nx));
-    CK(cudaMemset(c->Xg, 0, size_t(m) * std::max<int64_t>(1, c->gather_rows) * nx * sizeof(c64)));
-    const std::string e2 = build_vector_maps({VecBuf{(const c64 *)c->Y, N}, VecBuf{(const c64 *)c->X, N},
-                                              VecBuf{(const c64 *)c->Xg, std::max<int64_t>(1, c->gather_rows)}},
-                                             nx, m, &c->vmaps);
+    const std::string e2 = build_vector_maps({VecBuf{(const c64 *)c->Y, N}, VecBuf{(const c64 *)c->X, N}}, 1, nx, m,
+                                             &c->vmaps);
     if (!e2.empty()) return fail(c, TEM_ERR_CUDA, e2);
     if (c->vmaps) c->allocs.push_back(c->vmaps);
     TRY(dalloc(c, &c->mval_fact, size_t(m) * c->mesh.kval.size()));
@@ -793,7 +765,6 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   TRY(upload(c, &c->sbb, c->sbb_h));
   TRY(upload(c, &c->prod, c->prod_h));
   TRY(upload(c, &c->prod_simt, c->prod_simt_h));
-  TRY(upload(c, &c->gather, c->gather_h));
   TRY(upload(c, &c->rcopy, c->rcopy_h));
   TRY(upload(c, &c->t11r_ofs, c->t11r_ofs_h));
   TRY(upload(c, &c->l21t_ofs, c->l21t_ofs_h));
@@ -806,7 +777,6 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
       lv.prod[mode] = c->prod + (uintptr_t)lv.prod[mode];
       lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
     }
-    lv.gather_src = c->gather + (uintptr_t)lv.gather_src;
     lv.rcopy = c->rcopy + (uintptr_t)lv.rcopy;
     lv.inv_diag = c->invdiag + (uintptr_t)lv.inv_diag;
     for (auto &st : lv.inv) st.tasks = c->inv + (uintptr_t)st.tasks;

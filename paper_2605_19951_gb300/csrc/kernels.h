@@ -128,9 +128,6 @@ struct LevelDev {
   std::vector<InvStage> inv;
   const int2 *inv_diag = nullptr;   // (front, 32-block) of every diagonal block
   int n_inv_diag = 0;
-  // FP32 backward: source row (in X) of each row of the level's gather buffer
-  const int32_t *gather_src = nullptr;
-  int n_gather_rows = 0;
   // FP32 factorisation: (front, 0 = T11 / 1 = L21, 32-row block) of the row-major copies
   const int4 *rcopy = nullptr;
   int n_rcopy = 0;
@@ -193,9 +190,7 @@ struct SolvePlan {
   bool use_tc = false;        // FP32: front products on the tensor cores
   const cx<R> *dinv = nullptr;  // FP32: [m][N] inverse pivots
   const void *tmaps = nullptr;  // FP32: 4 tensor maps per front (one per product mode)
-  const void *vmaps = nullptr;  // FP32: tensor maps of Y, X and Xg (nullptr for an odd nrhs)
-  cx<R> *Xg = nullptr;          // FP32: [m][gather rows][nrhs] update rows of X, one level at a time
-  int64_t gstride = 0;          // pole stride of Xg
+  const void *vmaps = nullptr;  // FP32: tensor maps of Y and X, and the row-gather map of X (nullptr for an odd nrhs)
   int64_t N = 0;
   DevStatus *status = nullptr;
   void forward_level(const LevelDev &lv, cudaStream_t s);
@@ -204,9 +199,7 @@ struct SolvePlan {
 
 // FP32 front products (solve_tc.cu): tensor cores (P.use_tc) or SIMT.
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s);
-// Gathers the level's update rows of X into P.Xg for the tensor-core BWD21
-// product (no-op when that product runs on the SIMT kernel).
-void launch_gather(const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s);
+
 // Resident CTAs per SM of the tensor-core product kernel (0 before its first launch).
 int tc_ctas_per_sm();
 // Tensor maps of every front's factor block (4 per front, index 4 f + mode)
@@ -225,12 +218,15 @@ struct FactorViews {
   int64_t l21t_stride;
 };
 std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const FactorViews &v, int m, void **out);
-// Maps over [pole][rows][nrhs] complex vectors (pole stride rows * nrhs), in order.
+// Maps over [pole][rows][nrhs] complex vectors (pole stride rows * nrhs), in
+// order (boxes of 16 rows x 32 right-hand sides), then one row-gather map
+// over bufs[gather] seen as m * rows rows of nrhs values (boxes of one row x
+// 32 right-hand sides, for tile::gather4 loads).
 struct VecBuf {
   const c64 *base;
   int64_t rows;
 };
-std::string build_vector_maps(const std::vector<VecBuf> &bufs, int nrhs, int m, void **out);
+std::string build_vector_maps(const std::vector<VecBuf> &bufs, int gather, int nrhs, int m, void **out);
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s);
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
@@ -312,7 +308,7 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 
 // Kernel classes that can be timed individually with CUDA events.
 enum KernelClass {
-  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT, KC_GATHER,
+  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT,
   KC_COUNT
 };
 struct Profiler {

@@ -414,9 +414,6 @@ template <typename R>
 void SolvePlan<R>::backward_level(const LevelDev &lv, cudaStream_t s) {
   if (g_prof) g_prof->cur_level = lv.h;
   if constexpr (std::is_same<R, float>::value) {
-    if (g_prof) g_prof->begin(KC_GATHER, s);
-    launch_gather(*this, lv, s);
-    if (g_prof) g_prof->end(KC_GATHER, s);
     if (g_prof) g_prof->begin(KC_BWD_UPD, s);
     launch_prod(PM_BWD21, *this, lv, s);
     if (g_prof) g_prof->end(KC_BWD_UPD, s);

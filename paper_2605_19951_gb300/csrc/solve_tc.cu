@@ -63,7 +63,6 @@ struct ProdArgs {
   const CUtensorMap *bmap;   // B rows by TMA
   int64_t N;
   int64_t vstride;   // pole stride of the outputs (and of B, except BWD21 on the tensor cores)
-  int64_t bstride;   // pole stride of the B rows
   int nrhs, nchunk, np;
   const int *pmap;
   DevStatus *st;
@@ -192,13 +191,35 @@ __device__ __forceinline__ Item ki_begin(const Item &nxt) {
   return it;
 }
 
-// Loader (warp 9, lane 0; a warp of its own, so that its waits never hold up
-// the MMA issue): the TMA loads of every chunk, in order, into slot
-// gc % KI_SLOTS as soon as the MMAs of the slot's previous chunk are done.
-__device__ void ki_loader(const ProdArgs &a, KiShared &sh) {
+// Rows of the row-gather map (pole p's block of X) that feed inner indices
+// k0 + 4q .. k0 + 4q + 3 of a BWD21 item: X row rows[bbase + kk]; indices
+// outside [kfirst, kdim) repeat a valid row (the producers zero them).
+__device__ __forceinline__ int4 ki_gather_rows(const ProdArgs &a, const Item &it, int k0, int q) {
+  const TcTask &t = it.t;
+  if (t.kdim <= int(t.kfirst)) return make_int4(0, 0, 0, 0);   // no update rows: no chunks, nothing loaded
+  const int base = it.p * int(a.N);   // m * N < 2^31 (checked when the map is built)
+  int r[4];
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const int kk = min(max(k0 + 4 * q + e, int(t.kfirst)), t.kdim - 1);
+    r[e] = base + __ldg(a.rows + t.bbase + kk);
+  }
+  return make_int4(r[0], r[1], r[2], r[3]);
+}
+
+// Loader (warp 9, a warp of its own so that its waits never hold up the MMA
+// issue): the TMA loads of every chunk, in order, into slot gc % KI_SLOTS as
+// soon as the MMAs of the slot's previous chunk are done.  Lane 0 loads the
+// factor box and (except for BWD21) the 16 contiguous B rows; for BWD21 lanes
+// 0-3 each gather four B rows of X, whose indices they fetch one chunk ahead.
+template <int MODE>
+__device__ void ki_loader(const ProdArgs &a, KiShared &sh, int lane) {
+  constexpr bool kGather = MODE == PM_BWD21;
   int gc = 0;
   bool ok = true;
   Item nxt = ki_item(a, 0);
+  int4 rnext = make_int4(0, 0, 0, 0);
+  if (kGather && lane < 4 && nxt.valid) rnext = ki_gather_rows(a, nxt, 0, lane);
 #pragma unroll 1
   for (int j = 0; ok; j++) {
     if (!nxt.valid) break;
@@ -208,20 +229,36 @@ __device__ void ki_loader(const ProdArgs &a, KiShared &sh) {
 #pragma unroll 1
     for (int c = 0; c < it.nch; c++, gc++) {
       const int slot = gc % KI_SLOTS;
-      if (gc >= KI_SLOTS && !ki_wait(sh, &sh.freeb[slot], ((gc / KI_SLOTS) - 1) & 1, a.st)) {
+      const int4 rows = rnext;
+      if (kGather && lane < 4) {
+        if (c + 1 < it.nch) rnext = ki_gather_rows(a, it, (c + 1) * KI_K, lane);
+        else if (nxt.valid) rnext = ki_gather_rows(a, nxt, 0, lane);
+      }
+      bool free = true;
+      if (gc >= KI_SLOTS) {
+        if (lane == 0) free = ki_wait(sh, &sh.freeb[slot], ((gc / KI_SLOTS) - 1) & 1, a.st);
+        free = __shfl_sync(kFull, free, 0);
+      }
+      if (!free) {
         ok = false;
         break;
       }
       const int k0 = c * KI_K;
-      sh.kval[slot] = min(KI_K, t.kdim - k0);
-      sh.kfst[slot] = max(0, int(t.kfirst) - k0);
-      tc::mbar_arrive_expect_tx(&sh.rawfull[slot], (128 * 32 + KI_K * 64) * 4);
-      tc::tma_load_3d(sh.sl[slot].A, a.tmaps + t.map, t.x0 + 2 * k0, t.y0, it.p, &sh.rawfull[slot]);
-      tc::tma_load_3d(sh.sl[slot].Xr, a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
+      if (lane == 0) {
+        sh.kval[slot] = min(KI_K, t.kdim - k0);
+        sh.kfst[slot] = max(0, int(t.kfirst) - k0);
+        tc::mbar_arrive_expect_tx(&sh.rawfull[slot], (128 * 32 + KI_K * 64) * 4);
+        tc::tma_load_3d(sh.sl[slot].A, a.tmaps + t.map, t.x0 + 2 * k0, t.y0, it.p, &sh.rawfull[slot]);
+        if (!kGather) tc::tma_load_3d(sh.sl[slot].Xr, a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
+      }
+      if (kGather) {
+        __syncwarp();   // the slot's byte count is posted before its row gathers are issued
+        if (lane < 4) tc::tma_gather4(sh.sl[slot].Xr + lane * 4 * 64, a.bmap, 64 * it.ch, rows, &sh.rawfull[slot]);
+      }
     }
   }
   // after an abort: let the loads still in flight land before the CTA exits
-  if (!ok)
+  if (!ok && lane == 0)
     for (int q = max(0, gc - KI_SLOTS); q < gc; q++) tc::mbar_wait(&sh.rawfull[q % KI_SLOTS], (q / KI_SLOTS) & 1, kWaitIter);
 }
 
@@ -418,7 +455,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_tc_kint(const ProdArgs a) {
   if (warp < 4) ki_producer<MODE>(a, sh, tid);
   else if (warp < 8) ki_epilogue<MODE>(a, sh, tid - 128);
   else if (warp == 8 && (tid & 31) == 0) ki_mma(a, sh);
-  else if (warp == 9 && (tid & 31) == 0) ki_loader(a, sh);
+  else if (warp == 9) ki_loader<MODE>(a, sh, tid & 31);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -497,23 +534,6 @@ __global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtT
   }
 }
 
-// Xg[p][g] = X[p][src[g]] for the g < n gather rows of a level (the update
-// rows of its fronts, front after front); a warp per row, lanes over
-// right-hand sides.
-__global__ void __launch_bounds__(256) k_gather_upd(const c64 *__restrict__ X, int64_t vstride, c64 *__restrict__ Xg,
-                                                    int64_t gstride, const int32_t *__restrict__ src, int64_t n,
-                                                    int nrhs, int np, const int *__restrict__ pmap) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (w >= n * np) return;
-  const int ps = int(w / n);
-  const int64_t g = w - int64_t(ps) * n;
-  const int p = pole_of(ps, pmap);
-  const c64 *from = X + p * vstride + int64_t(__ldg(src + g)) * nrhs;
-  c64 *to = Xg + p * gstride + g * nrhs;
-  for (int j = lane; j < nrhs; j += 32) to[j] = from[j];
-}
-
 namespace {
 int g_tc_occupancy = 0;
 
@@ -550,15 +570,6 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
 
 int tc_ctas_per_sm() { return g_tc_occupancy; }
 
-void launch_gather(const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
-  const bool use_tc = P.use_tc && P.vmaps != nullptr;
-  if (!use_tc || lv.n_prod[PM_BWD21] == 0 || lv.n_gather_rows == 0 || P.np == 0) return;
-  const int64_t warps = int64_t(lv.n_gather_rows) * P.np;
-  tem::count_launch();
-  k_gather_upd<<<unsigned((warps + 7) / 8), 256, 0, s>>>(P.X, P.vstride, P.Xg, P.gstride, lv.gather_src,
-                                                         lv.n_gather_rows, P.nrhs, P.np, P.pmap);
-}
-
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
   // The tensor-core kernel loads B rows by TMA, which needs 16-byte rows (an
   // even number of right-hand sides); otherwise the SIMT kernels run.  (It is
@@ -575,7 +586,6 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
   a.rows = P.rows;
   a.N = P.N;
   a.vstride = P.vstride;
-  a.bstride = P.vstride;
   a.nrhs = P.nrhs;
   a.nchunk = (P.nrhs + 31) / 32;
   a.np = P.np;
@@ -603,12 +613,8 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
       a.B = P.X;
       a.out = P.Y;
       a.xaux = P.X;
-      if (use_tc) {
-        // the tensor-core kernel reads the update rows pre-gathered (launch_gather)
-        a.B = P.Xg;
-        a.bstride = P.gstride;
-        a.bmap = vm ? vm + 2 : nullptr;
-      }
+      // the tensor-core kernel loads the update rows of X by TMA row gathers
+      a.bmap = vm ? vm + 2 : nullptr;
       run_mode<PM_BWD21>(a, lv.prod_simt[mode], use_tc, s);
       break;
     default:
@@ -686,7 +692,7 @@ std::string build_tensor_maps(const std::vector<FrontGeom> &fronts, const Factor
 // floats: rows of 2 nrhs floats, R rows, m poles; a box is 16 rows x 32
 // right-hand sides.  Needs an even nrhs (16-byte row stride); *out = nullptr
 // otherwise (the kernels then copy B rows with cp.async).
-std::string build_vector_maps(const std::vector<VecBuf> &bufs, int nrhs, int m, void **out) {
+std::string build_vector_maps(const std::vector<VecBuf> &bufs, int gather, int nrhs, int m, void **out) {
   *out = nullptr;
   if (nrhs & 1) return "";
   EncodeTiledFn encode = nullptr;
@@ -699,7 +705,7 @@ std::string build_vector_maps(const std::vector<VecBuf> &bufs, int nrhs, int m, 
       return "cuTensorMapEncodeTiled is not available from the driver";
     encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
-  std::vector<CUtensorMap> maps(bufs.size());
+  std::vector<CUtensorMap> maps(bufs.size() + 1);
   for (size_t i = 0; i < bufs.size(); i++) {
     const int64_t rows = bufs[i].rows > 0 ? bufs[i].rows : 1;
     const cuuint64_t dims[3] = {cuuint64_t(2) * nrhs, cuuint64_t(rows), cuuint64_t(m)};
@@ -710,6 +716,19 @@ std::string build_vector_maps(const std::vector<VecBuf> &bufs, int nrhs, int m, 
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return "cuTensorMapEncodeTiled failed for a solve vector";
+  }
+  {
+    const VecBuf &g = bufs.at(gather);
+    const int64_t rows = (g.rows > 0 ? g.rows : 1) * m;
+    if (rows >= (int64_t(1) << 31)) return "too many vector rows for the row-gather map";
+    const cuuint64_t dims[2] = {cuuint64_t(2) * nrhs, cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(nrhs) * sizeof(c64)};
+    const cuuint32_t box[2] = {64u, 1u};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&maps[bufs.size()], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<c64 *>(g.base), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return "cuTensorMapEncodeTiled failed for the row-gather map";
   }
   void *d = nullptr;
   const size_t bytes = maps.size() * sizeof(CUtensorMap);

@@ -228,6 +228,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, 
       : "memory");
 }
 
+// TMA gather of four rows (2-D tensor map whose box is one row high): rows
+// r.x..r.w of the tensor, columns x.., land one after another at dst.
+__device__ __forceinline__ void tma_gather4(void *dst, const void *tmap, int x, int4 r, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], "
+      "[%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(smem_addr(mbar))
+      : "memory");
+}
+
 // Asynchronous global -> shared copies (cp.async, L1-allocating).  Bytes
 // past `valid` bytes of the copy are zero-filled (valid = 0: no global read).
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
