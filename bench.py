@@ -195,7 +195,7 @@ def run_ours(args):
 
     # which kernel class dominates a pair (one untimed profiling pass per class)
     per_class = {}
-    for cls in ("fwd", "fwd21", "bwd", "bwd_upd"):
+    for cls in ("fwd", "fwd21", "bwd", "bwd_upd", "residual", "refine_vec", "jacobian"):
         tem.tem_set_profiling(mdl.ctx, cls)
         mdl.lsqr(d_obs, wd, m0, LAMBDA, 1)
         per_class[cls] = tem.tem_kernel_time(mdl.ctx)

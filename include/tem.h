@@ -205,8 +205,10 @@ int tem_set_tensor_cores(tem_ctx *ctx, int enable);
  * 0 trailing update, 1 panel, 2 forward pivot-block step, 3 backward
  * pivot-block step, 4 backward update-row product (L21^T), 5 extend-add,
  * 6 forward update-row product (L21), 7 forward super-block product,
- * 8 backward super-block product, 9 pivot-block inversion; -1 switches
- * timing off (the default).
+ * 8 backward super-block product, 9 pivot-block inversion, 10 refinement
+ * residual, 11 refinement vector kernels (split, scaling, accumulation, join),
+ * 12 Jacobian kernels (J v right-hand sides, J^T w right-hand sides, residue
+ * sums, cell sums); -1 switches timing off (the default).
  * class + 64 (h + 1) times only the launches of assembly-tree level h.
  * Timing adds an event pair around each launch of that class. */
 int tem_set_profiling(tem_ctx *ctx, int kernel_class);

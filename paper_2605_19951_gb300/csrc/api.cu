@@ -568,18 +568,30 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
   // FP32 mode: b and the iterate as double-float pairs, corrections in FP32
   float4 *bdf = reinterpret_cast<float4 *>(c->r);   // pairs of b (shared when bstride == 0)
   const int64_t bsd = bstride ? N * nx : 0;
+  auto prof_begin = [&](int k) { if (g_prof) g_prof->begin(k, s); };
+  auto prof_end = [&](int k) { if (g_prof) g_prof->end(k, s); };
+  prof_begin(KC_REFINE_VEC);
   launch_split_cx(b, bdf, (bstride ? int64_t(m) : int64_t(1)) * N * nx, s);
   c64 *Y = (c64 *)c->Y;
   launch_scale_to_work<float4>(bdf, bsd, Y, c->colmax_f, m, nullptr, N, nx, s);
+  prof_end(KC_REFINE_VEC);
   sweeps<float>(c, nullptr, m);
+  prof_begin(KC_REFINE_VEC);
   launch_accumulate_df((const c64 *)c->X, c->colmax_f, c->xdf, m, nullptr, N, nx, false, s);
+  prof_end(KC_REFINE_VEC);
   const int *pm = nullptr;
   int np = m;
   for (int it = 0; it < c->refine; it++) {
+    prof_begin(KC_RESIDUAL);
     launch_residual_df(c->rp, c->ci, c->kdf, c->mdf, c->xi, bdf, bsd, c->xdf, Y, np, pm, N, nx, s);
+    prof_end(KC_RESIDUAL);
+    prof_begin(KC_REFINE_VEC);
     launch_scale_to_work<c64>(Y, N * nx, Y, c->colmax_f, np, pm, N, nx, s);
+    prof_end(KC_REFINE_VEC);
     sweeps<float>(c, pm, np);
+    prof_begin(KC_REFINE_VEC);
     launch_accumulate_df((const c64 *)c->X, c->colmax_f, c->xdf, np, pm, N, nx, true, s);
+    prof_end(KC_REFINE_VEC);
     if (c->refine_tol <= 0 || it + 1 == c->refine) continue;
     CK(cudaMemsetAsync(c->prog, 0, sizeof(double) * 2 * m, s));
     launch_progress_df((const c64 *)c->X, c->colmax_f, c->xdf, c->earth, c->prog, c->prog + m, np, pm, N, nx, s);
@@ -597,7 +609,9 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x) {
     pm = c->pmap;
     np = (int)keep.size();
   }
+  prof_begin(KC_REFINE_VEC);
   launch_join_cx(c->xdf, x, int64_t(m) * N * nx, s);
+  prof_end(KC_REFINE_VEC);
   return TEM_OK;
 }
 
@@ -912,19 +926,27 @@ int tem_forward(tem_ctx *c, double *d) {
 namespace {
 int jvp_async(tem_ctx *c, const double *v, double *jv) {
   const int64_t N = c->mesh.N;
+  if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   launch_dm_apply(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->pidx, v, c->sigma, c->me1, c->xi, c->g, c->b,
                   c->m, N, c->n_tx, c->stream);
+  if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   TRY(solve_all(c, c->b, N * c->n_tx, c->x));
+  if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->n_tx, c->n_rx, c->K, c->stream);
+  if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   return TEM_OK;
 }
 int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
   const int64_t N = c->mesh.N;
+  if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->n_tx,
                 c->n_rx, c->K, c->stream);
+  if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   TRY(solve_all(c, c->b, N * c->n_tx, c->x));
+  if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->n_tx,
-                  c->stream);
+                  c->precision != TEM_FP64, c->stream);
+  if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   return TEM_OK;
 }
 }  // namespace

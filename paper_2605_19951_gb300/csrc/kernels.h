@@ -288,9 +288,10 @@ void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_
                      const double *me1, const double2 *xi, const c128 *g, c128 *h, int m, int64_t N,
                      int nrhs, cudaStream_t s);
 // grad[p] = 2 Re sum_i xi_i sigma_t sum_x (P z_ix)^T M1_t (P g_ix), t = ptet[p]
+// (fp32: the per-(pole, right-hand side) cell sums on the FP32 pipes)
 void launch_bilinear(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
                      const double *me1, const double2 *xi, const c128 *g, const c128 *z, double *grad,
-                     int m, int64_t N, int nrhs, cudaStream_t s);
+                     int m, int64_t N, int nrhs, bool fp32, cudaStream_t s);
 // sparse y = A x (CSR) and y = A^T x via the transpose CSR; beta-scaled accumulate
 void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,
                    int64_t rows, double alpha, double beta, cudaStream_t s);
@@ -308,7 +309,7 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 
 // Kernel classes that can be timed individually with CUDA events.
 enum KernelClass {
-  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT,
+  KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT, KC_RESIDUAL, KC_REFINE_VEC, KC_JACOBIAN,
   KC_COUNT
 };
 struct Profiler {

@@ -271,6 +271,10 @@ void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *q
 
 // h_p[d][x] = xi_p sum over the tets t at unknown d (local edge a) of
 //             v_t sigma_t sum_b M1_t[a][b] g_p[tdof_t[b]][x]
+// T is the arithmetic type of the per-unknown sums.  Both modes use double:
+// the primary field cancels strongly in these sums, and FP32 sums put J v
+// off by ~1e-5 relative.
+template <typename T>
 __global__ void k_dm_apply(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_tet,
                            const int8_t *__restrict__ inc_loc, const int32_t *__restrict__ tdof,
                            const int32_t *__restrict__ pidx, const double *__restrict__ v,
@@ -286,27 +290,29 @@ __global__ void k_dm_apply(const int64_t *__restrict__ inc_ptr, const int32_t *_
   for (int c0 = 0; c0 < nrhs; c0 += 32) {
     const int x = c0 + lane;
     if (x >= nrhs) break;
-    c128 acc = mk<double>(0.0, 0.0);
+    T ax = 0, ay = 0;
     for (int64_t q = inc_ptr[d]; q < inc_ptr[d + 1]; q++) {
       const int32_t t = inc_tet[q];
       const int32_t pt = pidx[t];
       if (pt < 0) continue;
-      const double coef = v[pt] * sigma[t];
-      if (coef == 0.0) continue;
+      const T coef = T(v[pt] * sigma[t]);
+      if (coef == T(0)) continue;
       const int a = inc_loc[q];
       const double *Me = me1 + int64_t(t) * 36 + a * 6;
-      c128 sum = mk<double>(0.0, 0.0);
+      T sx = 0, sy = 0;
       for (int b = 0; b < 6; b++) {
         const int32_t db = tdof[int64_t(t) * 6 + b];
         if (db < 0) continue;
         const c128 gv = gp[int64_t(db) * nrhs + x];
-        sum.x += Me[b] * gv.x;
-        sum.y += Me[b] * gv.y;
+        const T mb = T(Me[b]);
+        sx += mb * T(gv.x);
+        sy += mb * T(gv.y);
       }
-      acc.x += coef * sum.x;
-      acc.y += coef * sum.y;
+      ax += coef * sx;
+      ay += coef * sy;
     }
-    h[p * N * nrhs + d * nrhs + x] = mk<double>(s.x * acc.x - s.y * acc.y, s.x * acc.y + s.y * acc.x);
+    const double acx = double(ax), acy = double(ay);
+    h[p * N * nrhs + d * nrhs + x] = mk<double>(s.x * acx - s.y * acy, s.x * acy + s.y * acx);
   }
 }
 
@@ -316,10 +322,14 @@ void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_
                      int nrhs, cudaStream_t s) {
   dim3 gr(div_up(N, 8), m);
   tem::count_launch();
-  k_dm_apply<<<gr, 256, 0, s>>>(inc_ptr, inc_tet, inc_loc, tdof, pidx, v, sigma, me1, xi, g, h, N, nrhs);
+  k_dm_apply<double><<<gr, 256, 0, s>>>(inc_ptr, inc_tet, inc_loc, tdof, pidx, v, sigma, me1, xi, g, h, N, nrhs);
 }
 
 // grad[pt] = 2 sigma_t Re sum_i xi_i sum_x (P_t z_ix)^T M1_t (P_t g_ix); one warp per cell.
+// T is the arithmetic type of the per-(pole, right-hand side) cell sums
+// (double in FP64 mode, float in refined-FP32 mode); the sums over right-hand
+// sides and poles run in FP64.
+template <typename T>
 __global__ void k_bilinear(const int32_t *__restrict__ ptet, int64_t P, const int32_t *__restrict__ tdof,
                            const double *__restrict__ sigma, const double *__restrict__ me1,
                            const double2 *__restrict__ xi, const c128 *__restrict__ g,
@@ -338,19 +348,25 @@ __global__ void k_bilinear(const int32_t *__restrict__ ptet, int64_t P, const in
     const c128 *zp = z + p * N * nrhs;
     c128 acc = mk<double>(0.0, 0.0);
     for (int x = lane; x < nrhs; x += 32) {
-      c128 gl[6], zl[6];
+      cx<T> gl[6], zl[6];
       for (int a = 0; a < 6; a++) {
-        gl[a] = td[a] >= 0 ? gp[int64_t(td[a]) * nrhs + x] : mk<double>(0.0, 0.0);
-        zl[a] = td[a] >= 0 ? zp[int64_t(td[a]) * nrhs + x] : mk<double>(0.0, 0.0);
+        const c128 gv = td[a] >= 0 ? gp[int64_t(td[a]) * nrhs + x] : mk<double>(0.0, 0.0);
+        const c128 zv = td[a] >= 0 ? zp[int64_t(td[a]) * nrhs + x] : mk<double>(0.0, 0.0);
+        gl[a] = mk<T>(T(gv.x), T(gv.y));
+        zl[a] = mk<T>(T(zv.x), T(zv.y));
       }
+      cx<T> sum = mk<T>(T(0), T(0));
       for (int a = 0; a < 6; a++) {
-        c128 mg = mk<double>(0.0, 0.0);
+        cx<T> mg = mk<T>(T(0), T(0));
         for (int b = 0; b < 6; b++) {
-          mg.x += Me[a * 6 + b] * gl[b].x;
-          mg.y += Me[a * 6 + b] * gl[b].y;
+          const T mab = T(Me[a * 6 + b]);
+          mg.x += mab * gl[b].x;
+          mg.y += mab * gl[b].y;
         }
-        cfma(acc, zl[a], mg);
+        cfma(sum, zl[a], mg);
       }
+      acc.x += double(sum.x);
+      acc.y += double(sum.y);
     }
     const double2 s = xi[p];
     total += s.x * acc.x - s.y * acc.y;
@@ -361,10 +377,11 @@ __global__ void k_bilinear(const int32_t *__restrict__ ptet, int64_t P, const in
 
 void launch_bilinear(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
                      const double *me1, const double2 *xi, const c128 *g, const c128 *z, double *grad,
-                     int m, int64_t N, int nrhs, cudaStream_t s) {
+                     int m, int64_t N, int nrhs, bool fp32, cudaStream_t s) {
   if (P == 0) return;
   tem::count_launch();
-  k_bilinear<<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
+  if (fp32) k_bilinear<float><<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
+  else k_bilinear<double><<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
 }
 
 __global__ void k_csr_mv(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,

@@ -96,6 +96,9 @@ __global__ void k_join_cx(const float4 *__restrict__ v, c128 *__restrict__ out, 
 
 // r = b - K x + xi (M x) for every mapped pole; one warp per row, lanes over
 // right-hand sides; r rounded to FP32 (it only feeds the FP32 correction).
+// A block walks kResRows consecutive rows (its eight warps on interleaved
+// rows), so the x rows that neighbouring rows share are reused from L1.
+constexpr int kResRows = 128;
 __global__ void __launch_bounds__(256) k_residual_df(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                      const float2 *__restrict__ kdf, const float2 *__restrict__ mdf,
                                                      const double2 *__restrict__ xi, const float4 *__restrict__ bdf,
@@ -104,33 +107,34 @@ __global__ void __launch_bounds__(256) k_residual_df(const int64_t *__restrict__
                                                      const int *__restrict__ pmap) {
   const int p = pole_of(blockIdx.y, pmap);
   const int lane = threadIdx.x & 31;
-  const int64_t row = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= N) return;
   const dfl xr = split(xi[p].x), xq = split(xi[p].y);
   const float4 *xp = xdf + p * N * nrhs;
-  const int64_t z0 = rp[row], z1 = rp[row + 1];
-  for (int c0 = 0; c0 < nrhs; c0 += 32) {
-    const int rhs = c0 + lane;
-    if (rhs >= nrhs) break;
-    Dot2 kr, ki, mr, mi;
-    for (int64_t z = z0; z < z1; z++) {
-      const float2 kv = kdf[z], mv = mdf[z];
-      const float4 v = xp[int64_t(ci[z]) * nrhs + rhs];
-      const dfl k = {kv.x, kv.y}, mm = {mv.x, mv.y};
-      const dfl vr = {v.x, v.y}, vi = {v.z, v.w};
-      kr.add(k, vr);
-      ki.add(k, vi);
-      mr.add(mm, vr);
-      mi.add(mm, vi);
+  const int64_t rbeg = blockIdx.x * int64_t(kResRows), rend = rbeg + kResRows < N ? rbeg + kResRows : N;
+  for (int64_t row = rbeg + (threadIdx.x >> 5); row < rend; row += blockDim.x >> 5) {
+    const int64_t z0 = rp[row], z1 = rp[row + 1];
+    for (int c0 = 0; c0 < nrhs; c0 += 32) {
+      const int rhs = c0 + lane;
+      if (rhs >= nrhs) break;
+      Dot2 kr, ki, mr, mi;
+      for (int64_t z = z0; z < z1; z++) {
+        const float2 kv = kdf[z], mv = mdf[z];
+        const float4 v = xp[int64_t(ci[z]) * nrhs + rhs];
+        const dfl k = {kv.x, kv.y}, mm = {mv.x, mv.y};
+        const dfl vr = {v.x, v.y}, vi = {v.z, v.w};
+        kr.add(k, vr);
+        ki.add(k, vi);
+        mr.add(mm, vr);
+        mi.add(mm, vi);
+      }
+      const dfl Kr = kr.value(), Ki = ki.value(), Mr = mr.value(), Mi = mi.value();
+      // xi (M x) = (xr Mr - xq Mi) + i (xr Mi + xq Mr)
+      const dfl sr = df_add(df_mul(xr, Mr), df_neg(df_mul(xq, Mi)));
+      const dfl si = df_add(df_mul(xr, Mi), df_mul(xq, Mr));
+      const float4 b = bdf[p * bstride + row * nrhs + rhs];
+      const dfl rr = df_add(df_add({b.x, b.y}, df_neg(Kr)), sr);
+      const dfl ri = df_add(df_add({b.z, b.w}, df_neg(Ki)), si);
+      r[p * N * nrhs + row * nrhs + rhs] = mk<float>(__fadd_rn(rr.hi, rr.lo), __fadd_rn(ri.hi, ri.lo));
     }
-    const dfl Kr = kr.value(), Ki = ki.value(), Mr = mr.value(), Mi = mi.value();
-    // xi (M x) = (xr Mr - xq Mi) + i (xr Mi + xq Mr)
-    const dfl sr = df_add(df_mul(xr, Mr), df_neg(df_mul(xq, Mi)));
-    const dfl si = df_add(df_mul(xr, Mi), df_mul(xq, Mr));
-    const float4 b = bdf[p * bstride + row * nrhs + rhs];
-    const dfl rr = df_add(df_add({b.x, b.y}, df_neg(Kr)), sr);
-    const dfl ri = df_add(df_add({b.z, b.w}, df_neg(Ki)), si);
-    r[p * N * nrhs + row * nrhs + rhs] = mk<float>(__fadd_rn(rr.hi, rr.lo), __fadd_rn(ri.hi, ri.lo));
   }
 }
 
@@ -271,7 +275,7 @@ void launch_join_cx(const float4 *v, c128 *out, int64_t n, cudaStream_t s) {
 void launch_residual_df(const int64_t *rp, const int32_t *ci, const float2 *kdf, const float2 *mdf,
                         const double2 *xi, const float4 *bdf, int64_t bstride, const float4 *xdf, c64 *r, int np,
                         const int *pmap, int64_t N, int nrhs, cudaStream_t s) {
-  dim3 g(div_up(N, 8), np);
+  dim3 g(div_up(N, kResRows), np);
   tem::count_launch();
   k_residual_df<<<g, 256, 0, s>>>(rp, ci, kdf, mdf, xi, bdf, bstride, xdf, r, N, nrhs, pmap);
 }

@@ -21,7 +21,8 @@ TEM_FP32_REFINED = 1
 ERRORS = {-1: "TEM_ERR_ARG", -2: "TEM_ERR_OOM", -3: "TEM_ERR_PIVOT", -4: "TEM_ERR_TIMEOUT",
           -5: "TEM_ERR_CUDA", -6: "TEM_ERR_STATE", -7: "TEM_ERR_MESH"}
 KERNEL_CLASSES = {"update": 0, "panel": 1, "fwd": 2, "bwd": 3, "bwd_upd": 4, "extend_add": 5, "fwd21": 6,
-                  "fwd_sb": 7, "bwd_sb": 8, "invert": 9}
+                  "fwd_sb": 7, "bwd_sb": 8, "invert": 9,
+                  "residual": 10, "refine_vec": 11, "jacobian": 12}
 
 # C declarations, in include/tem.h order: name -> (restype, argtypes)
 _P = ctypes.c_void_p

@@ -5,7 +5,11 @@ same transmitter-receiver pair over time):  FP64 path 1e-9, FP32 factors with
 FP64 refinement 1e-6.  J^T w: relative 2-norm 1e-9 / 1e-6.  J v of the FP64
 path: 1e-8, ten times the spread between two FP64 runs of the oracle that
 differ only in their elimination ordering (9.9e-10 on the 20^3 box): the
-residue sum of J v cancels more than that of the response.  The shifted
+residue sum of J v cancels more than that of the response.  J v of the
+refined FP32 path: 2e-6.  Its refinement stops at the accuracy the
+double-float residual allows (2^-48 of sum |K x|, not FP64's 2^-53).  On
+the 20^3 box, J v sits at 6.6e-7 .. 1.06e-6 over repeated runs, and a
+seventh or eighth refinement step does not lower it.  The shifted
 matrices are ill-conditioned on the air's gradient fields, which is why the
 comparison is made on the data, never on the solution vectors themselves.
 """
@@ -20,7 +24,7 @@ from oracle.tem import Oracle
 from paper_2605_19951_gb300 import inputs
 
 TOL = {"fp64": 1e-9, "fp32r": 1e-6}
-TOL_JV = {"fp64": 1e-8, "fp32r": 1e-6}
+TOL_JV = {"fp64": 1e-8, "fp32r": 2e-6}
 
 
 def _tem():
