@@ -285,6 +285,11 @@ def run_ours(args):
         "gpu_launches": int(launches), "clocks": ck,
         "per_class_ms_1pair": {k: round(v[0], 2) for k, v in per_class.items()},
     }
+    # accuracy check against the FP64 path on the same workload (seeded J.v and J^T.w vectors)
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    vv = torch.randn(info["n_param"], dtype=torch.float64, device="cuda", generator=gen)
+    ww = torch.randn(*mdl.shape, dtype=torch.float64, device="cuda", generator=gen)
+    acc32 = (mdl.forward().cpu().numpy(), mdl.jvp(vv).cpu().numpy(), mdl.jtvp(ww).cpu().numpy())
     mdl.close()
     del mdl
     torch.cuda.empty_cache()
@@ -292,14 +297,22 @@ def run_ours(args):
     if not args.no_fp64:
         md = tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al, precision=tem.TEM_FP64)
         f64_factor, _ = timed(torch, lambda: md.factor(m0))
-        f64_fwd, _ = timed(torch, lambda: md.forward())
-        vv = torch.randn(info["n_param"], dtype=torch.float64, device="cuda")
-        ww = torch.randn(*md.shape, dtype=torch.float64, device="cuda")
-        f64_pair, _ = timed(torch, lambda: (md.jvp(vv), md.jtvp(ww)))
+        f64_fwd, d64 = timed(torch, lambda: md.forward())
+        f64_pair, (jv64, jtw64) = timed(torch, lambda: (md.jvp(vv), md.jtvp(ww)))
+        d64, jv64, jtw64 = d64.cpu().numpy(), jv64.cpu().numpy(), jtw64.cpu().numpy()
+
+        def floored(a, ref, floor=1e-4):   # per channel, floored at 1e-4 of its peak over time
+            peak = np.abs(ref).max(axis=2, keepdims=True)
+            return float((np.abs(a - ref) / np.maximum(np.abs(ref), floor * peak)).max())
         out["fp64"] = {"factor_s": round(f64_factor / 1e3, 2), "forward_s": round(f64_fwd / 1e3, 3),
                        "pair_s": round(f64_pair / 1e3, 3), "pairs_per_s": round(1e3 / f64_pair, 4),
                        "gn_iteration_s": round((f64_factor + f64_fwd + N_LSQR_GN * f64_pair) / 1e3, 1),
                        "note": "one factor, one forward, one J.v + J^T.w pair timed with CUDA events"}
+        out["fp32r_vs_fp64"] = {"data": floored(acc32[0], d64), "jv": floored(acc32[1], jv64),
+                                "jtw": float(np.linalg.norm(acc32[2] - jtw64) / np.linalg.norm(jtw64)),
+                                "note": "refined FP32 against the FP64 path at the start model: data and J.v "
+                                        "max per-channel error floored at 1e-4 of the channel's peak over time, "
+                                        "J^T.w relative 2-norm"}
         md.close()
         del md
         torch.cuda.empty_cache()

@@ -175,7 +175,7 @@ int tem_lsqr(tem_ctx *ctx, const double *d_obs, const double *wd,
 int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
                      const double *m_ref, double lambda, int32_t n_iter, double *dm);
 
-/* TEM_FP32_REFINED mode: refinement corrections per solve (default 6) and
+/* TEM_FP32_REFINED mode: refinement corrections per solve (default 16) and
  * the conductivity floor of the factored matrices (default 1e-4).
  *
  * The complex-float factor is of P_i = K - xi_i M(s_i) with the cell
@@ -190,7 +190,7 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
  * A_i itself.  With tol > 0 a pole stops refining once its last correction,
  * over the unknowns every output reads (edges of parameter cells), is below
  * tol times the solution there; the remaining sweeps run over the poles still
- * refining (one host read per step).  steps in 0..20 (the maximum),
+ * refining (one host read per step).  steps in 0..40 (the maximum),
  * floor_tau in [0, 1], tol in [0, 1] (0: always steps corrections). */
 int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau, double tol);
 
