@@ -45,6 +45,7 @@ def _hbm_peak():
 
 HBM_PEAK_GBS = _hbm_peak()
 METRIC = "J.v+J^T.w pairs/s and factor time at 700k DoF, refined FP32 vs FP64, same GPU"
+BWD21_TRAFFIC_RATIO = 1.07   # DRAM bytes / factor bytes of the BWD21 product (ncu, 24^3 box)
 
 
 def parse():
@@ -256,14 +257,20 @@ def run_ours(args):
     entries = {"fwd": l11, "fwd21": l21, "bwd": l11, "bwd_upd": l21}[dom]
     alg_bytes = 8.0 * entries * m * sweeps
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    # DRAM traffic per launch: ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 24^3 box's
+    # BWD21 launches of this kernel read 1.07x their factor bytes (the gathered B rows and tile padding
+    # are the excess); the full-size launch is scaled by its factor bytes (entries x 8 B x poles)
+    traffic = round(BWD21_TRAFFIC_RATIO * alg_bytes / max(dom_launches, 1)) if dom == "bwd_upd" else None
     roof = {"kernel": "k_tc_kint<%s>" % {"fwd": "TRI_F", "fwd21": "FWD21", "bwd": "TRI_B", "bwd_upd": "BWD21"}[dom],
             "bound": "hbm", "achieved": round(achieved, 1), "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "frac": round(achieved / HBM_PEAK_GBS, 4), "traffic": None,
+            "frac": round(achieved / HBM_PEAK_GBS, 4), "traffic": traffic,
             "launches": dom_launches, "avg_launch_us": round(1e3 * dom_ms / max(dom_launches, 1), 2),
             "alg_bytes_per_launch": round(alg_bytes / max(dom_launches, 1)),
             "share_of_step": round(dom_ms / t_ms, 3),
             "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured",
-            "bytes_note": "factor entries of the class (c64) x poles x sweeps; B rows and outputs (<3%) not counted"}
+            "bytes_note": "factor entries of the class (c64) x poles x sweeps; B rows and outputs (<3%) not counted",
+            "traffic_note": "DRAM bytes per launch: ncu on the 24^3 box (BWD21 read 1.07x its factor bytes), "
+                            "scaled to this launch's factor bytes"}
 
     pairs_per_s = args.steps / (t_ms * 1e-3) * world
     out = {
