@@ -250,8 +250,9 @@ def run_ours(args):
     # factor once per sweep, so they are bound by HBM; algorithmic bytes = the
     # factor entries the class applies (8 bytes each) x poles x sweeps
     N, m, nrhs = info["n_dof"], info["m"], info["n_tx"]
-    refine = info["refine_steps"]
-    sweeps = (2 * args.steps + 1) * (1 + refine)
+    refine, refine_adj = info["refine_steps"], info["refine_steps_adjoint"]
+    # one LSQR call of K iterations: its start-up J^T.w, then K x (J.v + J^T.w)
+    sweeps = args.steps * (1 + refine) + (args.steps + 1) * (1 + refine_adj)
     l11 = info["nnz_l11"]                         # pivot blocks: T11 = L11^-1, lower triangle
     l21 = info["nnz_l"] - info["nnz_l11"]
     entries = {"fwd": l11, "fwd21": l21, "bwd": l11, "bwd_upd": l21}[dom]
@@ -280,7 +281,7 @@ def run_ours(args):
         "dtype": "c64 factor/solves, double-float (FP32 pair) refinement residual, f64 residue sums and LSQR",
         "data": "synthetic (seeded model, forward of the true model + 3% noise)",
         "config": {"workload": f"{s.n}^3 Kuhn box, {N} DoF, 10 pole pairs, 32 loops, 128 rx, 40 times",
-                   "precision": "fp32-refined", "refine_steps": refine,
+                   "precision": "fp32-refined", "refine_steps": refine, "refine_steps_adjoint": refine_adj,
                    "l2": "inputs larger than L2 (factors %.1f GB per sweep)" % (info["nnz_l"] * m * 8 / 1e9),
                    "step": "one LSQR iteration = one J.v + one J^T.w over all poles x transmitters"},
         "factor_s": round(factor_ms / 1e3, 3), "forward_s": round(forward_ms / 1e3, 3),

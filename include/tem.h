@@ -73,7 +73,7 @@ typedef struct tem_stats {
   int32_t n_times;       /* K */
   int32_t n_tx, n_rx;
   int32_t precision;
-  int32_t refine_steps;  /* refinement corrections per solve (FP32 mode) */
+  int32_t refine_steps;  /* refinement corrections per forward and J v solve (FP32 mode) */
   int32_t last_pivot_front; /* front of the last pivot failure, -1 if none */
   double min_pivot_abs;  /* smallest |d_kk| seen in the last factorisation */
   int64_t nnz_l11;       /* factor entries in the pivot blocks (sum k(k+1)/2) */
@@ -81,7 +81,7 @@ typedef struct tem_stats {
   int64_t pole_solves;   /* poles x (forward + backward sweep) issued so far */
   int64_t solve_calls;   /* multi-pole solves issued so far (each with its refinement) */
   int32_t tc_ctas_per_sm; /* resident CTAs per SM of the tensor-core product kernel (0 before its first launch) */
-  int32_t reserved_;
+  int32_t refine_steps_adjoint; /* refinement corrections per adjoint (J^T w) solve (FP32 mode) */
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or
@@ -175,13 +175,15 @@ int tem_lsqr(tem_ctx *ctx, const double *d_obs, const double *wd,
 int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
                      const double *m_ref, double lambda, int32_t n_iter, double *dm);
 
-/* TEM_FP32_REFINED mode: refinement corrections per solve (default 16) and
- * the conductivity floor of the factored matrices (default 1e-4).
+/* TEM_FP32_REFINED mode: refinement corrections per forward and J v solve
+ * (default 16) and the conductivity floor of the factored matrices (default
+ * 1e-4).
  *
  * The complex-float factor is of P_i = K - xi_i M(s_i) with the cell
  * conductivity raised to s_i,t = max(sigma_t, floor_tau / (|xi_i| mu0 h_t^2)),
  * h_t^2 = vol_t^(2/3); every correction solves with P_i, the residual
- * b - (K - xi_i M(sigma)) x is formed in FP64 with the true matrix.  Without
+ * b - (K - xi_i M(sigma)) x is formed with the true matrix in double-float
+ * pairs (compensated products on the FP32 pipes).  Without
  * the floor the gradient fields of resistive cells (air, 1e-8 S/m) have pivots
  * below float resolution and the refinement diverges.  Gradients of nodes
  * whose cells are all floored are eigenvectors of P_i^-1 A_i, every
@@ -193,6 +195,13 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
  * refining (one host read per step).  steps in 0..40 (the maximum),
  * floor_tau in [0, 1], tol in [0, 1] (0: always steps corrections). */
 int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau, double tol);
+
+/* TEM_FP32_REFINED mode: refinement corrections per adjoint solve, the
+ * solves of tem_jtvp (and of tem_lsqr's J^T w), default 6.  Their output is
+ * the cell sums over parameter cells, which converge in fewer corrections
+ * than the receivers' fields of tem_forward and tem_jvp.  steps in 0..40;
+ * TEM_ERR_ARG otherwise. */
+int tem_set_refine_adjoint(tem_ctx *ctx, int32_t steps);
 
 /* TEM_FP32_REFINED mode: run the update-row products of the solves on the
  * tensor cores (tcgen05, TF32 split into hi + lo parts, three MMAs per

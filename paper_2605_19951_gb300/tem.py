@@ -41,6 +41,7 @@ SIGNATURES = {
     "tem_lsqr": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
+    "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
     "tem_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
@@ -58,7 +59,7 @@ class TemStats(ctypes.Structure):
                 ("m", _I32), ("n_times", _I32), ("n_tx", _I32), ("n_rx", _I32),
                 ("precision", _I32), ("refine_steps", _I32), ("last_pivot_front", _I32),
                 ("min_pivot_abs", _D), ("nnz_l11", _I64), ("n_solve_launch", _I64),
-                ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("reserved_", _I32)]
+                ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("refine_steps_adjoint", _I32)]
 
 
 class TemError(RuntimeError):
@@ -177,6 +178,10 @@ def tem_lsqr_noalloc(ctx, d_obs, wd, m_ref, lam, n_iter, dm):
 
 def tem_set_refine(ctx, steps, floor_tau=1e-4, tol=0.0):
     _check(ctx, load().tem_set_refine(ctx, int(steps), float(floor_tau), float(tol)))
+
+
+def tem_set_refine_adjoint(ctx, steps):
+    _check(ctx, load().tem_set_refine_adjoint(ctx, int(steps)))
 
 
 def tem_set_tensor_cores(ctx, enable):
