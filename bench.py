@@ -291,7 +291,7 @@ def run_ours(args):
         "e2e": {"value": round(args.steps / (e2e_ms * 1e-3) * world, 4), "unit": "pairs/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(launches), "clocks": ck,
-        "per_class_ms_1pair": {k: round(v[0], 2) for k, v in per_class.items()},
+        "per_class_ms_lsqr_call": {k: round(v[0], 2) for k, v in per_class.items()},
     }
     # accuracy check against the FP64 path on the same workload (seeded J.v and J^T.w vectors)
     gen = torch.Generator(device="cuda").manual_seed(1234)
