@@ -6,10 +6,12 @@ FP64 refinement 1e-6.  J^T w: relative 2-norm 1e-9 / 1e-6.  J v of the FP64
 path: 1e-8, ten times the spread between two FP64 runs of the oracle that
 differ only in their elimination ordering (9.9e-10 on the 20^3 box): the
 residue sum of J v cancels more than that of the response.  J v of the
-refined FP32 path: 2e-6.  Its refinement stops at the accuracy the
-double-float residual allows (2^-48 of sum |K x|, not FP64's 2^-53).  On
-the 20^3 box, J v sits at 6.6e-7 .. 1.06e-6 over repeated runs, and a
-seventh or eighth refinement step does not lower it.  The shifted
+refined FP32 path: 2e-6.  Its refinement stops at a floor that more
+corrections do not lower: on the 20^3 box J v sits at 6.6e-7 .. 1.06e-6
+over repeated runs, also after a seventh or eighth step.  The floor comes
+from the floored factor, not from the double-float residual: on the 46^3
+box it rises as the floor tau falls (1e-4, 1e-5, 1e-6 give data 2e-6,
+6e-5, 2e-3).  The shifted
 matrices are ill-conditioned on the air's gradient fields, which is why the
 comparison is made on the data, never on the solution vectors themselves.
 """
