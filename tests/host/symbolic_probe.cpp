@@ -1,0 +1,50 @@
+// Test probe (not part of the library): runs the host set-up of a mesh
+// (edges, PEC removal, nested dissection, fronts) without a GPU and writes
+// what the symbolic checks need, in native binary:
+//   int64 N, int64 nt, int32 tdof[nt*6], int64 nfront,
+//   per front: int32 k, n, c0, parent, then n - k int32 update rows,
+//   int64 nnz_l (meaningful factor entries per pole).
+// Input (argv[1], native binary): int64 nv, int64 nt, int32 leaf_max,
+// double xyz[nv*3], int32 tets[nt*4], double sigma[nt], uint8 is_param[nt].
+#include <cstdio>
+#include <vector>
+#include "tem_internal.h"
+
+int main(int argc, char **argv) {
+  if (argc != 3) return 2;
+  FILE *f = std::fopen(argv[1], "rb");
+  if (!f) return 2;
+  int64_t nv = 0, nt = 0;
+  int32_t leaf = 0;
+  bool ok = std::fread(&nv, 8, 1, f) == 1 && std::fread(&nt, 8, 1, f) == 1 && std::fread(&leaf, 4, 1, f) == 1;
+  std::vector<double> xyz(3 * nv > 0 ? 3 * nv : 0), sig(nt > 0 ? nt : 0);
+  std::vector<int32_t> tets(4 * nt > 0 ? 4 * nt : 0);
+  std::vector<uint8_t> ip(nt > 0 ? nt : 0);
+  ok = ok && std::fread(xyz.data(), 8, xyz.size(), f) == xyz.size() &&
+       std::fread(tets.data(), 4, tets.size(), f) == tets.size() && std::fread(sig.data(), 8, sig.size(), f) == sig.size() &&
+       std::fread(ip.data(), 1, ip.size(), f) == ip.size();
+  std::fclose(f);
+  if (!ok) return 2;
+  tem::Mesh m;
+  tem::Symbolic s;
+  const std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), leaf, s);
+  if (!e.empty()) {
+    std::fprintf(stderr, "%s\n", e.c_str());
+    return 1;
+  }
+  FILE *o = std::fopen(argv[2], "wb");
+  if (!o) return 2;
+  const int64_t nf = (int64_t)s.fronts.size();
+  std::fwrite(&m.N, 8, 1, o);
+  std::fwrite(&m.nt, 8, 1, o);
+  std::fwrite(m.tdof.data(), 4, m.tdof.size(), o);
+  std::fwrite(&nf, 8, 1, o);
+  for (const tem::Front &F : s.fronts) {
+    const int32_t h[4] = {F.k, F.n, F.c0, F.parent};
+    std::fwrite(h, 4, 4, o);
+    std::fwrite(s.rows.data() + F.rows_off, 4, F.n - F.k, o);
+  }
+  std::fwrite(&s.nnz_l, 8, 1, o);
+  std::fclose(o);
+  return 0;
+}

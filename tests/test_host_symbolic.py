@@ -1,0 +1,141 @@
+"""Host set-up (nested dissection, assembly tree, update rows) checked on the CPU.
+
+The probe in tests/host/ runs the library's host code (csrc/host.cpp) on a mesh
+without a GPU.  The checks rebuild the factor structure independently:
+- A's pattern comes from the tetrahedra's unknowns (every pair of unknowns
+  of a tetrahedron couples);
+- the symbolic Cholesky structure of L, in the library's elimination order,
+  comes from the elimination tree with set unions: struct(j) = {i > j : A_ij
+  != 0} united with struct(c) - {j} over the children c of j.
+Then every nonzero of L must lie inside its front (the front's later pivots
+and its update rows), and the fronts must partition the unknowns and nest in
+their parents.
+"""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2605_19951_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "..", "paper_2605_19951_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def probe():
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    d = tempfile.mkdtemp(prefix="tem_symprobe_")
+    exe = os.path.join(d, "symprobe")
+    subprocess.check_call([gxx, "-O2", "-std=c++17", "-I", CSRC, "-o", exe,
+                           os.path.join(HERE, "host", "symbolic_probe.cpp"), os.path.join(CSRC, "host.cpp")])
+    yield exe, d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+def run_probe(probe, s, leaf):
+    exe, d = probe
+    src, dst = os.path.join(d, "mesh.bin"), os.path.join(d, "sym.bin")
+    with open(src, "wb") as f:
+        np.array([s.xyz.shape[0], s.tets.shape[0]], np.int64).tofile(f)
+        np.array([leaf], np.int32).tofile(f)
+        np.ascontiguousarray(s.xyz, np.float64).tofile(f)
+        np.ascontiguousarray(s.tets, np.int32).tofile(f)
+        np.ascontiguousarray(s.sigma, np.float64).tofile(f)
+        np.ascontiguousarray(s.is_param, np.uint8).tofile(f)
+    subprocess.check_call([exe, src, dst])
+    raw = open(dst, "rb").read()
+    pos = 0
+
+    def take(dtype, count):
+        nonlocal pos
+        a = np.frombuffer(raw, dtype=dtype, count=count, offset=pos)
+        pos += a.nbytes
+        return a
+
+    N, nt = (int(x) for x in take(np.int64, 2))
+    tdof = take(np.int32, 6 * nt).reshape(nt, 6)
+    nf = int(take(np.int64, 1)[0])
+    fronts = []
+    for _ in range(nf):
+        k, n, c0, parent = (int(x) for x in take(np.int32, 4))
+        rows = take(np.int32, n - k).copy()
+        fronts.append((k, n, c0, parent, rows))
+    nnz_l = int(take(np.int64, 1)[0])
+    assert pos == len(raw)
+    return N, tdof, fronts, nnz_l
+
+
+def symbolic_cholesky(N, tdof):
+    """Row structure below the diagonal of every column of L (elimination tree, set unions)."""
+    lower = [set() for _ in range(N)]
+    for dofs in tdof:
+        u = [int(x) for x in dofs if x >= 0]
+        for a in u:
+            for b in u:
+                if b > a:
+                    lower[a].add(b)
+    children = [[] for _ in range(N)]
+    struct = [None] * N
+    for j in range(N):
+        sj = set(lower[j])
+        for c in children[j]:
+            sj |= struct[c]
+        sj.discard(j)
+        struct[j] = sj
+        if sj:
+            children[min(sj)].append(j)
+    return struct
+
+
+def check_structure(N, tdof, fronts, nnz_l):
+    # unknowns: tdof covers 0..N-1 (PEC edges are -1)
+    used = np.unique(tdof[tdof >= 0])
+    assert used.size == N and used[0] == 0 and used[-1] == N - 1
+    # pivots of the fronts partition 0..N-1
+    cover = np.zeros(N, np.int32)
+    for k, n, c0, parent, rows in fronts:
+        assert k >= 0 and n >= k
+        cover[c0:c0 + k] += 1
+    assert (cover == 1).all()
+    # update rows: sorted, after the front's pivots, inside the parent's columns
+    for q, (k, n, c0, parent, rows) in enumerate(fronts):
+        assert (np.diff(rows) > 0).all()
+        if rows.size:
+            assert rows[0] >= c0 + k and rows[-1] < N
+            assert parent > q   # children precede parents
+        if parent >= 0:
+            pk, pn, pc0, _, prows = fronts[parent]
+            pcols = set(range(pc0, pc0 + pk)) | set(prows.tolist())
+            assert set(rows.tolist()) <= pcols
+    # every nonzero of L inside its front
+    owner = np.empty(N, np.int64)
+    for q, (k, n, c0, parent, rows) in enumerate(fronts):
+        owner[c0:c0 + k] = q
+    struct = symbolic_cholesky(N, tdof)
+    true_nnz = 0
+    for j in range(N):
+        k, n, c0, parent, rows = fronts[owner[j]]
+        allowed = set(range(j + 1, c0 + k)) | set(rows.tolist())
+        assert struct[j] <= allowed, (j, sorted(struct[j] - allowed)[:5])
+        true_nnz += len(struct[j]) + 1
+    # the library's count of factor entries: every front's triangle and update block
+    lib = sum(k * (k + 1) // 2 + k * (n - k) for k, n, c0, parent, rows in fronts)
+    assert lib == nnz_l
+    assert nnz_l >= true_nnz
+
+
+@pytest.mark.parametrize("leaf", [0, 16, 64])
+def test_fronts_contain_symbolic_cholesky(probe, leaf):
+    s = inputs.make_config(1)
+    check_structure(*run_probe(probe, s, leaf))
+
+
+def test_fronts_with_a_conductive_block(probe):
+    s = inputs.make_config(2, n=6)
+    check_structure(*run_probe(probe, s, 24))
