@@ -358,19 +358,21 @@ def cpu_baseline(steps=1, warmup=0, n=46):
         o.jtvp(w)
     t_pair = (time.perf_counter() - t0) / steps
     s4 = inputs.make_config(CONFIG, n=n)
-    units = {}
+    units, dofs = {}, {}
     for key, s in (("c2", s2), ("c4", s4)):
         ctx = tem.tem_create(tem.TEM_FP64)
         try:
             tem.tem_mesh(ctx, s.xyz, s.tets, s.sigma, s.is_param)
-            units[key] = tem.tem_info(ctx)["nnz_l"] * s.m * len(s.loops)
+            info = tem.tem_info(ctx)
+            units[key] = info["nnz_l"] * s.m * len(s.loops)
+            dofs[key] = info["n_dof"]
         finally:
             tem.tem_destroy(ctx)
     scale = units["c4"] / units["c2"]
     return {"value": round(1.0 / (t_pair * scale), 6), "unit": "pairs/s", "cores": 1, "kind": "oracle",
             "sample": f"{steps} oracle pair(s) of the 20^3 box ({t_pair:.2f} s each, one thread), "
                       f"scaled by factor entries x RHS x poles ({scale:.0f}x) to the {n}^3 workload",
-            "pair_s_sample": round(t_pair, 3), "scale": round(scale, 1)}
+            "pair_s_sample": round(t_pair, 3), "scale": round(scale, 1), "workload_dof": int(dofs["c4"])}
 
 
 def run_reference(args):
@@ -380,11 +382,12 @@ def run_reference(args):
     import torch  # noqa: F401  (the library context for the symbolic sizes needs the GPU)
     t0 = time.perf_counter()
     cb = cpu_baseline(steps=args.steps, warmup=args.warmup, n=args.n)
+    n, N = args.n, cb["workload_dof"]
     per_pair_s = 1.0 / cb["value"]
     out = {"metric": METRIC, "value": cb["value"], "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(per_pair_s * 1e3, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{s.n}^3 Kuhn box, {N} DoF, 10 pole pairs, 32 loops, 128 rx, 40 times",
+           "config": {"workload": f"{n}^3 Kuhn box, {N} DoF, 10 pole pairs, 32 loops, 128 rx, 40 times",
                       "sample": cb["sample"]},
            "impl": "reference", "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
