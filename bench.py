@@ -154,6 +154,20 @@ def synthetic(tem, s, xi, al, torch):
     return mdl, d_obs, wd
 
 
+def max_over_ranks(torch, dist, values, device):
+    """Each timing's largest value over all ranks (unchanged on one rank)."""
+    if dist is None:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def timed(torch, fn):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -223,10 +237,7 @@ def run_ours(args):
     barrier()
     dom_ms, dom_launches = tem.tem_kernel_time(mdl.ctx)
     tem.tem_set_profiling(mdl.ctx, None)
-    if dist is not None:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms, = max_over_ranks(torch, dist, [t_ms], "cuda")
 
     # end to end through the public API: pinned host inputs, result read back
     d_obs_p = torch.as_tensor(d_obs_h).pin_memory()
@@ -243,6 +254,7 @@ def run_ours(args):
         return dm_p
 
     e2e_ms, _ = timed(torch, e2e)
+    e2e_ms, = max_over_ranks(torch, dist, [e2e_ms], "cuda")
     h2d = (d_obs_p.numel() + wd_p.numel() + m0_p.numel()) * 8
     d2h = dm_p.numel() * 8
 
@@ -273,7 +285,7 @@ def run_ours(args):
             "traffic_note": "DRAM bytes per launch: ncu on the 24^3 box (BWD21 read 1.07x its factor bytes), "
                             "scaled to this launch's factor bytes"}
 
-    pairs_per_s = args.steps / (t_ms * 1e-3) * world
+    pairs_per_s = whole_job_rate(args.steps, world, t_ms)
     out = {
         "metric": METRIC, "value": round(pairs_per_s, 4), "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 2),
@@ -288,7 +300,7 @@ def run_ours(args):
         "gn_iteration_s": round((factor_ms + forward_ms + N_LSQR_GN * t_ms / args.steps) / 1e3, 2),
         "gn_iteration_note": "factor + forward + 30 LSQR pairs at the measured rates (linear model, Fig. 10)",
         "roofline": roof,
-        "e2e": {"value": round(args.steps / (e2e_ms * 1e-3) * world, 4), "unit": "pairs/s",
+        "e2e": {"value": round(whole_job_rate(args.steps, world, e2e_ms), 4), "unit": "pairs/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(launches), "clocks": ck,
         "per_class_ms_lsqr_call": {k: round(v[0], 2) for k, v in per_class.items()},
