@@ -3,7 +3,8 @@
 //   int64 N, int64 ne, int32 ev[ne*2], int32 dof_old[ne], int32 perm[N],
 //   int64 rp[N+1], int64 nnz, int32 ci[nnz], double kval[nnz],
 //   int32 n_tx, double f[N*n_tx], int32 n_rx, int64 q_rp[n_rx+1],
-//   int64 nq, int32 q_ci[nq], double q_val[nq].
+//   int64 nq, int32 q_ci[nq], double q_val[nq], then Q^T as distinct unknowns:
+//   int64 nqd, int32 qt_dof[nqd], int64 qt_rp[nqd+1], int32 qt_ci[nq], double qt_val[nq].
 // Input (argv[1]): int64 nv, int64 nt, double xyz[nv*3], int32 tets[nt*4],
 // double sigma[nt], uint8 is_param[nt], int32 n_tx, int64 loop_ptr[n_tx+1],
 // int32 loop_verts[loop_ptr[n_tx]], int32 n_rx, double rx[n_rx*3].
@@ -68,6 +69,12 @@ int main(int argc, char **argv) {
   std::fwrite(&nq, 8, 1, o);
   wr(o, q_ci);
   wr(o, q_val);
+  const int64_t nqd = (int64_t)qt_dof.size();
+  std::fwrite(&nqd, 8, 1, o);
+  wr(o, qt_dof);
+  wr(o, qt_rp);
+  wr(o, qt_ci);
+  wr(o, qt_val);
   std::fclose(o);
   return 0;
 }

@@ -7,7 +7,9 @@ unknowns are mapped to the oracle's through the edges' end points (both
 orient an edge from its lower to its higher vertex id).  Then:
 - K (curl-curl) must equal the oracle's element by element;
 - f must equal the oracle's exactly (+-1 on the loop's edges);
-- Q must equal the oracle's (Stokes reading of dB_z/dt on the surface faces).
+- Q must equal the oracle's (Stokes reading of dB_z/dt on the surface faces);
+- the library's Q^T (the unknowns Q reads, each with its receivers) must be
+  exactly Q transposed.
 """
 import os
 import shutil
@@ -76,6 +78,9 @@ def run_probe(probe, s):
     out["q_rp"] = take(np.int64, n_rx + 1)
     nq = int(take(np.int64, 1)[0])
     out["q_ci"], out["q_val"] = take(np.int32, nq), take(np.float64, nq)
+    nqd = int(take(np.int64, 1)[0])
+    out["qt_dof"], out["qt_rp"] = take(np.int32, nqd), take(np.int64, nqd + 1)
+    out["qt_ci"], out["qt_val"] = take(np.int32, nq), take(np.float64, nq)
     assert pos == len(raw)
     return out
 
@@ -110,3 +115,10 @@ def test_host_assembly_matches_oracle(probe, idx, n):
     Qo = observation_operator(fe, s.rx).tocsr()
     qmap = (Ql @ P.T).tocsr()
     assert abs(qmap - Qo).max() <= 1e-12 * abs(Qo).max()
+    # Q^T over the distinct unknowns Q reads is exactly Q transposed
+    qd = lib["qt_dof"].astype(np.int64)
+    assert (np.diff(qd) > 0).all()
+    cols = np.repeat(qd, np.diff(lib["qt_rp"]))
+    Qt = sp.csr_matrix((lib["qt_val"], (lib["qt_ci"], cols)), shape=(len(s.rx), N))
+    assert abs(Qt - Ql).max() == 0.0
+    assert np.array_equal(np.unique(lib["q_ci"]), qd)

@@ -8,8 +8,9 @@ without a GPU.  The checks rebuild the factor structure independently:
   comes from the elimination tree with set unions: struct(j) = {i > j : A_ij
   != 0} united with struct(c) - {j} over the children c of j.
 Then every nonzero of L must lie inside its front (the front's later pivots
-and its update rows), and the fronts must partition the unknowns and nest in
-their parents.
+and its update rows), the fronts must partition the unknowns and nest in
+their parents, and each extend-add relative map must point at exactly the
+child's update rows inside the parent front.
 """
 import os
 import shutil
@@ -65,7 +66,8 @@ def run_probe(probe, s, leaf):
     for _ in range(nf):
         k, n, c0, parent = (int(x) for x in take(np.int32, 4))
         rows = take(np.int32, n - k).copy()
-        fronts.append((k, n, c0, parent, rows))
+        rel = take(np.int32, n - k).copy() if parent >= 0 else None
+        fronts.append((k, n, c0, parent, rows, rel))
     nnz_l = int(take(np.int64, 1)[0])
     assert pos == len(raw)
     return N, tdof, fronts, nnz_l
@@ -99,33 +101,36 @@ def check_structure(N, tdof, fronts, nnz_l):
     assert used.size == N and used[0] == 0 and used[-1] == N - 1
     # pivots of the fronts partition 0..N-1
     cover = np.zeros(N, np.int32)
-    for k, n, c0, parent, rows in fronts:
+    for k, n, c0, parent, rows, rel in fronts:
         assert k >= 0 and n >= k
         cover[c0:c0 + k] += 1
     assert (cover == 1).all()
-    # update rows: sorted, after the front's pivots, inside the parent's columns
-    for q, (k, n, c0, parent, rows) in enumerate(fronts):
+    # update rows: sorted, after the front's pivots, inside the parent's columns, and the
+    # extend-add relative map points at exactly those rows of the parent front (pivots
+    # first, then its update rows)
+    for q, (k, n, c0, parent, rows, rel) in enumerate(fronts):
         assert (np.diff(rows) > 0).all()
         if rows.size:
             assert rows[0] >= c0 + k and rows[-1] < N
             assert parent > q   # children precede parents
         if parent >= 0:
-            pk, pn, pc0, _, prows = fronts[parent]
-            pcols = set(range(pc0, pc0 + pk)) | set(prows.tolist())
-            assert set(rows.tolist()) <= pcols
+            pk, pn, pc0, _, prows, _ = fronts[parent]
+            pglobal = np.concatenate([np.arange(pc0, pc0 + pk), prows])
+            assert ((rel >= 0) & (rel < pn)).all()
+            np.testing.assert_array_equal(pglobal[rel], rows)
     # every nonzero of L inside its front
     owner = np.empty(N, np.int64)
-    for q, (k, n, c0, parent, rows) in enumerate(fronts):
+    for q, (k, n, c0, parent, rows, rel) in enumerate(fronts):
         owner[c0:c0 + k] = q
     struct = symbolic_cholesky(N, tdof)
     true_nnz = 0
     for j in range(N):
-        k, n, c0, parent, rows = fronts[owner[j]]
+        k, n, c0, parent, rows, rel = fronts[owner[j]]
         allowed = set(range(j + 1, c0 + k)) | set(rows.tolist())
         assert struct[j] <= allowed, (j, sorted(struct[j] - allowed)[:5])
         true_nnz += len(struct[j]) + 1
     # the library's count of factor entries: every front's triangle and update block
-    lib = sum(k * (k + 1) // 2 + k * (n - k) for k, n, c0, parent, rows in fronts)
+    lib = sum(k * (k + 1) // 2 + k * (n - k) for k, n, c0, parent, rows, rel in fronts)
     assert lib == nnz_l
     assert nnz_l >= true_nnz
 
