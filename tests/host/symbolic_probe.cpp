@@ -2,9 +2,10 @@
 // (edges, PEC removal, nested dissection, fronts) without a GPU and writes
 // what the symbolic checks need, in native binary:
 //   int64 N, int64 nt, int32 tdof[nt*6], int64 nfront,
-//   per front: int32 k, n, c0, parent, then n - k int32 update rows and
-//   (non-root fronts) n - k int32 positions of those rows in the parent front
-//   (the extend-add relative map), int64 nnz_l (factor entries per pole).
+//   per front: int32 k, n, c0, parent, height, ld, int64 lofs, uofs, then
+//   n - k int32 update rows and (non-root fronts) n - k int32 positions of
+//   those rows in the parent front (the extend-add relative map),
+//   then int64 nnz_l (factor entries per pole), ltotal, utotal.
 // Input (argv[1], native binary): int64 nv, int64 nt, int32 leaf_max,
 // double xyz[nv*3], int32 tets[nt*4], double sigma[nt], uint8 is_param[nt].
 #include <cstdio>
@@ -41,12 +42,16 @@ int main(int argc, char **argv) {
   std::fwrite(m.tdof.data(), 4, m.tdof.size(), o);
   std::fwrite(&nf, 8, 1, o);
   for (const tem::Front &F : s.fronts) {
-    const int32_t h[4] = {F.k, F.n, F.c0, F.parent};
-    std::fwrite(h, 4, 4, o);
+    const int32_t h[6] = {F.k, F.n, F.c0, F.parent, F.height, F.ld};
+    const int64_t offs[2] = {F.lofs, F.uofs};
+    std::fwrite(h, 4, 6, o);
+    std::fwrite(offs, 8, 2, o);
     std::fwrite(s.rows.data() + F.rows_off, 4, F.n - F.k, o);
     if (F.parent >= 0) std::fwrite(s.rel.data() + F.rel_off, 4, F.n - F.k, o);
   }
   std::fwrite(&s.nnz_l, 8, 1, o);
+  std::fwrite(&s.ltotal, 8, 1, o);
+  std::fwrite(&s.utotal, 8, 1, o);
   std::fclose(o);
   return 0;
 }

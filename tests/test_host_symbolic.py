@@ -9,8 +9,9 @@ without a GPU.  The checks rebuild the factor structure independently:
   != 0} united with struct(c) - {j} over the children c of j.
 Then every nonzero of L must lie inside its front (the front's later pivots
 and its update rows), the fronts must partition the unknowns and nest in
-their parents, and each extend-add relative map must point at exactly the
-child's update rows inside the parent front.
+their parents, each extend-add relative map must point at exactly the
+child's update rows inside the parent front, and the memory plan must keep
+factor blocks disjoint and simultaneously alive update blocks disjoint.
 """
 import os
 import shutil
@@ -62,15 +63,17 @@ def run_probe(probe, s, leaf):
     N, nt = (int(x) for x in take(np.int64, 2))
     tdof = take(np.int32, 6 * nt).reshape(nt, 6)
     nf = int(take(np.int64, 1)[0])
-    fronts = []
+    fronts, layout = [], []
     for _ in range(nf):
-        k, n, c0, parent = (int(x) for x in take(np.int32, 4))
+        k, n, c0, parent, height, ld = (int(x) for x in take(np.int32, 6))
+        lofs, uofs = (int(x) for x in take(np.int64, 2))
         rows = take(np.int32, n - k).copy()
         rel = take(np.int32, n - k).copy() if parent >= 0 else None
         fronts.append((k, n, c0, parent, rows, rel))
-    nnz_l = int(take(np.int64, 1)[0])
+        layout.append((height, ld, lofs, uofs))
+    nnz_l, ltotal, utotal = (int(x) for x in take(np.int64, 3))
     assert pos == len(raw)
-    return N, tdof, fronts, nnz_l
+    return N, tdof, fronts, nnz_l, (layout, ltotal, utotal)
 
 
 def symbolic_cholesky(N, tdof):
@@ -95,7 +98,38 @@ def symbolic_cholesky(N, tdof):
     return struct
 
 
-def check_structure(N, tdof, fronts, nnz_l):
+def check_memory_plan(fronts, layout, ltotal, utotal):
+    """Factor blocks are disjoint; update blocks alive at the same level are disjoint.
+
+    Front f's n x k factor block (column stride ld = n rounded up to even) sits at
+    lofs.  Its b x b update block sits at uofs from its own level until its
+    parent's level, where extend-add consumes it while the parent's blocks are
+    being filled."""
+    spans = []
+    for (k, n, c0, parent, rows, rel), (height, ld, lofs, uofs) in zip(fronts, layout):
+        assert ld == n + (n & 1)
+        spans.append((lofs, lofs + ld * k))
+    spans.sort()
+    assert spans[0][0] >= 0 and spans[-1][1] <= ltotal
+    assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+    H = max(h for h, _, _, _ in layout)
+    for level in range(H + 1):
+        alive = []
+        for (k, n, c0, parent, rows, rel), (height, ld, lofs, uofs) in zip(fronts, layout):
+            b = n - k
+            if b == 0:
+                continue
+            assert parent >= 0 and layout[parent][0] > height
+            if height <= level <= layout[parent][0]:
+                alive.append((uofs, uofs + b * b))
+        alive.sort()
+        if alive:
+            assert alive[0][0] >= 0 and alive[-1][1] <= utotal
+            assert all(a[1] <= b[0] for a, b in zip(alive, alive[1:])), level
+
+
+def check_structure(N, tdof, fronts, nnz_l, plan):
+    check_memory_plan(fronts, *plan)
     # unknowns: tdof covers 0..N-1 (PEC edges are -1)
     used = np.unique(tdof[tdof >= 0])
     assert used.size == N and used[0] == 0 and used[-1] == N - 1
