@@ -5,7 +5,10 @@
 //   per front: int32 k, n, c0, parent, height, ld, int64 lofs, uofs, then
 //   n - k int32 update rows and (non-root fronts) n - k int32 positions of
 //   those rows in the parent front (the extend-add relative map),
-//   then int64 nnz_l (factor entries per pole), ltotal, utotal.
+//   then int64 nnz_l (factor entries per pole), ltotal, utotal, the CSR of A in
+//   the elimination order (int64 rp[N+1], int64 nnz, int32 ci[nnz]) and the
+//   map of A's lower-triangle entries to factor positions (int64 no,
+//   int64 orig_nz[no], int64 orig_dst[no]).
 // Input (argv[1], native binary): int64 nv, int64 nt, int32 leaf_max,
 // double xyz[nv*3], int32 tets[nt*4], double sigma[nt], uint8 is_param[nt].
 #include <cstdio>
@@ -52,6 +55,13 @@ int main(int argc, char **argv) {
   std::fwrite(&s.nnz_l, 8, 1, o);
   std::fwrite(&s.ltotal, 8, 1, o);
   std::fwrite(&s.utotal, 8, 1, o);
+  const int64_t nnz = (int64_t)m.ci.size(), no = (int64_t)s.orig_nz.size();
+  std::fwrite(m.rp.data(), 8, m.rp.size(), o);
+  std::fwrite(&nnz, 8, 1, o);
+  std::fwrite(m.ci.data(), 4, m.ci.size(), o);
+  std::fwrite(&no, 8, 1, o);
+  std::fwrite(s.orig_nz.data(), 8, s.orig_nz.size(), o);
+  std::fwrite(s.orig_dst.data(), 8, s.orig_dst.size(), o);
   std::fclose(o);
   return 0;
 }

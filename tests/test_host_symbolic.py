@@ -10,8 +10,9 @@ without a GPU.  The checks rebuild the factor structure independently:
 Then every nonzero of L must lie inside its front (the front's later pivots
 and its update rows), the fronts must partition the unknowns and nest in
 their parents, each extend-add relative map must point at exactly the
-child's update rows inside the parent front, and the memory plan must keep
-factor blocks disjoint and simultaneously alive update blocks disjoint.
+child's update rows inside the parent front, the memory plan must keep
+factor blocks disjoint and simultaneously alive update blocks disjoint, and
+every lower-triangle entry of A must go once to its factor position.
 """
 import os
 import shutil
@@ -72,8 +73,12 @@ def run_probe(probe, s, leaf):
         fronts.append((k, n, c0, parent, rows, rel))
         layout.append((height, ld, lofs, uofs))
     nnz_l, ltotal, utotal = (int(x) for x in take(np.int64, 3))
+    rp = take(np.int64, N + 1)
+    ci = take(np.int32, int(take(np.int64, 1)[0]))
+    no = int(take(np.int64, 1)[0])
+    onz, odst = take(np.int64, no), take(np.int64, no)
     assert pos == len(raw)
-    return N, tdof, fronts, nnz_l, (layout, ltotal, utotal)
+    return N, tdof, fronts, nnz_l, (layout, ltotal, utotal), (rp, ci, onz, odst)
 
 
 def symbolic_cholesky(N, tdof):
@@ -128,8 +133,30 @@ def check_memory_plan(fronts, layout, ltotal, utotal):
             assert all(a[1] <= b[0] for a, b in zip(alive, alive[1:])), level
 
 
-def check_structure(N, tdof, fronts, nnz_l, plan):
+def check_original_entries(N, fronts, layout, rp, ci, onz, odst):
+    """Every lower-triangle entry (row r >= column c) of A goes exactly once to
+    the factor position of (r, c) in the front that owns column c: column
+    c - c0, row r - c0 among the pivots or k + (r's place among the update
+    rows)."""
+    owner = np.empty(N, np.int64)
+    for q, (k, n, c0, parent, rows, rel) in enumerate(fronts):
+        owner[c0:c0 + k] = q
+    row_of = np.repeat(np.arange(N), np.diff(rp))
+    lower = np.nonzero(ci >= row_of)[0]
+    assert np.array_equal(np.sort(onz), lower)
+    for z, dst in zip(onz.tolist(), odst.tolist()):
+        c, r = int(row_of[z]), int(ci[z])
+        k, n, c0, parent, rows, rel = fronts[owner[c]]
+        height, ld, lofs, uofs = layout[owner[c]]
+        loc = r - c0 if r < c0 + k else k + int(np.searchsorted(rows, r))
+        assert loc < n and (r < c0 + k or rows[loc - k] == r)
+        assert dst == lofs + (c - c0) * ld + loc
+    assert np.unique(odst).size == odst.size
+
+
+def check_structure(N, tdof, fronts, nnz_l, plan, entries):
     check_memory_plan(fronts, *plan)
+    check_original_entries(N, fronts, plan[0], *entries)
     # unknowns: tdof covers 0..N-1 (PEC edges are -1)
     used = np.unique(tdof[tdof >= 0])
     assert used.size == N and used[0] == 0 and used[-1] == N - 1
