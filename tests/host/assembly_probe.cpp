@@ -4,7 +4,10 @@
 //   int64 rp[N+1], int64 nnz, int32 ci[nnz], double kval[nnz],
 //   int32 n_tx, double f[N*n_tx], int32 n_rx, int64 q_rp[n_rx+1],
 //   int64 nq, int32 q_ci[nq], double q_val[nq], then Q^T as distinct unknowns:
-//   int64 nqd, int32 qt_dof[nqd], int64 qt_rp[nqd+1], int32 qt_ci[nq], double qt_val[nq].
+//   int64 nqd, int32 qt_dof[nqd], int64 qt_rp[nqd+1], int32 qt_ci[nq], double qt_val[nq],
+//   then the M-value contributions (int64 mc_ptr[nnz+1], int64 nmc, uint32 mc_idx[nmc],
+//   double Me1[nt*36]) and the unknown -> (tet, local edge) incidence
+//   (int64 inc_ptr[N+1], int64 ninc, int32 inc_tet[ninc], int8 inc_loc[ninc], int32 tdof[nt*6]).
 // Input (argv[1]): int64 nv, int64 nt, double xyz[nv*3], int32 tets[nt*4],
 // double sigma[nt], uint8 is_param[nt], int32 n_tx, int64 loop_ptr[n_tx+1],
 // int32 loop_verts[loop_ptr[n_tx]], int32 n_rx, double rx[n_rx*3].
@@ -75,6 +78,16 @@ int main(int argc, char **argv) {
   wr(o, qt_rp);
   wr(o, qt_ci);
   wr(o, qt_val);
+  const int64_t nmc = (int64_t)m.mc_idx.size(), ninc = (int64_t)m.inc_tet.size();
+  wr(o, m.mc_ptr);
+  std::fwrite(&nmc, 8, 1, o);
+  wr(o, m.mc_idx);
+  wr(o, m.Me1);
+  wr(o, m.inc_ptr);
+  std::fwrite(&ninc, 8, 1, o);
+  wr(o, m.inc_tet);
+  wr(o, m.inc_loc);
+  wr(o, m.tdof);
   std::fclose(o);
   return 0;
 }

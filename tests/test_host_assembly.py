@@ -9,7 +9,11 @@ orient an edge from its lower to its higher vertex id).  Then:
 - f must equal the oracle's exactly (+-1 on the loop's edges);
 - Q must equal the oracle's (Stokes reading of dB_z/dt on the surface faces);
 - the library's Q^T (the unknowns Q reads, each with its receivers) must be
-  exactly Q transposed.
+  exactly Q transposed;
+- M(sigma) summed through the library's per-entry contribution lists (what
+  the GPU sums) must equal the oracle's mass matrix;
+- the unknown -> (tetrahedron, local edge) incidence must list exactly the
+  tetrahedra that carry each unknown.
 """
 import os
 import shutil
@@ -81,6 +85,14 @@ def run_probe(probe, s):
     nqd = int(take(np.int64, 1)[0])
     out["qt_dof"], out["qt_rp"] = take(np.int32, nqd), take(np.int64, nqd + 1)
     out["qt_ci"], out["qt_val"] = take(np.int32, nq), take(np.float64, nq)
+    out["mc_ptr"] = take(np.int64, nnz + 1)
+    out["mc_idx"] = take(np.uint32, int(take(np.int64, 1)[0]))
+    nt = s.tets.shape[0]
+    out["Me1"] = take(np.float64, nt * 36)
+    out["inc_ptr"] = take(np.int64, N + 1)
+    ninc = int(take(np.int64, 1)[0])
+    out["inc_tet"], out["inc_loc"] = take(np.int32, ninc), take(np.int8, ninc)
+    out["tdof"] = take(np.int32, nt * 6).reshape(nt, 6)
     assert pos == len(raw)
     return out
 
@@ -122,3 +134,21 @@ def test_host_assembly_matches_oracle(probe, idx, n):
     Qt = sp.csr_matrix((lib["qt_val"], (lib["qt_ci"], cols)), shape=(len(s.rx), N))
     assert abs(Qt - Ql).max() == 0.0
     assert np.array_equal(np.unique(lib["q_ci"]), qd)
+    # M(sigma) through the per-entry contribution lists (what the GPU sums)
+    idx = lib["mc_idx"].astype(np.int64)
+    contrib = s.sigma[idx // 36] * lib["Me1"][idx]
+    mvals = np.add.reduceat(contrib, lib["mc_ptr"][:-1]) if contrib.size else contrib
+    mvals[np.diff(lib["mc_ptr"]) == 0] = 0.0
+    Ml = sp.csr_matrix((mvals, lib["ci"], lib["rp"]), shape=(N, N))
+    Mo = fe.mass(s.sigma)
+    assert abs((P @ Ml @ P.T) - Mo).max() <= 1e-12 * abs(Mo).max()
+    # unknown -> (tet, local edge) incidence: exactly the tetrahedra that carry the unknown
+    tdof = lib["tdof"]
+    t_idx, a_idx = np.nonzero(tdof >= 0)
+    want = np.lexsort((a_idx, t_idx, tdof[t_idx, a_idx]))
+    want = np.stack([tdof[t_idx, a_idx][want], t_idx[want], a_idx[want]], axis=1)
+    dof_of = np.repeat(np.arange(N), np.diff(lib["inc_ptr"]))
+    inc_t, inc_a = lib["inc_tet"].astype(np.int64), lib["inc_loc"].astype(np.int64)
+    got = np.lexsort((inc_a, inc_t, dof_of))
+    got = np.stack([dof_of[got], inc_t[got], inc_a[got]], axis=1)
+    np.testing.assert_array_equal(got, want)
