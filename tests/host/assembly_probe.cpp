@@ -7,7 +7,9 @@
 //   int64 nqd, int32 qt_dof[nqd], int64 qt_rp[nqd+1], int32 qt_ci[nq], double qt_val[nq],
 //   then the M-value contributions (int64 mc_ptr[nnz+1], int64 nmc, uint32 mc_idx[nmc],
 //   double Me1[nt*36]) and the unknown -> (tet, local edge) incidence
-//   (int64 inc_ptr[N+1], int64 ninc, int32 inc_tet[ninc], int8 inc_loc[ninc], int32 tdof[nt*6]).
+//   (int64 inc_ptr[N+1], int64 ninc, int32 inc_tet[ninc], int8 inc_loc[ninc], int32 tdof[nt*6]),
+//   then the regulariser root W (int64 nf, P, int64 w_rp[nf+1], int32 w_ci[w_rp[nf]],
+//   double w_val[w_rp[nf]]) and the parameter index of every tet (int32 pidx[nt]).
 // Input (argv[1]): int64 nv, int64 nt, double xyz[nv*3], int32 tets[nt*4],
 // double sigma[nt], uint8 is_param[nt], int32 n_tx, int64 loop_ptr[n_tx+1],
 // int32 loop_verts[loop_ptr[n_tx]], int32 n_rx, double rx[n_rx*3].
@@ -88,6 +90,12 @@ int main(int argc, char **argv) {
   wr(o, m.inc_tet);
   wr(o, m.inc_loc);
   wr(o, m.tdof);
+  std::fwrite(&m.nf, 8, 1, o);
+  std::fwrite(&m.P, 8, 1, o);
+  wr(o, m.w_rp);
+  wr(o, m.w_ci);
+  wr(o, m.w_val);
+  wr(o, m.pidx);
   std::fclose(o);
   return 0;
 }

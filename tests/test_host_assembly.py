@@ -13,7 +13,9 @@ orient an edge from its lower to its higher vertex id).  Then:
 - M(sigma) summed through the library's per-entry contribution lists (what
   the GPU sums) must equal the oracle's mass matrix;
 - the unknown -> (tetrahedron, local edge) incidence must list exactly the
-  tetrahedra that carry each unknown.
+  tetrahedra that carry each unknown;
+- the regulariser root W must number the parameters like the oracle and give
+  the oracle's Laplacian W^T W (its rows may come in another face order).
 """
 import os
 import shutil
@@ -25,6 +27,7 @@ import pytest
 import scipy.sparse as sp
 
 from oracle.fem import FEModel
+from oracle.inversion import regulariser
 from oracle.survey import loop_source, observation_operator
 from paper_2605_19951_gb300 import inputs
 
@@ -93,6 +96,11 @@ def run_probe(probe, s):
     ninc = int(take(np.int64, 1)[0])
     out["inc_tet"], out["inc_loc"] = take(np.int32, ninc), take(np.int8, ninc)
     out["tdof"] = take(np.int32, nt * 6).reshape(nt, 6)
+    nf, P = (int(x) for x in take(np.int64, 2))
+    out["P"] = P
+    out["w_rp"] = take(np.int64, nf + 1)
+    out["w_ci"], out["w_val"] = take(np.int32, int(out["w_rp"][-1])), take(np.float64, int(out["w_rp"][-1]))
+    out["pidx"] = take(np.int32, nt)
     assert pos == len(raw)
     return out
 
@@ -152,3 +160,14 @@ def test_host_assembly_matches_oracle(probe, idx, n):
     got = np.lexsort((inc_a, inc_t, dof_of))
     got = np.stack([dof_of[got], inc_t[got], inc_a[got]], axis=1)
     np.testing.assert_array_equal(got, want)
+    # regulariser root W (faces x parameters): the same parameter numbering and the
+    # same Laplacian W^T W as the oracle's (rows may come in another face order)
+    param = np.asarray(s.is_param).astype(bool)
+    pid = -np.ones(len(param), np.int64)
+    pid[param] = np.arange(int(param.sum()))
+    np.testing.assert_array_equal(lib["pidx"], pid)
+    Wl = sp.csr_matrix((lib["w_val"], lib["w_ci"], lib["w_rp"]), shape=(len(lib["w_rp"]) - 1, lib["P"]))
+    Wo = regulariser(s.xyz, s.tets, s.is_param)
+    assert Wl.shape == Wo.shape
+    Ll, Lo = (Wl.T @ Wl).tocsr(), (Wo.T @ Wo).tocsr()
+    assert abs(Ll - Lo).max() <= 1e-12 * abs(Lo).max()
