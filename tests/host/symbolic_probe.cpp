@@ -8,7 +8,9 @@
 //   then int64 nnz_l (factor entries per pole), ltotal, utotal, the CSR of A in
 //   the elimination order (int64 rp[N+1], int64 nnz, int32 ci[nnz]) and the
 //   map of A's lower-triangle entries to factor positions (int64 no,
-//   int64 orig_nz[no], int64 orig_dst[no]).
+//   int64 orig_nz[no], int64 orig_dst[no]), then the levels (int64 nl; per
+//   level int64 nfront and int32 fronts[nfront], int64 ea_beg[2], ea_end[2]) and the
+//   extend-add tasks (int64 nea, int32 ea_child[nea], int32 ea_col[nea]).
 // Input (argv[1], native binary): int64 nv, int64 nt, int32 leaf_max,
 // double xyz[nv*3], int32 tets[nt*4], double sigma[nt], uint8 is_param[nt].
 #include <cstdio>
@@ -62,6 +64,18 @@ int main(int argc, char **argv) {
   std::fwrite(&no, 8, 1, o);
   std::fwrite(s.orig_nz.data(), 8, s.orig_nz.size(), o);
   std::fwrite(s.orig_dst.data(), 8, s.orig_dst.size(), o);
+  const int64_t nl = (int64_t)s.levels.size(), nea = (int64_t)s.ea_child.size();
+  std::fwrite(&nl, 8, 1, o);
+  for (const tem::Level &L : s.levels) {
+    const int64_t nfl = (int64_t)L.fronts.size();
+    std::fwrite(&nfl, 8, 1, o);
+    std::fwrite(L.fronts.data(), 4, L.fronts.size(), o);
+    std::fwrite(L.ea_beg, 8, 2, o);
+    std::fwrite(L.ea_end, 8, 2, o);
+  }
+  std::fwrite(&nea, 8, 1, o);
+  std::fwrite(s.ea_child.data(), 4, s.ea_child.size(), o);
+  std::fwrite(s.ea_col.data(), 4, s.ea_col.size(), o);
   std::fclose(o);
   return 0;
 }

@@ -11,8 +11,10 @@ Then every nonzero of L must lie inside its front (the front's later pivots
 and its update rows), the fronts must partition the unknowns and nest in
 their parents, each extend-add relative map must point at exactly the
 child's update rows inside the parent front, the memory plan must keep
-factor blocks disjoint and simultaneously alive update blocks disjoint, and
-every lower-triangle entry of A must go once to its factor position.
+factor blocks disjoint and simultaneously alive update blocks disjoint,
+every lower-triangle entry of A must go once to its factor position, and the
+extend-add tasks must cover every child update column once with no two
+children of one parent in the same (concurrently launched) child slot.
 """
 import os
 import shutil
@@ -77,8 +79,15 @@ def run_probe(probe, s, leaf):
     ci = take(np.int32, int(take(np.int64, 1)[0]))
     no = int(take(np.int64, 1)[0])
     onz, odst = take(np.int64, no), take(np.int64, no)
+    levels = []
+    for _ in range(int(take(np.int64, 1)[0])):
+        lf = take(np.int32, int(take(np.int64, 1)[0])).copy()
+        beg, end = take(np.int64, 2).copy(), take(np.int64, 2).copy()
+        levels.append((lf, beg, end))
+    nea = int(take(np.int64, 1)[0])
+    ea = (take(np.int32, nea).copy(), take(np.int32, nea).copy())
     assert pos == len(raw)
-    return N, tdof, fronts, nnz_l, (layout, ltotal, utotal), (rp, ci, onz, odst)
+    return N, tdof, fronts, nnz_l, (layout, ltotal, utotal), (rp, ci, onz, odst), (levels, ea)
 
 
 def symbolic_cholesky(N, tdof):
@@ -154,9 +163,33 @@ def check_original_entries(N, fronts, layout, rp, ci, onz, odst):
     assert np.unique(odst).size == odst.size
 
 
-def check_structure(N, tdof, fronts, nnz_l, plan, entries):
+def check_extend_add(fronts, layout, levels, ea):
+    """Level h lists the fronts of height h.  Its extend-add tasks (child front,
+    child update column) cover every update column of every child of those
+    fronts exactly once, and no two children of one parent fall into the same
+    child slot (the two slots run as separate launches, so the children's
+    scatter-adds into a parent never run concurrently)."""
+    ea_child, ea_col = ea
+    for h, (lf, beg, end) in enumerate(levels):
+        assert all(layout[f][0] == h for f in lf.tolist())
+        want = set()
+        for f in lf.tolist():
+            for c, fr in enumerate(fronts):
+                if fr[3] == f:
+                    want |= {(c, j) for j in range(fr[1] - fr[0])}
+        got = []
+        for sl in range(2):
+            kids = ea_child[beg[sl]:end[sl]].tolist()
+            got += list(zip(kids, ea_col[beg[sl]:end[sl]].tolist()))
+            parents = [fronts[c][3] for c in sorted(set(kids))]
+            assert len(parents) == len(set(parents)), (h, sl)
+        assert len(got) == len(set(got)) and set(got) == want
+
+
+def check_structure(N, tdof, fronts, nnz_l, plan, entries, ea):
     check_memory_plan(fronts, *plan)
     check_original_entries(N, fronts, plan[0], *entries)
+    check_extend_add(fronts, plan[0], *ea)
     # unknowns: tdof covers 0..N-1 (PEC edges are -1)
     used = np.unique(tdof[tdof >= 0])
     assert used.size == N and used[0] == 0 and used[-1] == N - 1
