@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline arm of ``bench.py`` may import or run anything in this package.
 It shares no code with the GPU library: it assembles its own Whitney-edge
 matrices, builds its own source vectors and observation operator, solves the
-shifted systems with a library sparse direct solver and forms the response
+shifted systems with its own plain up-looking sparse LDL^T (ldlt.c, under a
+coordinate-bisection ordering in sparse_ldlt.py) and forms the response
 and the Jacobian products straight from their definitions in the paper
 (Section 2.3 eq. for u(t_j); Section 3.1 for J and J^T).
 

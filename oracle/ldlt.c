@@ -9,6 +9,11 @@
  * No pivoting: for Re(xi) < 0 the real part K - Re(xi) M is positive definite,
  * so every leading principal submatrix is nonsingular.
  *
+ * Method: the up-looking sparse LDL^T of T. A. Davis, "Algorithm 849: A concise
+ * sparse Cholesky factorization package", ACM Trans. Math. Softw. 31(4), 2005
+ * (elimination tree, column counts, then a row-by-row numeric phase), restated
+ * here for complex symmetric matrices with transposes taken without conjugation.
+ *
  * The factorisation goes row by row.  Row k of L is found by a sparse
  * triangular solve L(0:k,0:k) D y = A(0:k,k), whose pattern is the set of
  * elimination-tree ancestors reachable from the nonzeros of A(0:k,k).

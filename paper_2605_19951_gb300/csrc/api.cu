@@ -1196,14 +1196,15 @@ extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *w
              kNoAllocDoubles);
     return fail(c, TEM_ERR_ARG, buf);
   }
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != c->device) return fail(c, TEM_ERR_STATE, "the context's device is not current");
+  ProfScope ps(c);
   double *base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     auto it = g_noalloc_addr.find(c->device);
     if (it == g_noalloc_addr.end()) {
-      int cur = -1;
-      CK(cudaGetDevice(&cur));
-      if (cur != c->device) return fail(c, TEM_ERR_STATE, "the context's device is not current");
       CK(cudaGetSymbolAddress((void **)&base, g_noalloc_scratch));
       g_noalloc_addr[c->device] = base;
     } else {

@@ -76,3 +76,55 @@ def test_gn_operator_adjoint():
     u = rng.standard_normal(wd.size + W.shape[0])
     a, b = u @ mv(v), v @ rmv(u)
     assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+
+
+def _share_face(tets):
+    """Pairs of tetrahedra that share three vertices (computed from the vertex
+    sets alone, independently of the regulariser's face matching)."""
+    sets = [set(int(v) for v in t) for t in tets]
+    return {(a, b) for a in range(len(sets)) for b in range(a + 1, len(sets)) if len(sets[a] & sets[b]) == 3}
+
+
+def test_regulariser_weights_one_cube():
+    """Hand-computed pin of the two-point RT0 weights (Section 3.2).  One cube
+    of side h cut into the six Kuhn tetrahedra: the interior faces are the six
+    triangles (v000, v_e, v111) through the main diagonal, each of area
+    |(1,0,0) x (1,1,1)| h^2 / 2 = h^2 / sqrt(2); the centroids of the two
+    tetrahedra on such a face, e.g. (3/4, 1/2, 1/4) h and (3/4, 1/4, 1/2) h,
+    are h sqrt(2) / 4 apart.  So every row of W is +-sqrt(|f| / d_f) =
+    +-sqrt(2 h), and W^T W is 2 h times the Laplacian of the six-cell ring."""
+    h = 3.0
+    xyz, tets = inputs.kuhn_box(1, h, 0)
+    W = regulariser(xyz, tets, np.ones(len(tets), dtype=np.uint8))
+    assert W.shape == (6, 6)
+    assert np.allclose(np.abs(W.data), np.sqrt(2.0 * h), rtol=1e-13)
+    ring = _share_face(tets)
+    assert len(ring) == 6
+    lap = np.zeros((6, 6))
+    for a, b in ring:
+        lap[a, a] += 1
+        lap[b, b] += 1
+        lap[a, b] = lap[b, a] = -1
+    assert np.allclose((W.T @ W).toarray(), 2.0 * h * lap, rtol=1e-13, atol=1e-13 * h)
+
+
+def test_regulariser_weights_two_cubes():
+    """Two unit cubes side by side along x (Kuhn cut, conforming on x = 1).
+    Inside each cube the six diagonal faces weigh sqrt(2) (the single-cube case
+    with h = 1).  On the shared square x = 1 the two triangles, e.g.
+    (1,0,0), (1,1,0), (1,1,1) of area 1/2, join the tetrahedra with centroids
+    (3/4, 1/2, 1/4) and (5/4, 3/4, 1/2), sqrt(6) / 4 apart, so they weigh
+    sqrt((1/2) / (sqrt(6) / 4)) = sqrt(2 / sqrt(6)).  Cells of the second cube
+    marked as air drop every face that touches them (Neumann)."""
+    xyz, tets = inputs.kuhn_grid([0.0, 1.0, 2.0], [0.0, 1.0], [0.0, 1.0])
+    W = regulariser(xyz, tets, np.ones(len(tets), dtype=np.uint8))
+    w = np.sort(np.abs(W.toarray()).max(axis=1))
+    expect = np.sort(np.r_[np.full(12, np.sqrt(2.0)), np.full(2, np.sqrt(2.0 / np.sqrt(6.0)))])
+    assert w.shape == expect.shape
+    assert np.allclose(w, expect, rtol=1e-13)
+    assert len(_share_face(tets)) == 14
+    half = np.zeros(len(tets), dtype=np.uint8)
+    half[:6] = 1                                     # cube 0 earth, cube 1 air
+    W0 = regulariser(xyz, tets, half)
+    assert W0.shape == (6, 6)
+    assert np.allclose(np.abs(W0.data), np.sqrt(2.0), rtol=1e-13)
