@@ -82,6 +82,8 @@ typedef struct tem_stats {
   int64_t solve_calls;   /* multi-pole solves issued so far (each with its refinement) */
   int32_t tc_ctas_per_sm; /* resident CTAs per SM of the tensor-core product kernel (0 before its first launch) */
   int32_t refine_steps_adjoint; /* refinement corrections per adjoint (J^T w) solve (FP32 mode) */
+  int64_t tc_prod_launches;   /* FP32 solve products run on the tensor cores, library-wide since load */
+  int64_t simt_prod_launches; /* FP32 solve products run on the FP32 pipes, library-wide since load */
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or

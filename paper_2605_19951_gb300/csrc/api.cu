@@ -135,6 +135,7 @@ struct tem_ctx {
 
   // sources
   int n_tx = 0, n_rx = 0, n_qdof = 0;
+  int nrhs = 0;   // right-hand sides per vector row: n_tx rounded up to even (TMA rows of 16 bytes)
   double *f = nullptr;
   int64_t *q_rp = nullptr, *qt_rp = nullptr;
   int32_t *q_ci = nullptr, *qt_ci = nullptr, *qt_dof = nullptr;
@@ -520,7 +521,7 @@ template <typename R>
 SolvePlan<R> solve_plan(tem_ctx *c) {
   SolvePlan<R> P;
   P.m = c->m;
-  P.nrhs = c->n_tx;
+  P.nrhs = c->nrhs;
   P.L = (const cx<R> *)c->L;
   P.lstride = c->sym.ltotal;
   P.Linv = (const cx<R> *)c->linv;
@@ -529,7 +530,7 @@ SolvePlan<R> solve_plan(tem_ctx *c) {
   P.rows = c->rows;
   P.Y = (cx<R> *)c->Y;
   P.X = (cx<R> *)c->X;
-  P.vstride = c->mesh.N * c->n_tx;
+  P.vstride = c->mesh.N * c->nrhs;
   P.dinv = (const cx<R> *)c->dinv;
   P.tmaps = c->tmaps;
   P.vmaps = c->vmaps;
@@ -557,7 +558,7 @@ void sweeps(tem_ctx *c, const int *pmap, int np) {
 // and later sweeps run over the remaining poles only (a host read per step).
 int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
   const int64_t N = c->mesh.N;
-  const int nx = c->n_tx, m = c->m;
+  const int nx = c->nrhs, m = c->m;
   cudaStream_t s = c->stream;
   c->solve_calls++;
   if (c->precision == TEM_FP64) {
@@ -620,7 +621,7 @@ int ensure_numeric(tem_ctx *c) {
   if (c->L) return TEM_OK;
   const size_t es = c->precision == TEM_FP64 ? sizeof(c128) : sizeof(c64);
   const int64_t N = c->mesh.N;
-  const int m = c->m, nx = c->n_tx;
+  const int m = c->m, nx = c->nrhs;
   void *p;
   TRY(dalloc(c, (char **)&p, size_t(m) * c->sym.ltotal * es));
   c->L = p;
@@ -843,8 +844,15 @@ int tem_sources(tem_ctx *c, int32_t n_tx, const int64_t *loop_ptr, const int32_t
                                   qt_rp, qt_ci, qt_val);
   if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
   c->n_tx = n_tx;
+  c->nrhs = n_tx + (n_tx & 1);
   c->n_rx = n_rx;
   c->n_qdof = (int)qt_dof.size();
+  if (c->nrhs != n_tx) {   // a zero right-hand side pads an odd transmitter count
+    std::vector<double> fp(size_t(c->mesh.N) * c->nrhs, 0.0);
+    for (int64_t i = 0; i < c->mesh.N; i++)
+      for (int x = 0; x < n_tx; x++) fp[size_t(i) * c->nrhs + x] = f[size_t(i) * n_tx + x];
+    f.swap(fp);
+  }
   TRY(upload(c, &c->f, f));
   TRY(upload(c, &c->q_rp, q_rp));
   TRY(upload(c, &c->q_ci, q_ci));
@@ -916,9 +924,9 @@ int tem_forward(tem_ctx *c, double *d) {
   ProfScope ps(c);
   cudaStream_t s = c->stream;
   const int64_t N = c->mesh.N;
-  launch_real_to_c128(c->f, c->fb, N * c->n_tx, s);
+  launch_real_to_c128(c->f, c->fb, N * c->nrhs, s);
   TRY(solve_all(c, c->fb, 0, c->g, c->refine));
-  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->g, d, c->m, N, c->n_tx, c->n_rx, c->K, s);
+  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->g, d, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K, s);
   CK(cudaMemcpyAsync(c->d_cur, d, sizeof(double) * c->n_tx * c->n_rx * c->K, cudaMemcpyDeviceToDevice, s));
   TRY(sync(c, "tem_forward"));
   TRY(check_solve_status(c));
@@ -931,26 +939,27 @@ int jvp_async(tem_ctx *c, const double *v, double *jv) {
   const int64_t N = c->mesh.N;
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   launch_dm_apply(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->pidx, v, c->sigma, c->me1, c->xi, c->g, c->b,
-                  c->m, N, c->n_tx, c->stream);
+                  c->m, N, c->nrhs, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
-  TRY(solve_all(c, c->b, N * c->n_tx, c->x, c->refine));
+  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine));
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->n_tx, c->n_rx, c->K, c->stream);
+  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K,
+                 c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   return TEM_OK;
 }
 int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
   const int64_t N = c->mesh.N;
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->n_tx,
+  launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->nrhs, c->n_tx,
                 c->n_rx, c->K, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   // the adjoint solves feed only the cell sums over parameter cells, which
   // converge in fewer corrections than the receivers' fields (46^3 box: within
   // 1e-7 of the converged J^T w after 6)
-  TRY(solve_all(c, c->b, N * c->n_tx, c->x, c->refine_adj));
+  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine_adj));
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->n_tx,
+  launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->nrhs,
                   c->precision != TEM_FP64, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   return TEM_OK;
@@ -1105,6 +1114,8 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   }
   o->n_solve_launch = nl;
   o->tc_ctas_per_sm = tc_ctas_per_sm();
+  o->tc_prod_launches = prod_launches(true);
+  o->simt_prod_launches = prod_launches(false);
   return TEM_OK;
 }
 

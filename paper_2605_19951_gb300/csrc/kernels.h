@@ -202,6 +202,8 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
 
 // Resident CTAs per SM of the tensor-core product kernel (0 before its first launch).
 int tc_ctas_per_sm();
+// FP32 solve-product launches on the tensor cores (true) or the FP32 pipes, library-wide.
+int64_t prod_launches(bool tensor_cores);
 // Tensor maps of every front's factor block (4 per front, index 4 f + mode)
 // in a new device array (*out, cudaFree by the caller); "" on success.
 struct FrontGeom {
@@ -274,14 +276,14 @@ void launch_progress_df(const c64 *X, const float *colmax, const float4 *x, cons
                         double *den, int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s);
 // F (real [N][nrhs]) -> c128 b
 void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s);
-// d[x][r][j] = 2 Re sum_p alpha_pj coef_p (Q y_p)[r][x]; coef = 1 (forward) or xi_p
+// d[x][r][j] = 2 Re sum_p alpha_pj (Q y_p)[r][x] for x < ntx (vector rows of nrhs >= ntx)
 void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_val,
                     const double2 *alpha, const c128 *y, double *d, int m, int64_t N, int nrhs,
-                    int n_rx, int K, cudaStream_t s);
-// rhs_p[dof][x] = sum_r Qt[dof][r] sum_j alpha_pj w[x][r][j] (zeroes rhs first)
+                    int ntx, int n_rx, int K, cudaStream_t s);
+// rhs_p[dof][x] = sum_r Qt[dof][r] sum_j alpha_pj w[x][r][j], x < ntx (zeroes rhs first)
 void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
                    const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,
-                   int m, int64_t N, int nrhs, int n_rx, int K, cudaStream_t s);
+                   int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s);
 // h_p[d][x] = xi_p sum_{(t,a) at d} v_t sigma_t sum_b M1_t[a][b] g_p[tdof_t[b]][x]
 void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc,
                      const int32_t *tdof, const int32_t *pidx, const double *v, const double *sigma,

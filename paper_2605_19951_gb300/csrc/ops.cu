@@ -194,14 +194,15 @@ void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s
 
 constexpr int kMaxPoles = 32;
 
-// d[x][r][j] = 2 Re sum_p alpha[p][j] (Q y_p)[r][x]
+// d[x][r][j] = 2 Re sum_p alpha[p][j] (Q y_p)[r][x] for the ntx transmitters
+// (y rows hold nrhs >= ntx right-hand sides; the rest are padding)
 __global__ void k_residue(const int64_t *__restrict__ q_rp, const int32_t *__restrict__ q_ci,
                           const double *__restrict__ q_val, const double2 *__restrict__ alpha,
                           const c128 *__restrict__ y, double *__restrict__ d, int m, int64_t N,
-                          int nrhs, int n_rx, int K) {
+                          int nrhs, int ntx, int n_rx, int K) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= int64_t(n_rx) * nrhs) return;
-  const int x = int(t % nrhs), r = int(t / nrhs);
+  if (t >= int64_t(n_rx) * ntx) return;
+  const int x = int(t % ntx), r = int(t / ntx);
   c128 yq[kMaxPoles];
   for (int p = 0; p < m; p++) {
     c128 acc = mk<double>(0.0, 0.0);
@@ -225,21 +226,22 @@ __global__ void k_residue(const int64_t *__restrict__ q_rp, const int32_t *__res
 
 void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_val,
                     const double2 *alpha, const c128 *y, double *d, int m, int64_t N, int nrhs,
-                    int n_rx, int K, cudaStream_t s) {
-  const int64_t cnt = int64_t(n_rx) * nrhs;
+                    int ntx, int n_rx, int K, cudaStream_t s) {
+  const int64_t cnt = int64_t(n_rx) * ntx;
   tem::count_launch();
-  k_residue<<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, n_rx, K);
+  k_residue<<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, ntx, n_rx, K);
 }
 
-// rhs_p[qdof][x] = sum_{r} Qt[qdof][r] * sum_j alpha[p][j] w[x][r][j]
+// rhs_p[qdof][x] = sum_{r} Qt[qdof][r] * sum_j alpha[p][j] w[x][r][j], x < ntx
+// (the padding right-hand sides x >= ntx stay zero)
 __global__ void k_qt_rhs(const int32_t *__restrict__ qt_dof, const int64_t *__restrict__ qt_rp,
                          const int32_t *__restrict__ qt_ci, const double *__restrict__ qt_val,
                          int n_qdof, const double2 *__restrict__ alpha, const double *__restrict__ w,
-                         c128 *__restrict__ rhs, int64_t N, int nrhs, int n_rx, int K) {
+                         c128 *__restrict__ rhs, int64_t N, int nrhs, int ntx, int n_rx, int K) {
   const int p = blockIdx.y;
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t >= int64_t(n_qdof) * nrhs) return;
-  const int x = int(t % nrhs), q = int(t / nrhs);
+  if (t >= int64_t(n_qdof) * ntx) return;
+  const int x = int(t % ntx), q = int(t / ntx);
   c128 acc = mk<double>(0.0, 0.0);
   for (int64_t z = qt_rp[q]; z < qt_rp[q + 1]; z++) {
     const int r = qt_ci[z];
@@ -258,13 +260,13 @@ __global__ void k_qt_rhs(const int32_t *__restrict__ qt_dof, const int64_t *__re
 
 void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
                    const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,
-                   int m, int64_t N, int nrhs, int n_rx, int K, cudaStream_t s) {
+                   int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s) {
   cudaMemsetAsync(rhs, 0, sizeof(c128) * m * N * nrhs, s);
-  const int64_t cnt = int64_t(n_qdof) * nrhs;
+  const int64_t cnt = int64_t(n_qdof) * ntx;
   if (cnt == 0) return;
   dim3 g(div_up(cnt, 128), m);
   tem::count_launch();
-  k_qt_rhs<<<g, 128, 0, s>>>(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, N, nrhs, n_rx, K);
+  k_qt_rhs<<<g, 128, 0, s>>>(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, N, nrhs, ntx, n_rx, K);
 }
 
 // ---- mass-derivative products ------------------------------------------------

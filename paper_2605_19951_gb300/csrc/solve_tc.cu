@@ -27,6 +27,7 @@
 // outstanding MMAs, in-flight loads land and the TMEM is released.
 //
 // The SIMT kernel (k_prod_simt) computes the same products on the FP32 pipes.
+#include <atomic>
 #include <cstring>
 #include <cuda.h>   // CUtensorMap and the encoder's signature (called through the runtime's entry point)
 
@@ -536,6 +537,7 @@ __global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtT
 
 namespace {
 int g_tc_occupancy = 0;
+std::atomic<int64_t> g_tc_launches{0}, g_simt_launches{0};
 
 template <int MODE>
 void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t s) {
@@ -559,16 +561,19 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
     const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
     const int grid = int(total < grid_max ? total : grid_max);
     tem::count_launch();
+    g_tc_launches.fetch_add(1, std::memory_order_relaxed);
     k_tc_kint<MODE><<<grid, NTHR, kKiSmem, s>>>(a);
   } else {
     dim3 g(a.ntask_simt, a.np * a.nchunk);
     tem::count_launch();
+    g_simt_launches.fetch_add(1, std::memory_order_relaxed);
     k_prod_simt<MODE><<<g, 256, 0, s>>>(a, simt);
   }
 }
 }  // namespace
 
 int tc_ctas_per_sm() { return g_tc_occupancy; }
+int64_t prod_launches(bool tensor_cores) { return (tensor_cores ? g_tc_launches : g_simt_launches).load(); }
 
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
   // The tensor-core kernel loads B rows by TMA, which needs 16-byte rows (an

@@ -59,7 +59,8 @@ class TemStats(ctypes.Structure):
                 ("m", _I32), ("n_times", _I32), ("n_tx", _I32), ("n_rx", _I32),
                 ("precision", _I32), ("refine_steps", _I32), ("last_pivot_front", _I32),
                 ("min_pivot_abs", _D), ("nnz_l11", _I64), ("n_solve_launch", _I64),
-                ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("refine_steps_adjoint", _I32)]
+                ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("refine_steps_adjoint", _I32),
+                ("tc_prod_launches", _I64), ("simt_prod_launches", _I64)]
 
 
 class TemError(RuntimeError):

@@ -79,11 +79,29 @@ def c2():
     return Case(2, 202)
 
 
+def _prod_launches(mdl):
+    info = mdl.info()
+    return info["tc_prod_launches"], info["simt_prod_launches"]
+
+
+def _assert_product_path(mdl, before, prec, tensor_cores):
+    """The FP32 solves ran their front products on the kernel asked for:
+    k_tc_kint (tcgen05) with tensor cores on, k_prod_simt otherwise."""
+    tc, simt = _prod_launches(mdl)
+    if prec == "fp64":
+        return
+    if tensor_cores:
+        assert tc > before[0] and simt == before[1], (before, tc, simt)
+    else:
+        assert simt > before[1] and tc == before[0], (before, tc, simt)
+
+
 def _check_case(case, prec, leaf=0, tensor_cores=True):
     mdl = _model(case.s, case.xi, case.al, prec, leaf)
     try:
         if not tensor_cores:
             _tem().tem_set_tensor_cores(mdl.ctx, 0)
+        before = _prod_launches(mdl)
         mdl.factor(_cuda(case.m0))
         d = mdl.forward().cpu().numpy()
         assert floored_err(d, case.d).max() <= TOL[prec]
@@ -93,6 +111,7 @@ def _check_case(case, prec, leaf=0, tensor_cores=True):
         assert np.linalg.norm(jtw - case.jtw) <= TOL[prec] * np.linalg.norm(case.jtw)
         info = mdl.info()
         assert info["last_pivot_front"] == -1 and info["min_pivot_abs"] > 0
+        _assert_product_path(mdl, before, prec, tensor_cores)
     finally:
         mdl.close()
 
@@ -102,12 +121,14 @@ def test_c1(c1, prec):
     _check_case(c1, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
+@pytest.mark.parametrize("prec,tensor_cores", [("fp64", False), ("fp32r", True), ("fp32r", False)])
 @pytest.mark.parametrize("leaf", [8, 33, 300])
-def test_c1_leaf_sizes(c1, leaf, prec):
+def test_c1_leaf_sizes(c1, leaf, prec, tensor_cores):
     """Different dissection leaves give ragged fronts (k not a multiple of
-    the 32-wide pivot block or the 64-row product tiles, single-front trees)."""
-    _check_case(c1, prec, leaf)
+    the 32-wide pivot block or the 64-row product tiles, single-front trees),
+    on the tensor-core products and on the FP32-pipe products.  C1 has one
+    transmitter: the solves carry it with a zero right-hand side as padding."""
+    _check_case(c1, prec, leaf, tensor_cores)
 
 
 def test_c1_fp32_simt_products(c1):
@@ -166,27 +187,38 @@ def test_adjoint_gpu(c1):
         mdl.close()
 
 
-def test_many_transmitters():
-    """More than 32 right-hand sides (two RHS chunks of the solve kernels)."""
+@pytest.mark.parametrize("n_tx", [37, 70])
+def test_many_transmitters(n_tx):
+    """More than 32 right-hand sides: 37 (odd, padded to 38: two RHS chunks,
+    the second ragged) and 70 (three chunks), on both product kernels."""
     s = inputs.make_config(1)
     n, na = s.n, s.n_air
-    loops = [inputs.square_loop(n, na, 1 + (i % 5), 1 + (i // 5) % 5, 1 + i % 2) for i in range(37)]
+    squares = [(i0, j0, side) for side in (1, 2, 3, 4) for i0 in range(1, n - side) for j0 in range(1, n - side)]
+    pick = np.random.default_rng(n_tx).permutation(len(squares))[:n_tx]   # distinct squares off the PEC walls
+    loops = [inputs.square_loop(n, na, *squares[q]) for q in pick]
     s.loops = loops
     xi, al = inputs.load_rational(8, s.times)
-    rng = np.random.default_rng(37)
-    m0 = s.log_sigma()
+    rng = np.random.default_rng(n_tx)
+    m0 = s.log_sigma() + 0.1 * rng.standard_normal(s.n_param)
     o = Oracle(s.xyz, s.tets, s.sigma, s.is_param, loops, s.rx, xi, al)
     o.set_model(m0)
-    w = rng.standard_normal((37, 1, len(s.times)))
-    ref_d, ref_jtw = o.forward(), o.jtvp(w)
-    for prec in ("fp64", "fp32r"):
+    v = rng.standard_normal(s.n_param)
+    w = rng.standard_normal((n_tx, 1, len(s.times)))
+    ref_d, ref_jv, ref_jtw = o.forward(), o.jvp(v), o.jtvp(w)
+    for prec, tc in (("fp64", False), ("fp32r", True), ("fp32r", False)):
         mdl = _model(s, xi, al, prec)
         try:
+            if not tc:
+                _tem().tem_set_tensor_cores(mdl.ctx, 0)
+            before = _prod_launches(mdl)
             mdl.factor(_cuda(m0))
             d = mdl.forward().cpu().numpy()
             assert floored_err(d, ref_d).max() <= TOL[prec]
+            jv = mdl.jvp(_cuda(v)).cpu().numpy()
+            assert floored_err(jv, ref_jv).max() <= TOL_JV[prec]
             jtw = mdl.jtvp(_cuda(w)).cpu().numpy()
             assert np.linalg.norm(jtw - ref_jtw) <= TOL[prec] * np.linalg.norm(ref_jtw)
+            _assert_product_path(mdl, before, prec, tc)
         finally:
             mdl.close()
 
