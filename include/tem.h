@@ -84,6 +84,10 @@ typedef struct tem_stats {
   int32_t refine_steps_adjoint; /* refinement corrections per adjoint (J^T w) solve (FP32 mode) */
   int64_t tc_prod_launches;   /* FP32 solve products run on the tensor cores, library-wide since load */
   int64_t simt_prod_launches; /* FP32 solve products run on the FP32 pipes, library-wide since load */
+  int64_t n_nodes;       /* FP32 mode: interior vertices (gradient-space unknowns) */
+  int64_t nnz_l_nodal;   /* FP32 mode: stored factor entries of the nodal Laplacian */
+  int32_t nodal;         /* FP32 mode: 1 = gradient-space correction on */
+  int32_t reserved0;
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or
@@ -178,8 +182,8 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
                      const double *m_ref, double lambda, int32_t n_iter, double *dm);
 
 /* TEM_FP32_REFINED mode: refinement corrections per forward and J v solve
- * (default 16) and the conductivity floor of the factored matrices (default
- * 1e-4).
+ * (default 3) and the conductivity floor of the factored matrices (default
+ * 1e-6).
  *
  * The complex-float factor is of P_i = K - xi_i M(s_i) with the cell
  * conductivity raised to s_i,t = max(sigma_t, floor_tau / (|xi_i| mu0 h_t^2)),
@@ -187,11 +191,11 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
  * b - (K - xi_i M(sigma)) x is formed with the true matrix in double-float
  * pairs (compensated products on the FP32 pipes).  Without
  * the floor the gradient fields of resistive cells (air, 1e-8 S/m) have pivots
- * below float resolution and the refinement diverges.  Gradients of nodes
- * whose cells are all floored are eigenvectors of P_i^-1 A_i, every
- * right-hand side of the path is orthogonal to them and no output reads
- * them, so the refined data converge to those of A_i.  The FP64 mode factors
- * A_i itself.  With tol > 0 a pole stops refining once its last correction,
+ * below float resolution and the refinement diverges.  P_i^-1 A_i is then
+ * ~sigma / s on the gradients of the floored cells: the gradient-space
+ * correction (tem_set_nodal) removes those error components every step,
+ * which lets the floor go down to 1e-6, where the remaining modes contract
+ * by ~1e-3 per step.  The FP64 mode factors A_i itself.  With tol > 0 a pole stops refining once its last correction,
  * over the unknowns every output reads (edges of parameter cells), is below
  * tol times the solution there; the remaining sweeps run over the poles still
  * refining (one host read per step).  steps in 0..40 (the maximum),
@@ -199,10 +203,10 @@ int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
 int tem_set_refine(tem_ctx *ctx, int32_t steps, double floor_tau, double tol);
 
 /* TEM_FP32_REFINED mode: refinement corrections per adjoint solve, the
- * solves of tem_jtvp (and of tem_lsqr's J^T w), default 6.  Their output is
- * the cell sums over parameter cells, which converge in fewer corrections
- * than the receivers' fields of tem_forward and tem_jvp.  steps in 0..40;
- * TEM_ERR_ARG otherwise. */
+ * solves of tem_jtvp (and of tem_lsqr's J^T w), default 1.  Their output is
+ * the cell sums over parameter cells (formed in double-float pairs), which
+ * converge in fewer corrections than the receivers' fields of tem_forward
+ * and tem_jvp.  steps in 0..40; TEM_ERR_ARG otherwise. */
 int tem_set_refine_adjoint(tem_ctx *ctx, int32_t steps);
 
 /* TEM_FP32_REFINED mode: run the update-row products of the solves on the
@@ -212,6 +216,18 @@ int tem_set_refine_adjoint(tem_ctx *ctx, int32_t steps);
  * TEM_ERR_TIMEOUT.  No effect in TEM_FP64 mode. */
 int tem_set_tensor_cores(tem_ctx *ctx, int enable);
 
+/* TEM_FP32_REFINED mode: the gradient-space correction of every refinement
+ * step (default 1).  The floored factor P_i leaves the gradient fields of the
+ * floored cells almost uncorrected (P_i^-1 A_i ~ sigma / s ~ 0 there), so each
+ * step also solves the residual equation on the discrete gradients G psi of
+ * the interior vertices.  With K G = 0 (Section 2.2, curl grad = 0),
+ * G^T A_i G = -xi_i G^T M(sigma) G: one real sigma-weighted nodal Laplacian
+ * L = G^T M G for every pole, factored with A_i in tem_factor, and per step
+ * psi = L^-1 G^T r, x += -G psi / xi_i, r -= M G psi, before the correction
+ * with P_i.  Switching it on after tem_factor without it requires a new
+ * tem_factor (TEM_ERR_STATE until then).  No effect in TEM_FP64 mode. */
+int tem_set_nodal(tem_ctx *ctx, int enable);
+
 /* Time one class of kernels with CUDA events on the context's stream:
  * 0 trailing update, 1 panel, 2 forward pivot-block step, 3 backward
  * pivot-block step, 4 backward update-row product (L21^T), 5 extend-add,
@@ -219,7 +235,10 @@ int tem_set_tensor_cores(tem_ctx *ctx, int enable);
  * 8 backward super-block product, 9 pivot-block inversion, 10 refinement
  * residual, 11 refinement vector kernels (split, scaling, accumulation, join),
  * 12 Jacobian kernels (J v right-hand sides, J^T w right-hand sides, residue
- * sums, cell sums); -1 switches timing off (the default).
+ * sums, cell sums), 13 gradient-space correction (G^T r, nodal sweeps,
+ * M G psi; its sweeps count in no other class), and its parts: 14 G^T r and
+ * scaling, 15 nodal sweeps, 16 M G psi and x update; -1 switches timing off
+ * (the default).
  * class + 64 (h + 1) times only the launches of assembly-tree level h.
  * Timing adds an event pair around each launch of that class. */
 int tem_set_profiling(tem_ctx *ctx, int kernel_class);
@@ -239,6 +258,12 @@ int tem_info(tem_ctx *ctx, tem_stats *out);
  * Pass NULL pointers to query nnz first (returned in *nnz). */
 int tem_export_pattern(tem_ctx *ctx, int64_t *nnz, int64_t *row_ptr,
                        int32_t *col, double *k_val, double *m_val);
+
+/* Host copy of the forward solutions g_i = A_i^-1 f_x of the last tem_forward
+ * (Algorithm 1, solve), for inspection and tests: g host [m][N][n_tx][2]
+ * (re, im) FP64, unknowns in the library's numbering (tem_export_dofs).
+ * TEM_ERR_STATE before tem_forward. */
+int tem_export_forward(tem_ctx *ctx, double *g);
 
 /* Permutation: perm[new] = interior-edge index in the library's own edge
  * numbering, and the edge's two vertex ids (lower first), host arrays of

@@ -27,7 +27,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_total() { return g_launches.load(); }
 
 void Profiler::begin(int c, cudaStream_t s) {
-  if (!on || c != cls || (level >= 0 && cur_level != level)) return;
+  if (!on || muted || c != cls || (level >= 0 && cur_level != level)) return;
   if (used + 2 > (int)pool.size()) {
     size_t old = pool.size();
     pool.resize(std::max<size_t>(64, 2 * old + 2));
@@ -36,7 +36,7 @@ void Profiler::begin(int c, cudaStream_t s) {
   cudaEventRecord(pool[used], s);
 }
 void Profiler::end(int c, cudaStream_t s) {
-  if (!on || c != cls || (level >= 0 && cur_level != level)) return;
+  if (!on || muted || c != cls || (level >= 0 && cur_level != level)) return;
   cudaEventRecord(pool[used + 1], s);
   used += 2;
 }
@@ -68,27 +68,14 @@ struct DVec {
 
 }  // namespace
 
-struct tem_ctx {
-  int precision = TEM_FP64;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  std::string err;
-  int state = 0;
-  int refine = 16;
-  int refine_adj = 6;        // FP32 mode: corrections per adjoint (J^T w) solve
-  double floor_tau = 1e-4;   // FP32 mode: conductivity floor of the factored matrix
-  double refine_tol = 0.0;   // FP32 mode: stop a pole's refinement below this progress (0: fixed count)
-  int64_t pole_solves = 0;   // statistics: poles x sweeps pairs issued
-  int64_t solve_calls = 0;
-  uint8_t *earth = nullptr;  // unknowns on edges of parameter cells (what every output reads)
-  int *pmap = nullptr;       // device list of the poles still refining
-  double *prog = nullptr;    // [2m] progress maxima
-  int64_t bytes = 0;
-  std::vector<void *> allocs;
-  Profiler prof;
-
-  Mesh mesh;
+// One family of sparse complex-symmetric matrices A_p = K - xi_p M_p (p < m)
+// sharing a pattern: its assembly tree, the task lists of the factor and
+// solve kernels, the factor store and the solve vectors.
+struct FactorSys {
   Symbolic sym;
+  int64_t N = 0;                          // unknowns
+  int m = 0;                              // matrices factored together (pole dimension)
+  int nrhs = 0;                           // right-hand sides per vector row (even)
   std::vector<LevelDev> levels;
   int max_level_fronts = 0;
   int64_t inv_blocks = 0;                 // diagonal-block inverses per pole
@@ -113,20 +100,75 @@ struct tem_ctx {
   std::vector<int2> invdiag_h;
   int2 *invdiag = nullptr;
   int64_t yscr_stride = 0;                // inversion scratch per pole
+  // device symbolic tables
+  FrontDev *fronts = nullptr;
+  int32_t *rows = nullptr, *rel = nullptr, *ea_child = nullptr, *ea_col = nullptr, *levfronts = nullptr;
+  int64_t *orig_nz = nullptr, *orig_dst = nullptr;
+  // numeric
+  void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr, *linv = nullptr;
+  void *dinv = nullptr, *yscr = nullptr;   // FP32: inverse pivots, inversion scratch
+  // matrix values: A_p = K - xi_p M_p, M_p = mval + p * mstride
+  const double *kval = nullptr;
+  const double *mval = nullptr;
+  int64_t mstride = 0;
+  const double2 *xi = nullptr;
+};
+
+struct tem_ctx {
+  int precision = TEM_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  int state = 0;
+  int refine = 3;
+  int refine_adj = 1;        // FP32 mode: corrections per adjoint (J^T w) solve
+  double floor_tau = 1e-6;   // FP32 mode: conductivity floor of the factored matrix
+  double refine_tol = 0.0;   // FP32 mode: stop a pole's refinement below this progress (0: fixed count)
+  int64_t pole_solves = 0;   // statistics: poles x sweeps pairs issued
+  int64_t solve_calls = 0;
+  uint8_t *earth = nullptr;  // unknowns on edges of parameter cells (what every output reads)
+  int *pmap = nullptr;       // device list of the poles still refining
+  double *prog = nullptr;    // [2m] progress maxima
+  int64_t bytes = 0;
+  std::vector<void *> allocs;
+  Profiler prof;
+
+  Mesh mesh;
+  FactorSys es;                           // the shifted edge systems A_i = K - xi_i M (all poles)
+  FactorSys ns;                           // FP32 mode: the nodal gradient-space Laplacian (one matrix)
+  NodalMesh nodal;
   bool use_tc = true;                     // FP32 mode: front products on tcgen05
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
   double *tetfloor = nullptr, *mval_fact = nullptr;   // FP32 mode: per-pole floored M values
-  int64_t *rp = nullptr, *mc_ptr = nullptr, *inc_ptr = nullptr, *orig_nz = nullptr, *orig_dst = nullptr;
+  int64_t *rp = nullptr, *mc_ptr = nullptr, *inc_ptr = nullptr;
   int32_t *ci = nullptr, *inc_tet = nullptr, *tdof = nullptr, *pidx = nullptr, *ptet = nullptr;
   uint32_t *mc_idx = nullptr;
   int8_t *inc_loc = nullptr;
-  FrontDev *fronts = nullptr;
-  int32_t *rows = nullptr, *rel = nullptr, *ea_child = nullptr, *ea_col = nullptr, *levfronts = nullptr;
   int64_t *w_rp = nullptr, *wt_rp = nullptr;
   int32_t *w_ci = nullptr, *wt_ci = nullptr;
   double *w_val = nullptr, *wt_val = nullptr;
+
+  // FP32 mode: nodal gradient-space correction of the refinement
+  bool use_nodal = true;
+  int32_t *n_tnode = nullptr, *n_elo = nullptr, *n_ehi = nullptr, *n_gedge = nullptr;
+  int64_t *n_mc_ptr = nullptr, *n_gptr = nullptr;
+  uint32_t *n_mc_idx = nullptr;
+  int8_t *n_gsign = nullptr;
+  double *n_stiff = nullptr, *n_kval = nullptr, *n_mval = nullptr;
+  int64_t *n_crp = nullptr, *n_cmc_ptr = nullptr;   // C = M(sigma) G: rows and contribution lists
+  int32_t *n_cci = nullptr;
+  uint32_t *n_cmc_idx = nullptr;
+  double *n_btab = nullptr;
+  float *n_cval = nullptr;                          // C values (FP32: they only feed the FP32 correction)
+  float2 *ninv_xi = nullptr;                        // -1 / xi_p
+  double2 *n_xi = nullptr;
+  float *colmax_n = nullptr;   // column scales of the nodal solves
+  double *part = nullptr;      // [m][P] per-pole J^T w cell sums (FP32 mode)
+  float2 *me1df = nullptr;     // FP32 mode: M1 element matrices as pairs [nt][36]
+  float4 *gdf = nullptr;       // FP32 mode: forward solutions as pairs [m][N][nrhs]
+  float2 *vsdf = nullptr;      // FP32 mode: v_t sigma_t as pairs [nt] (J v right-hand sides)
 
   // poles
   int m = 0, K = 0;
@@ -142,8 +184,6 @@ struct tem_ctx {
   double *q_val = nullptr, *qt_val = nullptr;
 
   // numeric
-  void *L = nullptr, *U = nullptr, *dscr = nullptr, *Y = nullptr, *X = nullptr, *linv = nullptr;
-  void *dinv = nullptr, *yscr = nullptr;   // FP32: inverse pivots, inversion scratch
   float2 *kdf = nullptr, *mdf = nullptr;   // FP32: K and M values as double-float pairs
   float4 *xdf = nullptr;                   // FP32: refined iterate as pairs [m][N][nrhs]
   float *colmax_f = nullptr;               // FP32: column scales of the correction solves
@@ -238,10 +278,10 @@ struct ProfScope {
 // / 64-column tiles; kernels.h gives each mode's operands) and the merge
 // stages of the pivot-block inversion.  List offsets are stored in the
 // LevelDev pointers until the lists are uploaded.
-void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
-  const auto &S = c->sym;
+void build_fp32_tasks(FactorSys &S_, const Level &L, LevelDev &lv) {
+  const auto &S = S_.sym;
   for (int mode = 0; mode < PM_COUNT; mode++) {
-    const size_t beg = c->prod_h.size(), beg_s = c->prod_simt_h.size();
+    const size_t beg = S_.prod_h.size(), beg_s = S_.prod_simt_h.size();
     for (int32_t fi : L.fronts) {
       const Front &F = S.fronts[fi];
       const int k = F.k, b = F.n - F.k;
@@ -261,7 +301,7 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
           t.obase = obase;
           t.mfirst = int16_t(mfirst);
           t.kfirst = int16_t(kfirst);
-          c->prod_h.push_back(t);
+          S_.prod_h.push_back(t);
         }
         if (simt) {
           SimtTask u;
@@ -273,7 +313,7 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
           u.obase = obase;
           u.mfirst = int16_t(mfirst);
           u.kfirst = int16_t(kfirst);
-          c->prod_simt_h.push_back(u);
+          S_.prod_simt_h.push_back(u);
         }
       };
       const int r0 = k & ~1;   // even origin of the update rows (row k - 1 is padding when k is odd)
@@ -283,7 +323,7 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
         // tensor cores: 128 rows of the row-major T11 copy (run origin x = 0, row origin y = i0)
         for (int i0 = 0; i0 < k; i0 += 128) {
           push(true, false, 0, 0, std::min(k, i0 + 128), std::min(128, k - i0), F.c0, F.c0 + i0, 0, 0);
-          c->prod_h.back().y0 = i0;
+          S_.prod_h.back().y0 = i0;
         }
       } else if (mode == PM_FWD21) {
         if (b > 0) {
@@ -292,7 +332,7 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
           // tensor cores: 128 rows of the row-major L21 copy
           for (int i0 = 0; i0 < b; i0 += 128) {
             push(true, false, 0, 0, k, std::min(128, b - i0), F.c0, (int)F.rows_off + i0, 0, 0);
-            c->prod_h.back().y0 = i0;
+            S_.prod_h.back().y0 = i0;
           }
         }
       } else if (mode == PM_BWD21) {
@@ -311,40 +351,40 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
           push(true, false, cb, cb, k - cb, std::min(128, k - cb), F.c0 + cb, F.c0 + cb, 0, 0);
       }
     }
-    lv.n_prod[mode] = int(c->prod_h.size() - beg);
-    lv.n_prod_simt[mode] = int(c->prod_simt_h.size() - beg_s);
+    lv.n_prod[mode] = int(S_.prod_h.size() - beg);
+    lv.n_prod_simt[mode] = int(S_.prod_simt_h.size() - beg_s);
     // tensor-core tasks, longest inner dimension first (the kernel deals them out in this order)
-    std::stable_sort(c->prod_h.begin() + beg, c->prod_h.end(),
+    std::stable_sort(S_.prod_h.begin() + beg, S_.prod_h.end(),
                      [](const TcTask &x, const TcTask &y) { return x.kdim > y.kdim; });
     lv.prod[mode] = (const TcTask *)(uintptr_t)beg;
     lv.prod_simt[mode] = (const SimtTask *)(uintptr_t)beg_s;
   }
   // row-major copies of T11 and L21 (after the level's inversion)
   {
-    const size_t beg = c->rcopy_h.size();
+    const size_t beg = S_.rcopy_h.size();
     for (int32_t fi : L.fronts) {
       const Front &F = S.fronts[fi];
       if (F.k <= 0) continue;
-      for (int rb = 0; rb * 32 < F.k; rb++) c->rcopy_h.push_back(make_int4(fi, 0, rb, 0));
-      for (int rb = 0; rb * 32 < F.n - F.k; rb++) c->rcopy_h.push_back(make_int4(fi, 1, rb, 0));
+      for (int rb = 0; rb * 32 < F.k; rb++) S_.rcopy_h.push_back(make_int4(fi, 0, rb, 0));
+      for (int rb = 0; rb * 32 < F.n - F.k; rb++) S_.rcopy_h.push_back(make_int4(fi, 1, rb, 0));
     }
-    lv.n_rcopy = int(c->rcopy_h.size() - beg);
+    lv.n_rcopy = int(S_.rcopy_h.size() - beg);
     lv.rcopy = (const int4 *)(uintptr_t)beg;
   }
   // inversion: 32-blocks, then pairwise merges of blocks of 32 * 2^stage
-  const size_t dbeg = c->invdiag_h.size();
+  const size_t dbeg = S_.invdiag_h.size();
   int kmax = 0;
   for (int32_t fi : L.fronts) {
     const Front &F = S.fronts[fi];
     kmax = std::max(kmax, F.k);
-    for (int J = 0; J * kNB < F.k; J++) c->invdiag_h.push_back(make_int2(fi, J));
+    for (int J = 0; J * kNB < F.k; J++) S_.invdiag_h.push_back(make_int2(fi, J));
   }
-  lv.n_inv_diag = int(c->invdiag_h.size() - dbeg);
+  lv.n_inv_diag = int(S_.invdiag_h.size() - dbeg);
   lv.inv_diag = (const int2 *)(uintptr_t)dbeg;
   lv.inv.clear();
   for (int sz = kNB; sz < kmax; sz *= 2) {
     LevelDev::InvStage st;
-    const size_t beg = c->inv_h.size();
+    const size_t beg = S_.inv_h.size();
     int64_t ybase = 0;
     for (int32_t fi : L.fronts) {
       const Front &F = S.fronts[fi];
@@ -360,52 +400,52 @@ void build_fp32_tasks(tem_ctx *c, const Level &L, LevelDev &lv) {
             t.ti = ti;
             t.tj = tj;
             t.ybase = ybase;
-            c->inv_h.push_back(t);
+            S_.inv_h.push_back(t);
           }
         ybase += int64_t(sc) * sz;
       }
     }
-    st.n = int(c->inv_h.size() - beg);
+    st.n = int(S_.inv_h.size() - beg);
     st.tasks = (const InvTask *)(uintptr_t)beg;
-    c->yscr_stride = std::max(c->yscr_stride, ybase);
+    S_.yscr_stride = std::max(S_.yscr_stride, ybase);
     lv.inv.push_back(st);
   }
 }
 
 // Grid dimensions of every pivot step (depend on the precision's tile sizes).
 template <typename R>
-void build_steps(tem_ctx *c) {
-  const auto &S = c->sym;
-  c->levels.clear();
-  c->f21_h.clear();
-  c->b21_h.clear();
-  c->sbf_h.clear();
-  c->sbb_h.clear();
-  c->prod_h.clear();
-  c->prod_simt_h.clear();
-  c->rcopy_h.clear();
+void build_steps(FactorSys &S_) {
+  const auto &S = S_.sym;
+  S_.levels.clear();
+  S_.f21_h.clear();
+  S_.b21_h.clear();
+  S_.sbf_h.clear();
+  S_.sbb_h.clear();
+  S_.prod_h.clear();
+  S_.prod_simt_h.clear();
+  S_.rcopy_h.clear();
   // row-major copy layout: per front k x ld2 (T11) and b x ld2 (L21), ld2 = k rounded up to even
-  c->t11r_ofs_h.assign(S.fronts.size(), 0);
-  c->l21t_ofs_h.assign(S.fronts.size(), 0);
-  c->t11r_total = c->l21t_total = 0;
+  S_.t11r_ofs_h.assign(S.fronts.size(), 0);
+  S_.l21t_ofs_h.assign(S.fronts.size(), 0);
+  S_.t11r_total = S_.l21t_total = 0;
   for (size_t f = 0; f < S.fronts.size(); f++) {
     const Front &F = S.fronts[f];
     const int64_t ld2 = F.k + (F.k & 1);
-    c->t11r_ofs_h[f] = c->t11r_total;
-    c->l21t_ofs_h[f] = c->l21t_total;
-    c->t11r_total += int64_t(F.k) * ld2;
-    c->l21t_total += int64_t(F.n - F.k) * ld2;
+    S_.t11r_ofs_h[f] = S_.t11r_total;
+    S_.l21t_ofs_h[f] = S_.l21t_total;
+    S_.t11r_total += int64_t(F.k) * ld2;
+    S_.l21t_total += int64_t(F.n - F.k) * ld2;
   }
-  c->inv_h.clear();
-  c->invdiag_h.clear();
-  c->yscr_stride = 0;
-  c->max_level_fronts = 0;
+  S_.inv_h.clear();
+  S_.invdiag_h.clear();
+  S_.yscr_stride = 0;
+  S_.max_level_fronts = 0;
   int64_t off = 0;
   for (const Level &L : S.levels) {
     LevelDev lv;
-    lv.h = (int)c->levels.size();
+    lv.h = (int)S_.levels.size();
     lv.nf = (int)L.fronts.size();
-    lv.fronts = c->levfronts + off;
+    lv.fronts = S_.levfronts + off;
     off += lv.nf;
     lv.lbeg = L.lbeg;
     lv.lend = L.lend;
@@ -419,7 +459,7 @@ void build_steps(tem_ctx *c) {
     lv.max_k = L.max_k;
     lv.n_f21 = 0;
     lv.n_b21 = 0;
-    const size_t f21_beg = c->f21_h.size(), b21_beg = c->b21_h.size();
+    const size_t f21_beg = S_.f21_h.size(), b21_beg = S_.b21_h.size();
     for (int32_t fi : L.fronts) {
       const Front &F = S.fronts[fi];
       const int b = F.n - F.k;
@@ -427,12 +467,12 @@ void build_steps(tem_ctx *c) {
       // the forward product only where there are update rows; the backward
       // one for every front (it also forms w = D^-1 y of the pivots)
       if (b > 0)
-        for (int t = 0; t < div_up(b, SolveTile<R>::BM); t++) c->f21_h.push_back(make_int2(fi, t));
-      for (int t = 0; t < div_up(F.k, SolveTile<R>::BN); t++) c->b21_h.push_back(make_int2(fi, t));
+        for (int t = 0; t < div_up(b, SolveTile<R>::BM); t++) S_.f21_h.push_back(make_int2(fi, t));
+      for (int t = 0; t < div_up(F.k, SolveTile<R>::BN); t++) S_.b21_h.push_back(make_int2(fi, t));
     }
-    lv.n_f21 = int(c->f21_h.size() - f21_beg);
-    lv.n_b21 = int(c->b21_h.size() - b21_beg);
-    if constexpr (std::is_same<R, float>::value) build_fp32_tasks(c, L, lv);
+    lv.n_f21 = int(S_.f21_h.size() - f21_beg);
+    lv.n_b21 = int(S_.b21_h.size() - b21_beg);
+    if constexpr (std::is_same<R, float>::value) build_fp32_tasks(S_, L, lv);
     lv.f21_tasks = (const int2 *)(uintptr_t)f21_beg;   // offsets until the lists are on the device
     lv.b21_tasks = (const int2 *)(uintptr_t)b21_beg;
     // super-block products: forward rows of block J against pivots [0, J0);
@@ -440,7 +480,7 @@ void build_steps(tem_ctx *c) {
     const int nsb = div_up(L.max_k, kSB);
     lv.sb.assign(nsb, LevelDev::SuperBlock());
     for (int J = 0; J < nsb; J++) {
-      const size_t fb = c->sbf_h.size(), bb = c->sbb_h.size();
+      const size_t fb = S_.sbf_h.size(), bb = S_.sbb_h.size();
       for (int32_t fi : L.fronts) {
         const Front &F = S.fronts[fi];
         const int J0 = J * kSB;
@@ -448,13 +488,13 @@ void build_steps(tem_ctx *c) {
         const int J1 = std::min(F.k, J0 + kSB);
         for (int kb = 0; kb < J0; kb += kSplitK)
           for (int t = 0; t < div_up(J1 - J0, SolveTile<R>::BM); t++)
-            c->sbf_h.push_back(make_int4(fi, t, kb, std::min(J0, kb + kSplitK)));
+            S_.sbf_h.push_back(make_int4(fi, t, kb, std::min(J0, kb + kSplitK)));
         for (int rb = J1; rb < F.k; rb += kSplitK)
           for (int t = 0; t < div_up(J1 - J0, SolveTile<R>::BN); t++)
-            c->sbb_h.push_back(make_int4(fi, t, rb, std::min(F.k, rb + kSplitK)));
+            S_.sbb_h.push_back(make_int4(fi, t, rb, std::min(F.k, rb + kSplitK)));
       }
-      lv.sb[J].n_fwd = int(c->sbf_h.size() - fb);
-      lv.sb[J].n_bwd = int(c->sbb_h.size() - bb);
+      lv.sb[J].n_fwd = int(S_.sbf_h.size() - fb);
+      lv.sb[J].n_bwd = int(S_.sbb_h.size() - bb);
       lv.sb[J].fwd = (const int4 *)(uintptr_t)fb;   // offsets until the lists are on the device
       lv.sb[J].bwd = (const int4 *)(uintptr_t)bb;
     }
@@ -477,78 +517,120 @@ void build_steps(tem_ctx *c) {
       }
       lv.steps.push_back(d);
     }
-    c->max_level_fronts = std::max(c->max_level_fronts, lv.nf);
-    c->levels.push_back(std::move(lv));
+    S_.max_level_fronts = std::max(S_.max_level_fronts, lv.nf);
+    S_.levels.push_back(std::move(lv));
   }
 }
 
 template <typename R>
-FactorPlan<R> factor_plan(tem_ctx *c) {
+FactorPlan<R> factor_plan(FactorSys &S, DevStatus *status) {
   FactorPlan<R> P;
-  P.m = c->m;
-  P.L = (cx<R> *)c->L;
-  P.lstride = c->sym.ltotal;
-  P.U = (cx<R> *)c->U;
-  P.ustride = c->sym.utotal;
-  P.F = c->fronts;
-  P.rel = c->rel;
-  P.ea_child = c->ea_child;
-  P.ea_col = c->ea_col;
-  P.orig_nz = c->orig_nz;
-  P.orig_dst = c->orig_dst;
-  P.kval = c->kval;
-  P.mval = c->mval_fact ? c->mval_fact : c->mval;
-  P.mstride = c->mval_fact ? (int64_t)c->mesh.kval.size() : 0;
-  P.xi = c->xi;
-  P.dscr = (cx<R> *)c->dscr;
-  P.linv = (cx<R> *)c->linv;
-  P.istride = c->inv_blocks * kNB * kNB;
-  P.status = c->status;
-  P.dinv = (cx<R> *)c->dinv;
-  P.N = c->mesh.N;
-  P.yscr = (cx<R> *)c->yscr;
-  P.yscr_stride = c->yscr_stride;
-  P.T11R = (cx<R> *)c->T11R;
-  P.L21T = (cx<R> *)c->L21T;
-  P.t11r_stride = std::max<int64_t>(1, c->t11r_total);
-  P.l21t_stride = std::max<int64_t>(1, c->l21t_total);
-  P.t11r_ofs = c->t11r_ofs;
-  P.l21t_ofs = c->l21t_ofs;
+  P.m = S.m;
+  P.L = (cx<R> *)S.L;
+  P.lstride = S.sym.ltotal;
+  P.U = (cx<R> *)S.U;
+  P.ustride = S.sym.utotal;
+  P.F = S.fronts;
+  P.rel = S.rel;
+  P.ea_child = S.ea_child;
+  P.ea_col = S.ea_col;
+  P.orig_nz = S.orig_nz;
+  P.orig_dst = S.orig_dst;
+  P.kval = S.kval;
+  P.mval = S.mval;
+  P.mstride = S.mstride;
+  P.xi = S.xi;
+  P.dscr = (cx<R> *)S.dscr;
+  P.linv = (cx<R> *)S.linv;
+  P.istride = S.inv_blocks * kNB * kNB;
+  P.status = status;
+  P.dinv = (cx<R> *)S.dinv;
+  P.N = S.N;
+  P.yscr = (cx<R> *)S.yscr;
+  P.yscr_stride = S.yscr_stride;
+  P.T11R = (cx<R> *)S.T11R;
+  P.L21T = (cx<R> *)S.L21T;
+  P.t11r_stride = std::max<int64_t>(1, S.t11r_total);
+  P.l21t_stride = std::max<int64_t>(1, S.l21t_total);
+  P.t11r_ofs = S.t11r_ofs;
+  P.l21t_ofs = S.l21t_ofs;
   return P;
 }
 
 template <typename R>
-SolvePlan<R> solve_plan(tem_ctx *c) {
+SolvePlan<R> solve_plan(const FactorSys &S) {
   SolvePlan<R> P;
-  P.m = c->m;
-  P.nrhs = c->nrhs;
-  P.L = (const cx<R> *)c->L;
-  P.lstride = c->sym.ltotal;
-  P.Linv = (const cx<R> *)c->linv;
-  P.istride = c->inv_blocks * kNB * kNB;
-  P.F = c->fronts;
-  P.rows = c->rows;
-  P.Y = (cx<R> *)c->Y;
-  P.X = (cx<R> *)c->X;
-  P.vstride = c->mesh.N * c->nrhs;
-  P.dinv = (const cx<R> *)c->dinv;
-  P.tmaps = c->tmaps;
-  P.vmaps = c->vmaps;
-  P.N = c->mesh.N;
+  P.m = S.m;
+  P.nrhs = S.nrhs;
+  P.L = (const cx<R> *)S.L;
+  P.lstride = S.sym.ltotal;
+  P.Linv = (const cx<R> *)S.linv;
+  P.istride = S.inv_blocks * kNB * kNB;
+  P.F = S.fronts;
+  P.rows = S.rows;
+  P.Y = (cx<R> *)S.Y;
+  P.X = (cx<R> *)S.X;
+  P.vstride = S.N * S.nrhs;
+  P.dinv = (const cx<R> *)S.dinv;
+  P.tmaps = S.tmaps;
+  P.vmaps = S.vmaps;
+  P.N = S.N;
   return P;
 }
 
+// Factor every matrix of S, level by level (FP32: each level's pivot blocks
+// inverted in place and row-major copies written for the solves).
 template <typename R>
-void sweeps(tem_ctx *c, const int *pmap, int np) {
-  SolvePlan<R> P = solve_plan<R>(c);
+void factor_sys(tem_ctx *c, FactorSys &S) {
+  FactorPlan<R> P = factor_plan<R>(S, c->status);
+  const int H = (int)S.levels.size();
+  for (int h = 0; h < H; h++) {
+    P.level(h, S.levels[h], c->stream);
+    if constexpr (std::is_same<R, float>::value) P.invert_level(S.levels[h], c->stream);
+  }
+}
+
+// X = A_p^-1 Y for the mapped poles of S (forward and backward sweeps).
+template <typename R>
+void sweeps(tem_ctx *c, FactorSys &S, const int *pmap, int np) {
+  SolvePlan<R> P = solve_plan<R>(S);
   P.pmap = pmap;
   P.np = np;
   P.use_tc = c->use_tc;
   P.status = c->status;
   c->pole_solves += np;
-  const int H = (int)c->levels.size();
-  for (int h = 0; h < H; h++) P.forward_level(c->levels[h], c->stream);
-  for (int h = H - 1; h >= 0; h--) P.backward_level(c->levels[h], c->stream);
+  const int H = (int)S.levels.size();
+  for (int h = 0; h < H; h++) P.forward_level(S.levels[h], c->stream);
+  for (int h = H - 1; h >= 0; h--) P.backward_level(S.levels[h], c->stream);
+}
+
+// Gradient-space correction of one refinement step (FP32 mode), with the
+// residual r of the mapped poles in the edge system's Y (FP32, unscaled):
+// psi = L_sigma^-1 G^T r for all poles and right-hand sides at once (the
+// nodal system, one matrix), then x += -G psi / xi_p and r -= M(sigma) G psi.
+void nodal_correct(tem_ctx *c, const int *pm, int np) {
+  FactorSys &S = c->ns;
+  cudaStream_t s = c->stream;
+  auto pb = [&](int k) { if (g_prof) g_prof->begin(k, s); };
+  auto pe = [&](int k) { if (g_prof) g_prof->end(k, s); };
+  pb(KC_NODAL);
+  pb(KC_NODAL_RHS);
+  c64 *Yn = (c64 *)S.Y;
+  launch_nodal_rhs(c->n_gptr, c->n_gedge, c->n_gsign, (const c64 *)c->es.Y, Yn, S.N, np, pm, c->m, c->mesh.N,
+                   c->nrhs, s);
+  launch_scale_to_work<c64>(Yn, 0, Yn, c->colmax_n, 1, nullptr, S.N, S.nrhs, s);
+  pe(KC_NODAL_RHS);
+  pb(KC_NODAL_SWEEP);
+  if (g_prof) g_prof->muted = true;   // the nodal sweeps are not edge-system product launches
+  sweeps<float>(c, S, nullptr, 1);
+  if (g_prof) g_prof->muted = false;
+  pe(KC_NODAL_SWEEP);
+  c->pole_solves -= 1;
+  pb(KC_NODAL_APPLY);
+  launch_nodal_apply(c->n_crp, c->n_cci, c->n_cval, (const c64 *)S.X, c->colmax_n, (c64 *)c->es.Y, np, pm, c->m,
+                     c->mesh.N, c->nrhs, s);
+  pe(KC_NODAL_APPLY);
+  pe(KC_NODAL);
 }
 
 // x = A_i^-1 b for all poles; b c128 with pole stride bstride (0 = shared).
@@ -562,9 +644,9 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
   cudaStream_t s = c->stream;
   c->solve_calls++;
   if (c->precision == TEM_FP64) {
-    launch_rhs_to_work<double>(b, bstride, (c128 *)c->Y, nullptr, m, nullptr, N, nx, false, s);
-    sweeps<double>(c, nullptr, m);
-    launch_accumulate<double>((const c128 *)c->X, nullptr, x, m, nullptr, N, nx, false, s);
+    launch_rhs_to_work<double>(b, bstride, (c128 *)c->es.Y, nullptr, m, nullptr, N, nx, false, s);
+    sweeps<double>(c, c->es, nullptr, m);
+    launch_accumulate<double>((const c128 *)c->es.X, nullptr, x, m, nullptr, N, nx, false, s);
     return TEM_OK;
   }
   // FP32 mode: b and the iterate as double-float pairs, corrections in FP32
@@ -574,12 +656,12 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
   auto prof_end = [&](int k) { if (g_prof) g_prof->end(k, s); };
   prof_begin(KC_REFINE_VEC);
   launch_split_cx(b, bdf, (bstride ? int64_t(m) : int64_t(1)) * N * nx, s);
-  c64 *Y = (c64 *)c->Y;
+  c64 *Y = (c64 *)c->es.Y;
   launch_scale_to_work<float4>(bdf, bsd, Y, c->colmax_f, m, nullptr, N, nx, s);
   prof_end(KC_REFINE_VEC);
-  sweeps<float>(c, nullptr, m);
+  sweeps<float>(c, c->es, nullptr, m);
   prof_begin(KC_REFINE_VEC);
-  launch_accumulate_df((const c64 *)c->X, c->colmax_f, c->xdf, m, nullptr, N, nx, false, s);
+  launch_accumulate_df((const c64 *)c->es.X, c->colmax_f, c->xdf, m, nullptr, N, nx, false, s);
   prof_end(KC_REFINE_VEC);
   const int *pm = nullptr;
   int np = m;
@@ -587,16 +669,26 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
     prof_begin(KC_RESIDUAL);
     launch_residual_df(c->rp, c->ci, c->kdf, c->mdf, c->xi, bdf, bsd, c->xdf, Y, np, pm, N, nx, s);
     prof_end(KC_RESIDUAL);
+    if (c->use_nodal) nodal_correct(c, pm, np);
     prof_begin(KC_REFINE_VEC);
     launch_scale_to_work<c64>(Y, N * nx, Y, c->colmax_f, np, pm, N, nx, s);
     prof_end(KC_REFINE_VEC);
-    sweeps<float>(c, pm, np);
+    sweeps<float>(c, c->es, pm, np);
     prof_begin(KC_REFINE_VEC);
-    launch_accumulate_df((const c64 *)c->X, c->colmax_f, c->xdf, np, pm, N, nx, true, s);
+    NodalPart nd;   // the x update of this step's gradient-space correction, added with the edge correction
+    if (c->use_nodal) {
+      nd.Xn = (const c64 *)c->ns.X;
+      nd.colmax_n = c->colmax_n;
+      nd.e_lo = c->n_elo;
+      nd.e_hi = c->n_ehi;
+      nd.ninv_xi = c->ninv_xi;
+      nd.ncol = c->ns.nrhs;
+    }
+    launch_accumulate_df((const c64 *)c->es.X, c->colmax_f, c->xdf, np, pm, N, nx, true, s, nd);
     prof_end(KC_REFINE_VEC);
     if (c->refine_tol <= 0 || it + 1 == steps) continue;
     CK(cudaMemsetAsync(c->prog, 0, sizeof(double) * 2 * m, s));
-    launch_progress_df((const c64 *)c->X, c->colmax_f, c->xdf, c->earth, c->prog, c->prog + m, np, pm, N, nx, s);
+    launch_progress_df((const c64 *)c->es.X, c->colmax_f, c->xdf, c->earth, c->prog, c->prog + m, np, pm, N, nx, s);
     std::vector<double> pr(2 * m);
     std::vector<int> keep;
     CK(cudaMemcpyAsync(pr.data(), c->prog, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s));
@@ -617,63 +709,142 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
   return TEM_OK;
 }
 
+// Device copies of a system's assembly tree and of its factor / solve task lists.
+int upload_sys(tem_ctx *c, FactorSys &Q, bool fp32) {
+  const Symbolic &S = Q.sym;
+  std::vector<FrontDev> fd(S.fronts.size());
+  int64_t inv = 0;
+  for (size_t i = 0; i < S.fronts.size(); i++) {
+    const Front &F = S.fronts[i];
+    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, inv, F.n, F.k, F.c0, F.parent, F.ld, 0};
+    inv += div_up(F.k, kNB);
+  }
+  Q.inv_blocks = inv;
+  TRY(upload(c, &Q.fronts, fd));
+  TRY(upload(c, &Q.rows, S.rows));
+  TRY(upload(c, &Q.rel, S.rel));
+  TRY(upload(c, &Q.orig_nz, S.orig_nz));
+  TRY(upload(c, &Q.orig_dst, S.orig_dst));
+  TRY(upload(c, &Q.ea_child, S.ea_child));
+  TRY(upload(c, &Q.ea_col, S.ea_col));
+  std::vector<int32_t> lf;
+  for (const Level &L : S.levels) lf.insert(lf.end(), L.fronts.begin(), L.fronts.end());
+  TRY(upload(c, &Q.levfronts, lf));
+  if (fp32) build_steps<float>(Q);
+  else build_steps<double>(Q);
+  TRY(upload(c, &Q.f21, Q.f21_h));
+  TRY(upload(c, &Q.b21, Q.b21_h));
+  TRY(upload(c, &Q.sbf, Q.sbf_h));
+  TRY(upload(c, &Q.sbb, Q.sbb_h));
+  TRY(upload(c, &Q.prod, Q.prod_h));
+  TRY(upload(c, &Q.prod_simt, Q.prod_simt_h));
+  TRY(upload(c, &Q.rcopy, Q.rcopy_h));
+  TRY(upload(c, &Q.t11r_ofs, Q.t11r_ofs_h));
+  TRY(upload(c, &Q.l21t_ofs, Q.l21t_ofs_h));
+  TRY(upload(c, &Q.inv, Q.inv_h));
+  TRY(upload(c, &Q.invdiag, Q.invdiag_h));
+  for (LevelDev &lv : Q.levels) {
+    lv.f21_tasks = Q.f21 + (uintptr_t)lv.f21_tasks;
+    lv.b21_tasks = Q.b21 + (uintptr_t)lv.b21_tasks;
+    for (int mode = 0; mode < PM_COUNT; mode++) {
+      lv.prod[mode] = Q.prod + (uintptr_t)lv.prod[mode];
+      lv.prod_simt[mode] = Q.prod_simt + (uintptr_t)lv.prod_simt[mode];
+    }
+    lv.rcopy = Q.rcopy + (uintptr_t)lv.rcopy;
+    lv.inv_diag = Q.invdiag + (uintptr_t)lv.inv_diag;
+    for (auto &st : lv.inv) st.tasks = Q.inv + (uintptr_t)st.tasks;
+    for (auto &sb : lv.sb) {
+      sb.fwd = Q.sbf + (uintptr_t)sb.fwd;
+      sb.bwd = Q.sbb + (uintptr_t)sb.bwd;
+    }
+  }
+  for (const LevelDev &lv : Q.levels)
+    if (lv.nf > 65535) return fail(c, TEM_ERR_MESH, "more than 65535 fronts in one tree level");
+  return TEM_OK;
+}
+
+// Factor store, solve vectors and (FP32) inverse pivots, row-major copies and
+// tensor maps of one system.
+int alloc_sys(tem_ctx *c, FactorSys &S, bool fp32) {
+  const size_t es = fp32 ? sizeof(c64) : sizeof(c128);
+  const int64_t N = S.N;
+  const int m = S.m, nx = S.nrhs;
+  void *p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * S.sym.ltotal * es));
+  S.L = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * S.sym.utotal * es));
+  S.U = p;
+  TRY(dalloc(c, (char **)&p, size_t(std::max(1, S.max_level_fronts)) * m * kNB * kNB * es));
+  S.dscr = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * std::max<int64_t>(1, S.inv_blocks) * kNB * kNB * es));
+  S.linv = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
+  S.Y = p;
+  TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
+  S.X = p;
+  // the products read whole 16-row chunks of these (finite values past a block)
+  CK(cudaMemset(S.Y, 0, size_t(m) * N * nx * es));
+  CK(cudaMemset(S.X, 0, size_t(m) * N * nx * es));
+  if (!fp32) return TEM_OK;
+  TRY(dalloc(c, (c64 **)&S.dinv, size_t(m) * N));
+  TRY(dalloc(c, (c64 **)&S.yscr, size_t(m) * std::max<int64_t>(1, S.yscr_stride)));
+  TRY(dalloc(c, (c64 **)&S.T11R, size_t(m) * std::max<int64_t>(1, S.t11r_total)));
+  TRY(dalloc(c, (c64 **)&S.L21T, size_t(m) * std::max<int64_t>(1, S.l21t_total)));
+  std::vector<FrontGeom> geo(S.sym.fronts.size());
+  for (size_t i = 0; i < geo.size(); i++) {
+    const Front &F = S.sym.fronts[i];
+    geo[i] = FrontGeom{F.lofs, S.t11r_ofs_h[i], S.l21t_ofs_h[i], F.n, F.k, F.ld, F.k + (F.k & 1)};
+  }
+  const FactorViews views{(const c64 *)S.L, S.sym.ltotal, (const c64 *)S.T11R, std::max<int64_t>(1, S.t11r_total),
+                          (const c64 *)S.L21T, std::max<int64_t>(1, S.l21t_total)};
+  const std::string e = build_tensor_maps(geo, views, m, &S.tmaps);
+  if (!e.empty()) return fail(c, TEM_ERR_CUDA, e);
+  c->allocs.push_back(S.tmaps);
+  const std::string e2 =
+      build_vector_maps({VecBuf{(const c64 *)S.Y, N}, VecBuf{(const c64 *)S.X, N}}, 1, nx, m, &S.vmaps);
+  if (!e2.empty()) return fail(c, TEM_ERR_CUDA, e2);
+  if (S.vmaps) c->allocs.push_back(S.vmaps);
+  return TEM_OK;
+}
+
 int ensure_numeric(tem_ctx *c) {
-  if (c->L) return TEM_OK;
-  const size_t es = c->precision == TEM_FP64 ? sizeof(c128) : sizeof(c64);
+  if (c->es.L) return TEM_OK;
+  const bool fp32 = c->precision != TEM_FP64;
   const int64_t N = c->mesh.N;
   const int m = c->m, nx = c->nrhs;
-  void *p;
-  TRY(dalloc(c, (char **)&p, size_t(m) * c->sym.ltotal * es));
-  c->L = p;
-  TRY(dalloc(c, (char **)&p, size_t(m) * c->sym.utotal * es));
-  c->U = p;
-  TRY(dalloc(c, (char **)&p, size_t(std::max(1, c->max_level_fronts)) * m * kNB * kNB * es));
-  c->dscr = p;
-  TRY(dalloc(c, (char **)&p, size_t(m) * std::max<int64_t>(1, c->inv_blocks) * kNB * kNB * es));
-  c->linv = p;
-  TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
-  c->Y = p;
-  TRY(dalloc(c, (char **)&p, size_t(m) * N * nx * es));
-  c->X = p;
-  // the products read whole 16-row chunks of these (finite values past a block)
-  CK(cudaMemset(c->Y, 0, size_t(m) * N * nx * es));
-  CK(cudaMemset(c->X, 0, size_t(m) * N * nx * es));
+  c->es.m = m;
+  c->es.nrhs = nx;
+  TRY(alloc_sys(c, c->es, fp32));
   TRY(dalloc(c, &c->g, size_t(m) * N * nx));
   TRY(dalloc(c, &c->b, size_t(m) * N * nx));
   TRY(dalloc(c, &c->x, size_t(m) * N * nx));
-  if (c->precision != TEM_FP64) {
+  if (fp32) {
     TRY(dalloc(c, &c->r, size_t(m) * N * nx));
-    TRY(dalloc(c, (c64 **)&c->dinv, size_t(m) * N));
     TRY(dalloc(c, &c->kdf, c->mesh.kval.size()));
     TRY(dalloc(c, &c->mdf, c->mesh.kval.size()));
     TRY(dalloc(c, &c->xdf, size_t(m) * N * nx));
     TRY(dalloc(c, &c->colmax_f, size_t(m) * nx));
-    TRY(dalloc(c, (c64 **)&c->yscr, size_t(m) * std::max<int64_t>(1, c->yscr_stride)));
-    TRY(dalloc(c, (c64 **)&c->T11R, size_t(m) * std::max<int64_t>(1, c->t11r_total)));
-    TRY(dalloc(c, (c64 **)&c->L21T, size_t(m) * std::max<int64_t>(1, c->l21t_total)));
-    std::vector<FrontGeom> geo(c->sym.fronts.size());
-    for (size_t i = 0; i < geo.size(); i++) {
-      const Front &F = c->sym.fronts[i];
-      geo[i] = FrontGeom{F.lofs, c->t11r_ofs_h[i], c->l21t_ofs_h[i], F.n, F.k, F.ld, F.k + (F.k & 1)};
-    }
-    const FactorViews views{(const c64 *)c->L, c->sym.ltotal, (const c64 *)c->T11R,
-                            std::max<int64_t>(1, c->t11r_total), (const c64 *)c->L21T,
-                            std::max<int64_t>(1, c->l21t_total)};
-    const std::string e = build_tensor_maps(geo, views, m, &c->tmaps);
-    if (!e.empty()) return fail(c, TEM_ERR_CUDA, e);
-    c->allocs.push_back(c->tmaps);
-    const std::string e2 = build_vector_maps({VecBuf{(const c64 *)c->Y, N}, VecBuf{(const c64 *)c->X, N}}, 1, nx, m,
-                                             &c->vmaps);
-    if (!e2.empty()) return fail(c, TEM_ERR_CUDA, e2);
-    if (c->vmaps) c->allocs.push_back(c->vmaps);
     TRY(dalloc(c, &c->mval_fact, size_t(m) * c->mesh.kval.size()));
     std::vector<double> tf(c->mesh.nt);
     for (int64_t t = 0; t < c->mesh.nt; t++) tf[t] = 1.0 / (kMu0 * std::pow(c->mesh.vol[t], 2.0 / 3.0));
     TRY(upload(c, &c->tetfloor, tf));   // 1 / (mu0 h_t^2); tau applied at factor time
+    // nodal gradient space: one real Laplacian (as a complex matrix with xi = -1)
+    // for all m * nrhs right-hand sides of a refinement step
+    c->ns.m = 1;
+    c->ns.nrhs = m * nx;
+    TRY(alloc_sys(c, c->ns, true));
+    TRY(dalloc(c, &c->colmax_n, size_t(m) * nx));
+    TRY(dalloc(c, &c->part, size_t(m) * std::max<int64_t>(1, c->mesh.P)));
+    TRY(dalloc(c, &c->gdf, size_t(m) * N * nx));
+    TRY(dalloc(c, &c->vsdf, size_t(c->mesh.nt)));
   }
+  c->es.kval = c->kval;
+  c->es.mval = fp32 ? c->mval_fact : c->mval;
+  c->es.mstride = fp32 ? (int64_t)c->mesh.kval.size() : 0;
+  c->es.xi = c->xi;
   TRY(dalloc(c, &c->fb, size_t(N) * nx));
   TRY(dalloc(c, &c->colmax, size_t(m) * nx));
-  TRY(dalloc(c, &c->d_cur, size_t(nx) * c->n_rx * c->K));
+  TRY(dalloc(c, &c->d_cur, size_t(c->n_tx) * c->n_rx * c->K));
   TRY(dalloc(c, &c->pmap, size_t(m)));
   TRY(dalloc(c, &c->prog, size_t(2 * m)));
   TRY(dalloc(c, &c->m_cur, size_t(std::max<int64_t>(1, c->mesh.P))));
@@ -696,9 +867,11 @@ int tem_create(tem_ctx **ctx, int precision, void *stream) {
   c->precision = precision;
   c->stream = (cudaStream_t)stream;
   c->device = dev;
-  // 16 corrections: on the 46^3 box the data reach their floor after ~12 and J v after ~16
-  c->refine = precision == TEM_FP64 ? 0 : 16;
-  c->refine_adj = precision == TEM_FP64 ? 0 : 6;
+  // with the gradient-space correction and the floor tau = 1e-6, three corrections bring the
+  // data and J v within 1e-7 of the FP64 path on the 46^3 box (two leave J v near 3e-6), and one
+  // brings J^T w within 3e-9
+  c->refine = precision == TEM_FP64 ? 0 : 3;
+  c->refine_adj = precision == TEM_FP64 ? 0 : 1;
   if (dalloc(c, &c->status, 1)) {
     std::string m = c->err;
     delete c;
@@ -724,10 +897,9 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   if (!c) return TEM_ERR_ARG;
   if (c->state & ST_MESH) return fail(c, TEM_ERR_STATE, "mesh already set");
   if (!xyz || !tets || !sigma || !is_param) return fail(c, TEM_ERR_ARG, "NULL mesh array");
-  std::string msg = build_mesh(c->mesh, n_vert, xyz, n_tet, tets, sigma, is_param, leaf_max, c->sym);
+  std::string msg = build_mesh(c->mesh, n_vert, xyz, n_tet, tets, sigma, is_param, leaf_max, c->es.sym);
   if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
   Mesh &M = c->mesh;
-  Symbolic &S = c->sym;
   TRY(upload(c, &c->sigma_fixed, M.sigma));
   TRY(dalloc(c, &c->sigma, M.nt));
   TRY(upload(c, &c->me1, M.Me1));
@@ -751,60 +923,50 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
     TRY(upload(c, &c->earth, earth));
   }
   TRY(upload(c, &c->ptet, M.ptet));
-  std::vector<FrontDev> fd(S.fronts.size());
-  int64_t inv = 0;
-  for (size_t i = 0; i < S.fronts.size(); i++) {
-    const Front &F = S.fronts[i];
-    fd[i] = FrontDev{F.lofs, F.uofs, F.rows_off, F.rel_off, inv, F.n, F.k, F.c0, F.parent, F.ld, 0};
-    inv += div_up(F.k, kNB);
-  }
-  c->inv_blocks = inv;
-  TRY(upload(c, &c->fronts, fd));
-  TRY(upload(c, &c->rows, S.rows));
-  TRY(upload(c, &c->rel, S.rel));
-  TRY(upload(c, &c->orig_nz, S.orig_nz));
-  TRY(upload(c, &c->orig_dst, S.orig_dst));
-  TRY(upload(c, &c->ea_child, S.ea_child));
-  TRY(upload(c, &c->ea_col, S.ea_col));
-  std::vector<int32_t> lf;
-  for (const Level &L : S.levels) lf.insert(lf.end(), L.fronts.begin(), L.fronts.end());
-  TRY(upload(c, &c->levfronts, lf));
+  c->es.N = M.N;
+  TRY(upload_sys(c, c->es, c->precision != TEM_FP64));
   TRY(upload(c, &c->w_rp, M.w_rp));
   TRY(upload(c, &c->w_ci, M.w_ci));
   TRY(upload(c, &c->w_val, M.w_val));
   TRY(upload(c, &c->wt_rp, M.wt_rp));
   TRY(upload(c, &c->wt_ci, M.wt_ci));
   TRY(upload(c, &c->wt_val, M.wt_val));
-  if (c->precision == TEM_FP64) build_steps<double>(c);
-  else build_steps<float>(c);
-  TRY(upload(c, &c->f21, c->f21_h));
-  TRY(upload(c, &c->b21, c->b21_h));
-  TRY(upload(c, &c->sbf, c->sbf_h));
-  TRY(upload(c, &c->sbb, c->sbb_h));
-  TRY(upload(c, &c->prod, c->prod_h));
-  TRY(upload(c, &c->prod_simt, c->prod_simt_h));
-  TRY(upload(c, &c->rcopy, c->rcopy_h));
-  TRY(upload(c, &c->t11r_ofs, c->t11r_ofs_h));
-  TRY(upload(c, &c->l21t_ofs, c->l21t_ofs_h));
-  TRY(upload(c, &c->inv, c->inv_h));
-  TRY(upload(c, &c->invdiag, c->invdiag_h));
-  for (LevelDev &lv : c->levels) {
-    lv.f21_tasks = c->f21 + (uintptr_t)lv.f21_tasks;
-    lv.b21_tasks = c->b21 + (uintptr_t)lv.b21_tasks;
-    for (int mode = 0; mode < PM_COUNT; mode++) {
-      lv.prod[mode] = c->prod + (uintptr_t)lv.prod[mode];
-      lv.prod_simt[mode] = c->prod_simt + (uintptr_t)lv.prod_simt[mode];
+  if (c->precision != TEM_FP64) {
+    std::vector<float2> mp(M.Me1.size());
+    for (size_t q = 0; q < mp.size(); q++) {   // pairs hi + lo, both rounded to nearest
+      const float hi = static_cast<float>(M.Me1[q]);
+      mp[q] = make_float2(hi, static_cast<float>(M.Me1[q] - double(hi)));
     }
-    lv.rcopy = c->rcopy + (uintptr_t)lv.rcopy;
-    lv.inv_diag = c->invdiag + (uintptr_t)lv.inv_diag;
-    for (auto &st : lv.inv) st.tasks = c->inv + (uintptr_t)st.tasks;
-    for (auto &sb : lv.sb) {
-      sb.fwd = c->sbf + (uintptr_t)sb.fwd;
-      sb.bwd = c->sbb + (uintptr_t)sb.bwd;
-    }
+    TRY(upload(c, &c->me1df, mp));
+    // the gradient space of the refinement: interior vertices, P1 Laplacian
+    msg = build_nodal(M, leaf_max, c->nodal, c->ns.sym);
+    if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
+    const NodalMesh &G = c->nodal;
+    c->ns.N = G.N;
+    TRY(upload_sys(c, c->ns, true));
+    TRY(upload(c, &c->n_tnode, G.tnode));
+    TRY(upload(c, &c->n_stiff, G.S));
+    TRY(upload(c, &c->n_mc_ptr, G.mc_ptr));
+    TRY(upload(c, &c->n_mc_idx, G.mc_idx));
+    TRY(upload(c, &c->n_elo, G.e_lo));
+    TRY(upload(c, &c->n_ehi, G.e_hi));
+    TRY(upload(c, &c->n_gptr, G.g_ptr));
+    TRY(upload(c, &c->n_gedge, G.g_edge));
+    TRY(upload(c, &c->n_gsign, G.g_sign));
+    TRY(upload(c, &c->n_crp, G.c_rp));
+    TRY(upload(c, &c->n_cci, G.c_ci));
+    TRY(upload(c, &c->n_cmc_ptr, G.c_mc_ptr));
+    TRY(upload(c, &c->n_cmc_idx, G.c_mc_idx));
+    TRY(upload(c, &c->n_btab, G.B));
+    TRY(dalloc(c, &c->n_cval, G.c_ci.size()));
+    TRY(upload(c, &c->n_kval, std::vector<double>(G.ci.size(), 0.0)));
+    TRY(dalloc(c, &c->n_mval, G.ci.size()));
+    TRY(upload(c, &c->n_xi, std::vector<double2>{make_double2(-1.0, 0.0)}));
+    c->ns.kval = c->n_kval;
+    c->ns.mval = c->n_mval;
+    c->ns.mstride = 0;
+    c->ns.xi = c->n_xi;
   }
-  for (const LevelDev &lv : c->levels)
-    if (lv.nf > 65535) return fail(c, TEM_ERR_MESH, "more than 65535 fronts in one tree level");
   TRY(sync(c, "tem_mesh"));
   c->state |= ST_MESH;
   return TEM_OK;
@@ -824,6 +986,14 @@ int tem_poles(tem_ctx *c, int32_t m, const double *xi, int32_t n_times, const do
   std::vector<double> xv(c->xi_h), av(c->alpha_h);
   TRY(dalloc(c, &c->xi, m));
   TRY(dalloc(c, &c->alpha, size_t(m) * n_times));
+  {
+    std::vector<float2> w(m);
+    for (int i = 0; i < m; i++) {   // -1 / xi_i, for the gradient-space correction
+      const double a = xi[2 * i], b = xi[2 * i + 1], d = a * a + b * b;
+      w[i] = make_float2(float(-a / d), float(b / d));
+    }
+    TRY(upload(c, &c->ninv_xi, w));
+  }
   CK(cudaMemcpyAsync(c->xi, xv.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->alpha, av.data(), sizeof(double2) * m * n_times, cudaMemcpyHostToDevice, c->stream));
   TRY(sync(c, "tem_poles"));
@@ -880,7 +1050,7 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
     CK(cudaMemcpyAsync(c->m_cur, log_sigma, sizeof(double) * M.P, cudaMemcpyDeviceToDevice, s));
     launch_sigma(log_sigma, c->ptet, M.P, c->sigma, s);
   }
-  launch_mvals(c->mc_ptr, c->mc_idx, c->sigma, c->me1, (int64_t)M.kval.size(), c->mval, s);
+  launch_mvals(c->mc_ptr, c->mc_idx, c->sigma, c->me1, 36, (int64_t)M.kval.size(), c->mval, s);
   if (c->mval_fact) {
     launch_mvals_floor(c->mc_ptr, c->mc_idx, c->sigma, c->tetfloor, c->me1, c->xi, c->floor_tau, c->m,
                        (int64_t)M.kval.size(), c->mval_fact, s);
@@ -894,15 +1064,15 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
   double big = 1e308;
   memcpy(&init.min_pivot_bits, &big, sizeof(double));
   CK(cudaMemcpyAsync(c->status, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
-  const int H = (int)c->levels.size();
   if (c->precision == TEM_FP64) {
-    FactorPlan<double> P = factor_plan<double>(c);
-    for (int h = 0; h < H; h++) P.level(h, c->levels[h], s);
+    factor_sys<double>(c, c->es);
   } else {
-    FactorPlan<float> P = factor_plan<float>(c);
-    for (int h = 0; h < H; h++) {
-      P.level(h, c->levels[h], s);
-      P.invert_level(c->levels[h], s);
+    factor_sys<float>(c, c->es);
+    if (c->use_nodal) {
+      // sigma-weighted P1 Laplacian G^T M(sigma) G of the gradient space (pole independent)
+      launch_mvals(c->n_mc_ptr, c->n_mc_idx, c->sigma, c->n_stiff, 16, (int64_t)c->nodal.ci.size(), c->n_mval, s);
+      launch_mvals(c->n_cmc_ptr, c->n_cmc_idx, c->sigma, c->n_btab, 24, (int64_t)c->nodal.c_ci.size(), c->n_cval, s);
+      factor_sys<float>(c, c->ns);
     }
   }
   CK(cudaMemcpyAsync(&c->status_h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -926,6 +1096,8 @@ int tem_forward(tem_ctx *c, double *d) {
   const int64_t N = c->mesh.N;
   launch_real_to_c128(c->f, c->fb, N * c->nrhs, s);
   TRY(solve_all(c, c->fb, 0, c->g, c->refine));
+  if (c->precision != TEM_FP64)   // the Jacobian kernels read the forward solutions as pairs
+    CK(cudaMemcpyAsync(c->gdf, c->xdf, sizeof(float4) * c->m * N * c->nrhs, cudaMemcpyDeviceToDevice, s));
   launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->g, d, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K, s);
   CK(cudaMemcpyAsync(c->d_cur, d, sizeof(double) * c->n_tx * c->n_rx * c->K, cudaMemcpyDeviceToDevice, s));
   TRY(sync(c, "tem_forward"));
@@ -938,8 +1110,12 @@ namespace {
 int jvp_async(tem_ctx *c, const double *v, double *jv) {
   const int64_t N = c->mesh.N;
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_dm_apply(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->pidx, v, c->sigma, c->me1, c->xi, c->g, c->b,
-                  c->m, N, c->nrhs, c->stream);
+  if (c->precision == TEM_FP64)
+    launch_dm_apply(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->pidx, v, c->sigma, c->me1, c->xi, c->g, c->b,
+                    c->m, N, c->nrhs, c->stream);
+  else
+    launch_dm_apply_df(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->ptet, c->mesh.P, v, c->sigma, c->vsdf,
+                       c->mesh.nt, c->me1df, c->xi, c->gdf, c->b, c->m, N, c->nrhs, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine));
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
@@ -959,8 +1135,12 @@ int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
   // 1e-7 of the converged J^T w after 6)
   TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine_adj));
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->nrhs,
-                  c->precision != TEM_FP64, c->stream);
+  if (c->precision == TEM_FP64)
+    launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->nrhs,
+                    c->stream);
+  else   // per-pole double-float cell sums of the refined pairs (xdf holds z), then summed over poles
+    launch_bilinear_df(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1df, c->xi, c->gdf, c->xdf, jtw, c->m, N,
+                       c->nrhs, c->part, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   return TEM_OK;
 }
@@ -1068,6 +1248,16 @@ int tem_set_refine(tem_ctx *c, int32_t steps, double floor_tau, double tol) {
   return TEM_OK;
 }
 
+int tem_set_nodal(tem_ctx *c, int enable) {
+  if (!c) return TEM_ERR_ARG;
+  if (c->state & ST_FACTORED) {
+    // the nodal factor is formed by tem_factor: switching it on needs a new factorisation
+    if (enable && !c->use_nodal) c->state &= ~(ST_FACTORED | ST_FORWARD);
+  }
+  c->use_nodal = enable != 0;
+  return TEM_OK;
+}
+
 int tem_set_refine_adjoint(tem_ctx *c, int32_t steps) {
   if (!c) return TEM_ERR_ARG;
   if (steps < 0 || steps > 40) return fail(c, TEM_ERR_ARG, "refine steps in 0..40");
@@ -1082,12 +1272,12 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   o->n_tet = c->mesh.nt;
   o->n_param = c->mesh.P;
   o->n_faces_reg = c->mesh.nf;
-  o->n_fronts = (int64_t)c->sym.fronts.size();
-  o->n_levels = (int64_t)c->sym.levels.size();
+  o->n_fronts = (int64_t)c->es.sym.fronts.size();
+  o->n_levels = (int64_t)c->es.sym.levels.size();
   o->nnz_a = (int64_t)c->mesh.ci.size();
-  o->nnz_l = c->sym.nnz_l;
-  o->flops_factor = c->sym.flops;
-  o->max_front = c->sym.max_front;
+  o->nnz_l = c->es.sym.nnz_l;
+  o->flops_factor = c->es.sym.flops;
+  o->max_front = c->es.sym.max_front;
   o->bytes_device = c->bytes;
   o->m = c->m;
   o->n_times = c->K;
@@ -1100,11 +1290,11 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   double mp;
   memcpy(&mp, &c->status_h.min_pivot_bits, sizeof(double));
   o->min_pivot_abs = mp;
-  o->nnz_l11 = c->sym.nnz_l11;
+  o->nnz_l11 = c->es.sym.nnz_l11;
   o->pole_solves = c->pole_solves;
   o->solve_calls = c->solve_calls;
   int64_t nl = 0;
-  for (const LevelDev &lv : c->levels) {
+  for (const LevelDev &lv : c->es.levels) {
     if (c->precision == TEM_FP64) {
       nl += 2 * (int64_t)lv.steps.size() + (lv.n_f21 > 0 ? 1 : 0) + (lv.n_b21 > 0 ? 1 : 0);
       for (const auto &sb : lv.sb) nl += (sb.n_fwd > 0 ? 1 : 0) + (sb.n_bwd > 0 ? 1 : 0);
@@ -1116,6 +1306,9 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   o->tc_ctas_per_sm = tc_ctas_per_sm();
   o->tc_prod_launches = prod_launches(true);
   o->simt_prod_launches = prod_launches(false);
+  o->n_nodes = c->ns.N;
+  o->nnz_l_nodal = c->ns.sym.nnz_l;
+  o->nodal = c->precision != TEM_FP64 && c->use_nodal ? 1 : 0;
   return TEM_OK;
 }
 
@@ -1131,6 +1324,24 @@ int tem_export_pattern(tem_ctx *c, int64_t *nnz, int64_t *row_ptr, int32_t *col,
     if (!(c->state & ST_FACTORED)) return fail(c, TEM_ERR_STATE, "M values exist after tem_factor");
     CK(cudaMemcpy(m_val, c->mval, sizeof(double) * M.kval.size(), cudaMemcpyDeviceToHost));
   }
+  return TEM_OK;
+}
+
+int tem_export_forward(tem_ctx *c, double *g) {
+  if (!c || !g) return TEM_ERR_ARG;
+  if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
+  const int64_t N = c->mesh.N;
+  const int nx = c->nrhs;
+  std::vector<c128> h(size_t(c->m) * N * nx);
+  CK(cudaMemcpy(h.data(), c->g, sizeof(c128) * h.size(), cudaMemcpyDeviceToHost));
+  for (int p = 0; p < c->m; p++)
+    for (int64_t i = 0; i < N; i++)
+      for (int x = 0; x < c->n_tx; x++) {   // drop the padding right-hand side
+        const c128 v = h[(size_t(p) * N + i) * nx + x];
+        const size_t o = 2 * ((size_t(p) * N + i) * c->n_tx + x);
+        g[o] = v.x;
+        g[o + 1] = v.y;
+      }
   return TEM_OK;
 }
 

@@ -23,18 +23,21 @@ __global__ void k_sigma(const double *__restrict__ logs, const int32_t *__restri
   if (p < P) sigma[ptet[p]] = exp(logs[p]);
 }
 
-// M values: M_z = sum over element contributions sigma_t M1_t[a][b].
+// Conductivity-weighted values: M_z = sum over element contributions
+// sigma_t E_t[a][b], with `per` table entries per tetrahedron (36: the edge
+// mass matrices M1_t; 16: the P1 stiffness of the nodal gradient space).
+template <typename T>
 __global__ void k_mvals(const int64_t *__restrict__ mc_ptr, const uint32_t *__restrict__ mc_idx,
-                        const double *__restrict__ sigma, const double *__restrict__ me1,
-                        int64_t nnz, double *__restrict__ mval) {
+                        const double *__restrict__ sigma, const double *__restrict__ me1, uint32_t per,
+                        int64_t nnz, T *__restrict__ mval) {
   for (int64_t z = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; z < nnz;
        z += int64_t(gridDim.x) * blockDim.x) {
     double s = 0;
     for (int64_t q = mc_ptr[z]; q < mc_ptr[z + 1]; q++) {
       uint32_t idx = mc_idx[q];
-      s += sigma[idx / 36] * me1[idx];
+      s += sigma[idx / per] * me1[idx];
     }
-    mval[z] = s;
+    mval[z] = T(s);
   }
 }
 
@@ -337,10 +340,17 @@ void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *si
 }
 
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
-                  const double *me1, int64_t nnz, double *mval, cudaStream_t s) {
-  int blocks = (int)std::min<int64_t>(div_up(nnz, 256), 152 * 16);
+                  const double *me1, int per, int64_t nnz, double *mval, cudaStream_t s) {
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(div_up(nnz, 256), 152 * 16));
   tem::count_launch();
-  k_mvals<<<blocks, 256, 0, s>>>(mc_ptr, mc_idx, sigma, me1, nnz, mval);
+  k_mvals<double><<<blocks, 256, 0, s>>>(mc_ptr, mc_idx, sigma, me1, uint32_t(per), nnz, mval);
+}
+
+void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
+                  const double *me1, int per, int64_t nnz, float *mval, cudaStream_t s) {
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(div_up(nnz, 256), 152 * 16));
+  tem::count_launch();
+  k_mvals<float><<<blocks, 256, 0, s>>>(mc_ptr, mc_idx, sigma, me1, uint32_t(per), nnz, mval);
 }
 
 void launch_mvals_floor(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,

@@ -175,123 +175,37 @@ int32_t nd_recurse(NDState &st, std::vector<int32_t> &dofs, std::vector<int32_t>
 
 }  // namespace
 
-std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
-                       const double *sigma, const uint8_t *is_param, int32_t leaf_max,
-                       Symbolic &s) {
-  if (nv <= 0 || nt <= 0) return "empty mesh";
-  if (nv >= (int64_t(1) << 21)) return "more than 2^21 vertices are not supported";
-  if (nt * 36 >= (int64_t(1) << 32)) return "too many tetrahedra";
-  m.nv = nv;
-  m.nt = nt;
-  m.xyz.assign(xyz, xyz + 3 * nv);
-  m.tv.resize(4 * nt);
-  for (int64_t t = 0; t < nt; t++) {
-    int32_t v[4];
-    for (int a = 0; a < 4; a++) {
-      v[a] = tets[4 * t + a];
-      if (v[a] < 0 || v[a] >= nv) return "tet vertex id out of range";
-    }
-    std::sort(v, v + 4);
-    if (v[0] == v[1] || v[1] == v[2] || v[2] == v[3]) return "tet with repeated vertex";
-    for (int a = 0; a < 4; a++) m.tv[4 * t + a] = v[a];
-  }
-  // ---- edges ----
-  std::vector<int64_t> keys(6 * nt);
-  for (int64_t t = 0; t < nt; t++)
-    for (int i = 0; i < 6; i++)
-      keys[6 * t + i] = int64_t(m.tv[4 * t + kLocalEdge[i][0]]) * nv + m.tv[4 * t + kLocalEdge[i][1]];
-  m.ekey = keys;
-  std::sort(m.ekey.begin(), m.ekey.end());
-  m.ekey.erase(std::unique(m.ekey.begin(), m.ekey.end()), m.ekey.end());
-  m.ne = (int64_t)m.ekey.size();
-  m.ev.resize(2 * m.ne);
-  for (int64_t e = 0; e < m.ne; e++) {
-    m.ev[2 * e] = int32_t(m.ekey[e] / nv);
-    m.ev[2 * e + 1] = int32_t(m.ekey[e] % nv);
-  }
-  m.tedge.resize(6 * nt);
-  for (int64_t q = 0; q < 6 * nt; q++)
-    m.tedge[q] = int32_t(std::lower_bound(m.ekey.begin(), m.ekey.end(), keys[q]) - m.ekey.begin());
-  std::vector<int64_t>().swap(keys);
-  // ---- faces; PEC on edges of faces that belong to one tetrahedron ----
-  const int lf[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
-  std::vector<int64_t> fk(4 * nt);
-  const int64_t nv2 = nv * nv;
-  for (int64_t t = 0; t < nt; t++)
-    for (int f = 0; f < 4; f++)
-      fk[4 * t + f] = int64_t(m.tv[4 * t + lf[f][0]]) * nv2 + int64_t(m.tv[4 * t + lf[f][1]]) * nv +
-                      m.tv[4 * t + lf[f][2]];
-  std::sort(fk.begin(), fk.end());
-  std::vector<uint8_t> pec(m.ne, 0);
-  m.faces.clear();
-  for (size_t i = 0; i < fk.size();) {
-    size_t j = i;
-    while (j < fk.size() && fk[j] == fk[i]) j++;
-    int32_t a = int32_t(fk[i] / nv2), b = int32_t((fk[i] / nv) % nv), c = int32_t(fk[i] % nv);
-    m.faces.push_back(a);
-    m.faces.push_back(b);
-    m.faces.push_back(c);
-    if (j - i == 1) {
-      int32_t fv[3] = {a, b, c};
-      for (int q = 0; q < 3; q++)
-        for (int r = q + 1; r < 3; r++) {
-          int64_t key = int64_t(fv[q]) * nv + fv[r];
-          int64_t e = std::lower_bound(m.ekey.begin(), m.ekey.end(), key) - m.ekey.begin();
-          pec[e] = 1;
-        }
-    } else if (j - i > 2) {
-      return "non-manifold face shared by more than two tetrahedra";
-    }
-    i = j;
-  }
-  m.dof_old.assign(m.ne, -1);
-  int64_t N = 0;
-  for (int64_t e = 0; e < m.ne; e++)
-    if (!pec[e]) m.dof_old[e] = int32_t(N++);
-  m.N = N;
-  if (N == 0) return "no interior edges";
-  // ---- element matrices ----
-  m.vol.resize(nt);
-  m.Ke.resize(36 * nt);
-  m.Me1.resize(36 * nt);
-  std::vector<double> cent(3 * nt);
-  for (int64_t t = 0; t < nt; t++) {
-    double p[4][3];
-    for (int a = 0; a < 4; a++)
-      for (int d = 0; d < 3; d++) p[a][d] = m.xyz[3 * m.tv[4 * t + a] + d];
-    element_matrices(p, &m.Ke[36 * t], &m.Me1[36 * t], m.vol[t]);
-    if (!(m.vol[t] > 0)) return "degenerate tetrahedron";
-    for (int d = 0; d < 3; d++) cent[3 * t + d] = 0.25 * (p[0][d] + p[1][d] + p[2][d] + p[3][d]);
-  }
-  m.sigma.assign(sigma, sigma + nt);
-  m.is_param.assign(is_param, is_param + nt);
-  m.pidx.assign(nt, -1);
-  m.ptet.clear();
-  for (int64_t t = 0; t < nt; t++)
-    if (m.is_param[t]) {
-      m.pidx[t] = int32_t(m.ptet.size());
-      m.ptet.push_back(int32_t(t));
-    }
-  m.P = (int64_t)m.ptet.size();
-  // ---- old interior index -> incident tets ----
+// Ordering (nested dissection by plane cuts), full symmetric pattern and
+// assembly tree (fronts, relative maps, levels, update-arena plan, original
+// entries -> factor positions, extend-add tasks) of a symmetric matrix whose
+// unknowns sit on the tetrahedra: `per` slots per tetrahedron (its 6 edges or
+// its 4 vertices) hold the unknown there (-1: none).
+std::string build_symbolic(const SymIn &in, SymOut &out, Symbolic &s) {
+  const Mesh &m = *in.m;
+  const int64_t nt = m.nt, N = in.N;
+  const int per = in.per;
+  const std::vector<int32_t> &tu = *in.tunk;
+  const int32_t leaf_max = in.leaf_max;
+  if (N <= 0) return "no unknowns";
+  // ---- old unknown -> incident tets ----
   std::vector<int64_t> ip(N + 1, 0);
-  for (int64_t q = 0; q < 6 * nt; q++) {
-    int32_t d = m.dof_old[m.tedge[q]];
+  for (int64_t q = 0; q < per * nt; q++) {
+    int32_t d = tu[q];
     if (d >= 0) ip[d + 1]++;
   }
   for (int64_t d = 0; d < N; d++) ip[d + 1] += ip[d];
   std::vector<int32_t> itet(ip[N]);
   {
     std::vector<int64_t> pos(ip.begin(), ip.end() - 1);
-    for (int64_t q = 0; q < 6 * nt; q++) {
-      int32_t d = m.dof_old[m.tedge[q]];
-      if (d >= 0) itet[pos[d]++] = int32_t(q / 6);
+    for (int64_t q = 0; q < per * nt; q++) {
+      int32_t d = tu[q];
+      if (d >= 0) itet[pos[d]++] = int32_t(q / per);
     }
   }
   // ---- nested dissection ----
   NDState st;
   st.m = &m;
-  st.cent = &cent;
+  st.cent = &m.cent;
   st.inc_ptr = &ip;
   st.inc_tet = &itet;
   st.side.assign(nt, 0);
@@ -304,101 +218,49 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
   }
   std::vector<NDNode> &nodes = st.nodes;  // postorder: children precede parents
   const int32_t nn = (int32_t)nodes.size();
-  m.perm.resize(N);
-  m.iperm.assign(N, -1);
+  out.perm.resize(N);
+  out.iperm.assign(N, -1);
   std::vector<int32_t> node_c0(nn), owner(N);
   {
     int32_t pos = 0;
     for (int32_t i = 0; i < nn; i++) {
       node_c0[i] = pos;
       for (int32_t d : nodes[i].piv) {
-        m.perm[pos] = d;
-        m.iperm[d] = pos;
+        out.perm[pos] = d;
+        out.iperm[d] = pos;
         owner[pos] = i;
         pos++;
       }
     }
     if (pos != N) return "internal: ordering lost unknowns";
   }
-  m.tdof.resize(6 * nt);
-  for (int64_t q = 0; q < 6 * nt; q++) {
-    int32_t d = m.dof_old[m.tedge[q]];
-    m.tdof[q] = d >= 0 ? m.iperm[d] : -1;
+  out.tunk.resize(per * nt);
+  for (int64_t q = 0; q < per * nt; q++) {
+    int32_t d = tu[q];
+    out.tunk[q] = d >= 0 ? out.iperm[d] : -1;
   }
-  // ---- symmetric pattern of A (elimination numbering) ----
+  // ---- full symmetric pattern (elimination numbering) ----
   {
     std::vector<int64_t> pk;
-    pk.reserve(36 * nt);
+    pk.reserve(size_t(per) * per * nt);
     for (int64_t t = 0; t < nt; t++)
-      for (int a = 0; a < 6; a++) {
-        int32_t r = m.tdof[6 * t + a];
+      for (int a = 0; a < per; a++) {
+        int32_t r = out.tunk[per * t + a];
         if (r < 0) continue;
-        for (int b = 0; b < 6; b++) {
-          int32_t c = m.tdof[6 * t + b];
+        for (int b = 0; b < per; b++) {
+          int32_t c = out.tunk[per * t + b];
           if (c >= 0) pk.push_back(int64_t(r) * N + c);
         }
       }
     std::sort(pk.begin(), pk.end());
     pk.erase(std::unique(pk.begin(), pk.end()), pk.end());
-    m.rp.assign(N + 1, 0);
-    m.ci.resize(pk.size());
+    out.rp.assign(N + 1, 0);
+    out.ci.resize(pk.size());
     for (size_t q = 0; q < pk.size(); q++) {
-      m.rp[pk[q] / N + 1]++;
-      m.ci[q] = int32_t(pk[q] % N);
+      out.rp[pk[q] / N + 1]++;
+      out.ci[q] = int32_t(pk[q] % N);
     }
-    for (int64_t r = 0; r < N; r++) m.rp[r + 1] += m.rp[r];
-  }
-  const int64_t nnz = m.rp[N];
-  auto find_nz = [&](int32_t r, int32_t c) -> int64_t {
-    auto b = m.ci.begin() + m.rp[r], e = m.ci.begin() + m.rp[r + 1];
-    return std::lower_bound(b, e, c) - m.ci.begin();
-  };
-  m.kval.assign(nnz, 0.0);
-  m.mc_ptr.assign(nnz + 1, 0);
-  for (int64_t t = 0; t < nt; t++)
-    for (int a = 0; a < 6; a++) {
-      int32_t r = m.tdof[6 * t + a];
-      if (r < 0) continue;
-      for (int b = 0; b < 6; b++) {
-        int32_t c = m.tdof[6 * t + b];
-        if (c < 0) continue;
-        int64_t z = find_nz(r, c);
-        m.kval[z] += m.Ke[36 * t + 6 * a + b];
-        m.mc_ptr[z + 1]++;
-      }
-    }
-  for (int64_t z = 0; z < nnz; z++) m.mc_ptr[z + 1] += m.mc_ptr[z];
-  m.mc_idx.resize(m.mc_ptr[nnz]);
-  {
-    std::vector<int64_t> pos(m.mc_ptr.begin(), m.mc_ptr.end() - 1);
-    for (int64_t t = 0; t < nt; t++)
-      for (int a = 0; a < 6; a++) {
-        int32_t r = m.tdof[6 * t + a];
-        if (r < 0) continue;
-        for (int b = 0; b < 6; b++) {
-          int32_t c = m.tdof[6 * t + b];
-          if (c < 0) continue;
-          int64_t z = find_nz(r, c);
-          m.mc_idx[pos[z]++] = uint32_t(36 * t + 6 * a + b);
-        }
-      }
-  }
-  // ---- dof (new) -> incident (tet, local) ----
-  m.inc_ptr.assign(N + 1, 0);
-  for (int64_t q = 0; q < 6 * nt; q++)
-    if (m.tdof[q] >= 0) m.inc_ptr[m.tdof[q] + 1]++;
-  for (int64_t d = 0; d < N; d++) m.inc_ptr[d + 1] += m.inc_ptr[d];
-  m.inc_tet.resize(m.inc_ptr[N]);
-  m.inc_loc.resize(m.inc_ptr[N]);
-  {
-    std::vector<int64_t> pos(m.inc_ptr.begin(), m.inc_ptr.end() - 1);
-    for (int64_t q = 0; q < 6 * nt; q++) {
-      int32_t d = m.tdof[q];
-      if (d < 0) continue;
-      m.inc_tet[pos[d]] = int32_t(q / 6);
-      m.inc_loc[pos[d]] = int8_t(q % 6);
-      pos[d]++;
-    }
+    for (int64_t r = 0; r < N; r++) out.rp[r + 1] += out.rp[r];
   }
   // ---- assembly tree: update rows of every node (postorder) ----
   std::vector<std::vector<int32_t>> upd(nn);
@@ -408,8 +270,8 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
     const int32_t last = c0 + k - 1;
     std::vector<int32_t> &u = upd[i];
     for (int32_t r = c0; r < c0 + k; r++)
-      for (int64_t z = m.rp[r]; z < m.rp[r + 1]; z++) {
-        int32_t c = m.ci[z];
+      for (int64_t z = out.rp[r]; z < out.rp[r + 1]; z++) {
+        int32_t c = out.ci[z];
         if (c > last && stamp[c] != i) { stamp[c] = i; u.push_back(c); }
       }
     for (int q = 0; q < nodes[i].nchild; q++) {
@@ -561,8 +423,8 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
       const Front &F = s.fronts[f];
       const int32_t *urow = s.rows.data() + F.rows_off;
       const int32_t b = F.n - F.k;
-      for (int64_t z = m.rp[c]; z < m.rp[c + 1]; z++) {
-        int32_t r = m.ci[z];
+      for (int64_t z = out.rp[c]; z < out.rp[c + 1]; z++) {
+        int32_t r = out.ci[z];
         if (r < c) continue;
         int32_t loc;
         if (r < F.c0 + F.k) {
@@ -604,6 +466,175 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
       }
       L.ea_end[sl] = (int64_t)s.ea_child.size();
     }
+  return "";
+}
+
+std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
+                       const double *sigma, const uint8_t *is_param, int32_t leaf_max,
+                       Symbolic &s) {
+  if (nv <= 0 || nt <= 0) return "empty mesh";
+  if (nv >= (int64_t(1) << 21)) return "more than 2^21 vertices are not supported";
+  if (nt * 36 >= (int64_t(1) << 32)) return "too many tetrahedra";
+  m.nv = nv;
+  m.nt = nt;
+  m.xyz.assign(xyz, xyz + 3 * nv);
+  m.tv.resize(4 * nt);
+  for (int64_t t = 0; t < nt; t++) {
+    int32_t v[4];
+    for (int a = 0; a < 4; a++) {
+      v[a] = tets[4 * t + a];
+      if (v[a] < 0 || v[a] >= nv) return "tet vertex id out of range";
+    }
+    std::sort(v, v + 4);
+    if (v[0] == v[1] || v[1] == v[2] || v[2] == v[3]) return "tet with repeated vertex";
+    for (int a = 0; a < 4; a++) m.tv[4 * t + a] = v[a];
+  }
+  // ---- edges ----
+  std::vector<int64_t> keys(6 * nt);
+  for (int64_t t = 0; t < nt; t++)
+    for (int i = 0; i < 6; i++)
+      keys[6 * t + i] = int64_t(m.tv[4 * t + kLocalEdge[i][0]]) * nv + m.tv[4 * t + kLocalEdge[i][1]];
+  m.ekey = keys;
+  std::sort(m.ekey.begin(), m.ekey.end());
+  m.ekey.erase(std::unique(m.ekey.begin(), m.ekey.end()), m.ekey.end());
+  m.ne = (int64_t)m.ekey.size();
+  m.ev.resize(2 * m.ne);
+  for (int64_t e = 0; e < m.ne; e++) {
+    m.ev[2 * e] = int32_t(m.ekey[e] / nv);
+    m.ev[2 * e + 1] = int32_t(m.ekey[e] % nv);
+  }
+  m.tedge.resize(6 * nt);
+  for (int64_t q = 0; q < 6 * nt; q++)
+    m.tedge[q] = int32_t(std::lower_bound(m.ekey.begin(), m.ekey.end(), keys[q]) - m.ekey.begin());
+  std::vector<int64_t>().swap(keys);
+  // ---- faces; PEC on edges of faces that belong to one tetrahedron ----
+  const int lf[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+  std::vector<int64_t> fk(4 * nt);
+  const int64_t nv2 = nv * nv;
+  for (int64_t t = 0; t < nt; t++)
+    for (int f = 0; f < 4; f++)
+      fk[4 * t + f] = int64_t(m.tv[4 * t + lf[f][0]]) * nv2 + int64_t(m.tv[4 * t + lf[f][1]]) * nv +
+                      m.tv[4 * t + lf[f][2]];
+  std::sort(fk.begin(), fk.end());
+  std::vector<uint8_t> pec(m.ne, 0);
+  m.vbnd.assign(nv, 0);
+  m.faces.clear();
+  for (size_t i = 0; i < fk.size();) {
+    size_t j = i;
+    while (j < fk.size() && fk[j] == fk[i]) j++;
+    int32_t a = int32_t(fk[i] / nv2), b = int32_t((fk[i] / nv) % nv), c = int32_t(fk[i] % nv);
+    m.faces.push_back(a);
+    m.faces.push_back(b);
+    m.faces.push_back(c);
+    if (j - i == 1) {
+      int32_t fv[3] = {a, b, c};
+      m.vbnd[a] = m.vbnd[b] = m.vbnd[c] = 1;
+      for (int q = 0; q < 3; q++)
+        for (int r = q + 1; r < 3; r++) {
+          int64_t key = int64_t(fv[q]) * nv + fv[r];
+          int64_t e = std::lower_bound(m.ekey.begin(), m.ekey.end(), key) - m.ekey.begin();
+          pec[e] = 1;
+        }
+    } else if (j - i > 2) {
+      return "non-manifold face shared by more than two tetrahedra";
+    }
+    i = j;
+  }
+  m.dof_old.assign(m.ne, -1);
+  int64_t N = 0;
+  for (int64_t e = 0; e < m.ne; e++)
+    if (!pec[e]) m.dof_old[e] = int32_t(N++);
+  m.N = N;
+  if (N == 0) return "no interior edges";
+  // ---- element matrices ----
+  m.vol.resize(nt);
+  m.Ke.resize(36 * nt);
+  m.Me1.resize(36 * nt);
+  m.cent.assign(3 * nt, 0.0);
+  for (int64_t t = 0; t < nt; t++) {
+    double p[4][3];
+    for (int a = 0; a < 4; a++)
+      for (int d = 0; d < 3; d++) p[a][d] = m.xyz[3 * m.tv[4 * t + a] + d];
+    element_matrices(p, &m.Ke[36 * t], &m.Me1[36 * t], m.vol[t]);
+    if (!(m.vol[t] > 0)) return "degenerate tetrahedron";
+    for (int d = 0; d < 3; d++) m.cent[3 * t + d] = 0.25 * (p[0][d] + p[1][d] + p[2][d] + p[3][d]);
+  }
+  m.sigma.assign(sigma, sigma + nt);
+  m.is_param.assign(is_param, is_param + nt);
+  m.pidx.assign(nt, -1);
+  m.ptet.clear();
+  for (int64_t t = 0; t < nt; t++)
+    if (m.is_param[t]) {
+      m.pidx[t] = int32_t(m.ptet.size());
+      m.ptet.push_back(int32_t(t));
+    }
+  m.P = (int64_t)m.ptet.size();
+  // ---- ordering and assembly tree of A (unknowns on the interior edges) ----
+  {
+    std::vector<int32_t> tu(6 * nt);
+    for (int64_t q = 0; q < 6 * nt; q++) tu[q] = m.dof_old[m.tedge[q]];
+    SymIn in{&m, N, 6, &tu, leaf_max};
+    SymOut so;
+    const std::string e = build_symbolic(in, so, s);
+    if (!e.empty()) return e;
+    m.perm.swap(so.perm);
+    m.iperm.swap(so.iperm);
+    m.tdof.swap(so.tunk);
+    m.rp.swap(so.rp);
+    m.ci.swap(so.ci);
+  }
+  const int64_t nnz = m.rp[N];
+  auto find_nz = [&](int32_t r, int32_t c) -> int64_t {
+    auto b = m.ci.begin() + m.rp[r], e = m.ci.begin() + m.rp[r + 1];
+    return std::lower_bound(b, e, c) - m.ci.begin();
+  };
+  m.kval.assign(nnz, 0.0);
+  m.mc_ptr.assign(nnz + 1, 0);
+  for (int64_t t = 0; t < nt; t++)
+    for (int a = 0; a < 6; a++) {
+      int32_t r = m.tdof[6 * t + a];
+      if (r < 0) continue;
+      for (int b = 0; b < 6; b++) {
+        int32_t c = m.tdof[6 * t + b];
+        if (c < 0) continue;
+        int64_t z = find_nz(r, c);
+        m.kval[z] += m.Ke[36 * t + 6 * a + b];
+        m.mc_ptr[z + 1]++;
+      }
+    }
+  for (int64_t z = 0; z < nnz; z++) m.mc_ptr[z + 1] += m.mc_ptr[z];
+  m.mc_idx.resize(m.mc_ptr[nnz]);
+  {
+    std::vector<int64_t> pos(m.mc_ptr.begin(), m.mc_ptr.end() - 1);
+    for (int64_t t = 0; t < nt; t++)
+      for (int a = 0; a < 6; a++) {
+        int32_t r = m.tdof[6 * t + a];
+        if (r < 0) continue;
+        for (int b = 0; b < 6; b++) {
+          int32_t c = m.tdof[6 * t + b];
+          if (c < 0) continue;
+          int64_t z = find_nz(r, c);
+          m.mc_idx[pos[z]++] = uint32_t(36 * t + 6 * a + b);
+        }
+      }
+  }
+  // ---- dof (new) -> incident (tet, local) ----
+  m.inc_ptr.assign(N + 1, 0);
+  for (int64_t q = 0; q < 6 * nt; q++)
+    if (m.tdof[q] >= 0) m.inc_ptr[m.tdof[q] + 1]++;
+  for (int64_t d = 0; d < N; d++) m.inc_ptr[d + 1] += m.inc_ptr[d];
+  m.inc_tet.resize(m.inc_ptr[N]);
+  m.inc_loc.resize(m.inc_ptr[N]);
+  {
+    std::vector<int64_t> pos(m.inc_ptr.begin(), m.inc_ptr.end() - 1);
+    for (int64_t q = 0; q < 6 * nt; q++) {
+      int32_t d = m.tdof[q];
+      if (d < 0) continue;
+      m.inc_tet[pos[d]] = int32_t(q / 6);
+      m.inc_loc[pos[d]] = int8_t(q % 6);
+      pos[d]++;
+    }
+  }
   // ---- regulariser root W over parameter cells (two-point RT0 form) ----
   {
     std::vector<std::pair<int64_t, int32_t>> ft;  // (face key, tet)
@@ -628,7 +659,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
       for (int d = 0; d < 3; d++) {
         e1[d] = m.xyz[3 * v1 + d] - m.xyz[3 * v0 + d];
         e2[d] = m.xyz[3 * v2 + d] - m.xyz[3 * v0 + d];
-        dc[d] = cent[3 * a + d] - cent[3 * b + d];
+        dc[d] = m.cent[3 * a + d] - m.cent[3 * b + d];
       }
       cross3(e1, e2, cr);
       double area = 0.5 * std::sqrt(dot3(cr, cr));
@@ -663,6 +694,137 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
         m.wt_val[pos[p]] = m.w_val[q];
         pos[p]++;
       }
+  }
+  return "";
+}
+
+std::string build_nodal(const Mesh &m, int32_t leaf_max, NodalMesh &nm, Symbolic &s) {
+  const int64_t nt = m.nt, nv = m.nv;
+  // interior vertices: the hat functions whose gradients are interior edge fields
+  std::vector<int32_t> vold(nv, -1), vert_of;
+  for (int64_t v = 0; v < nv; v++)
+    if (!m.vbnd[v]) {
+      vold[v] = int32_t(vert_of.size());
+      vert_of.push_back(int32_t(v));
+    }
+  const int64_t N = (int64_t)vert_of.size();
+  if (N == 0) return "no interior vertices";
+  std::vector<int32_t> tu(4 * nt);
+  for (int64_t q = 0; q < 4 * nt; q++) tu[q] = vold[m.tv[q]];
+  SymIn in{&m, N, 4, &tu, leaf_max};
+  SymOut so;
+  const std::string e = build_symbolic(in, so, s);
+  if (!e.empty()) return e;
+  nm.N = N;
+  nm.perm.resize(N);
+  for (int64_t i = 0; i < N; i++) nm.perm[i] = vert_of[so.perm[i]];
+  nm.tnode.swap(so.tunk);
+  nm.rp.swap(so.rp);
+  nm.ci.swap(so.ci);
+  // P1 stiffness of every tetrahedron: S_t[a][b] = vol grad l_a . grad l_b
+  nm.S.resize(16 * nt);
+  for (int64_t t = 0; t < nt; t++) {
+    double p[4][3], g[4][3];
+    for (int a = 0; a < 4; a++)
+      for (int d = 0; d < 3; d++) p[a][d] = m.xyz[3 * m.tv[4 * t + a] + d];
+    bary_gradients(p, g);
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) nm.S[16 * t + 4 * a + b] = m.vol[t] * dot3(g[a], g[b]);
+  }
+  // contributions of the tetrahedra to each Laplacian entry
+  auto find_nz = [&](int32_t r, int32_t c) -> int64_t {
+    auto b = nm.ci.begin() + nm.rp[r], e2 = nm.ci.begin() + nm.rp[r + 1];
+    return std::lower_bound(b, e2, c) - nm.ci.begin();
+  };
+  const int64_t nnz = nm.rp[N];
+  nm.mc_ptr.assign(nnz + 1, 0);
+  for (int64_t t = 0; t < nt; t++)
+    for (int a = 0; a < 4; a++) {
+      const int32_t r = nm.tnode[4 * t + a];
+      if (r < 0) continue;
+      for (int b = 0; b < 4; b++) {
+        const int32_t c = nm.tnode[4 * t + b];
+        if (c >= 0) nm.mc_ptr[find_nz(r, c) + 1]++;
+      }
+    }
+  for (int64_t z = 0; z < nnz; z++) nm.mc_ptr[z + 1] += nm.mc_ptr[z];
+  nm.mc_idx.resize(nm.mc_ptr[nnz]);
+  {
+    std::vector<int64_t> pos(nm.mc_ptr.begin(), nm.mc_ptr.end() - 1);
+    for (int64_t t = 0; t < nt; t++)
+      for (int a = 0; a < 4; a++) {
+        const int32_t r = nm.tnode[4 * t + a];
+        if (r < 0) continue;
+        for (int b = 0; b < 4; b++) {
+          const int32_t c = nm.tnode[4 * t + b];
+          if (c >= 0) nm.mc_idx[pos[find_nz(r, c)]++] = uint32_t(16 * t + 4 * a + b);
+        }
+      }
+  }
+  // gradient incidence: edge unknown d (lower -> higher vertex) and its end nodes
+  std::vector<int32_t> vnew(nv, -1);
+  for (int64_t i = 0; i < N; i++) vnew[nm.perm[i]] = int32_t(i);
+  std::vector<int64_t> edge_of_old(m.N);
+  for (int64_t ed = 0; ed < m.ne; ed++)
+    if (m.dof_old[ed] >= 0) edge_of_old[m.dof_old[ed]] = ed;
+  nm.e_lo.resize(m.N);
+  nm.e_hi.resize(m.N);
+  nm.g_ptr.assign(N + 1, 0);
+  for (int64_t d = 0; d < m.N; d++) {
+    const int64_t ed = edge_of_old[m.perm[d]];
+    nm.e_lo[d] = vnew[m.ev[2 * ed]];
+    nm.e_hi[d] = vnew[m.ev[2 * ed + 1]];
+    if (nm.e_lo[d] >= 0) nm.g_ptr[nm.e_lo[d] + 1]++;
+    if (nm.e_hi[d] >= 0) nm.g_ptr[nm.e_hi[d] + 1]++;
+  }
+  for (int64_t i = 0; i < N; i++) nm.g_ptr[i + 1] += nm.g_ptr[i];
+  nm.g_edge.resize(nm.g_ptr[N]);
+  nm.g_sign.resize(nm.g_ptr[N]);
+  {
+    std::vector<int64_t> pos(nm.g_ptr.begin(), nm.g_ptr.end() - 1);
+    for (int64_t d = 0; d < m.N; d++) {
+      if (nm.e_lo[d] >= 0) {
+        const int64_t q = pos[nm.e_lo[d]]++;
+        nm.g_edge[q] = int32_t(d);
+        nm.g_sign[q] = -1;
+      }
+      if (nm.e_hi[d] >= 0) {
+        const int64_t q = pos[nm.e_hi[d]]++;
+        nm.g_edge[q] = int32_t(d);
+        nm.g_sign[q] = 1;
+      }
+    }
+  }
+  // C = M(sigma) G through the edge unknowns' incident (tet, local edge) pairs
+  nm.B.resize(24 * nt);
+  for (int64_t t = 0; t < nt; t++)
+    for (int a = 0; a < 4; a++)
+      for (int l = 0; l < 6; l++)
+        nm.B[24 * t + 6 * a + l] =
+            0.25 * (nm.S[16 * t + 4 * a + kLocalEdge[l][1]] - nm.S[16 * t + 4 * a + kLocalEdge[l][0]]);
+  nm.c_rp.assign(m.N + 1, 0);
+  nm.c_ci.clear();
+  nm.c_mc_ptr.assign(1, 0);
+  nm.c_mc_idx.clear();
+  std::vector<std::pair<int32_t, uint32_t>> row;   // (node, contribution)
+  for (int64_t d = 0; d < m.N; d++) {
+    row.clear();
+    for (int64_t q = m.inc_ptr[d]; q < m.inc_ptr[d + 1]; q++) {
+      const int32_t t = m.inc_tet[q], l = m.inc_loc[q];
+      for (int a = 0; a < 4; a++) {
+        const int32_t nd = nm.tnode[4 * int64_t(t) + a];
+        if (nd >= 0) row.push_back({nd, uint32_t(24 * int64_t(t) + 6 * a + l)});
+      }
+    }
+    std::sort(row.begin(), row.end());
+    for (size_t i = 0; i < row.size();) {
+      size_t j = i;
+      while (j < row.size() && row[j].first == row[i].first) nm.c_mc_idx.push_back(row[j++].second);
+      nm.c_ci.push_back(row[i].first);
+      nm.c_mc_ptr.push_back((int64_t)nm.c_mc_idx.size());
+      i = j;
+    }
+    nm.c_rp[d + 1] = (int64_t)nm.c_ci.size();
   }
   return "";
 }

@@ -231,8 +231,11 @@ struct VecBuf {
 std::string build_vector_maps(const std::vector<VecBuf> &bufs, int gather, int nrhs, int m, void **out);
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s);
+// mval[z] = sum over the contributions idx of entry z: sigma[idx / per] * me1[idx]
 void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
-                  const double *me1, int64_t nnz, double *mval, cudaStream_t s);
+                  const double *me1, int per, int64_t nnz, double *mval, cudaStream_t s);
+void launch_mvals(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
+                  const double *me1, int per, int64_t nnz, float *mval, cudaStream_t s);   // FP32 result
 void launch_mvals_floor(const int64_t *mc_ptr, const uint32_t *mc_idx, const double *sigma,
                         const double *tetfloor, const double *me1, const double2 *xi, double tau, int m,
                         int64_t nnz, double *mval, cudaStream_t s);
@@ -269,9 +272,26 @@ void launch_residual_df(const int64_t *rp, const int32_t *ci, const float2 *kdf,
 template <typename T>
 void launch_scale_to_work(const T *v, int64_t vstride, c64 *Y, float *colmax, int np, const int *pmap, int64_t N,
                           int nrhs, cudaStream_t s);
-// x (+)= colmax X in pairs
+// The gradient-space part of a refinement step's x update (Xn == nullptr: none):
+// x_p[d] += -(psi[e_hi[d]] - psi[e_lo[d]]) * ninv_xi[p], psi = colmax_n * Xn ([Nn][ncol]).
+struct NodalPart {
+  const c64 *Xn = nullptr;
+  const float *colmax_n = nullptr;
+  const int32_t *e_lo = nullptr, *e_hi = nullptr;
+  const float2 *ninv_xi = nullptr;   // -1 / xi_p
+  int ncol = 0;
+};
+// x (+)= colmax X in pairs (plus the nodal part)
 void launch_accumulate_df(const c64 *X, const float *colmax, float4 *x, int np, const int *pmap, int64_t N, int nrhs,
-                          bool add, cudaStream_t s);
+                          bool add, cudaStream_t s, const NodalPart &nd = NodalPart());
+// Gradient-space correction (refine.cu): Yn[a][p nrhs + j] = (G^T r_p)[a][j] for the
+// mapped poles (Yn [Nn][m nrhs], other poles' columns zeroed when pmap is set) ...
+void launch_nodal_rhs(const int64_t *g_ptr, const int32_t *g_edge, const int8_t *g_sign, const c64 *r, c64 *Yn,
+                      int64_t Nn, int np, const int *pmap, int m, int64_t N, int nrhs, cudaStream_t s);
+// ... and with psi = colmax_n Xn: r_p -= M(sigma) G psi_p (C = M G in CSR, FP32 values)
+void launch_nodal_apply(const int64_t *c_rp, const int32_t *c_ci, const float *c_val, const c64 *Xn,
+                        const float *colmax_n, c64 *r, int np, const int *pmap, int m, int64_t N, int nrhs,
+                        cudaStream_t s);
 void launch_progress_df(const c64 *X, const float *colmax, const float4 *x, const uint8_t *mask, double *num,
                         double *den, int np, const int *pmap, int64_t N, int nrhs, cudaStream_t s);
 // F (real [N][nrhs]) -> c128 b
@@ -289,11 +309,20 @@ void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_
                      const int32_t *tdof, const int32_t *pidx, const double *v, const double *sigma,
                      const double *me1, const double2 *xi, const c128 *g, c128 *h, int m, int64_t N,
                      int nrhs, cudaStream_t s);
-// grad[p] = 2 Re sum_i xi_i sigma_t sum_x (P z_ix)^T M1_t (P g_ix), t = ptet[p]
-// (fp32: the per-(pole, right-hand side) cell sums on the FP32 pipes)
+// grad[p] = 2 Re sum_i xi_i sigma_t sum_x (P z_ix)^T M1_t (P g_ix), t = ptet[p] (FP64)
 void launch_bilinear(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
                      const double *me1, const double2 *xi, const c128 *g, const c128 *z, double *grad,
-                     int m, int64_t N, int nrhs, bool fp32, cudaStream_t s);
+                     int m, int64_t N, int nrhs, cudaStream_t s);
+// the same from pairs (g, z float4 [m][N][nrhs], M1 float2 [nt][36]) in double-float
+// arithmetic; part: scratch [m][P] of per-pole cell sums
+void launch_bilinear_df(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
+                        const float2 *me1df, const double2 *xi, const float4 *gdf, const float4 *zdf, double *grad,
+                        int m, int64_t N, int nrhs, double *part, cudaStream_t s);
+// J v right-hand sides from pairs (vs: scratch [nt] for v_t sigma_t as pairs)
+void launch_dm_apply_df(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc, const int32_t *tdof,
+                        const int32_t *ptet, int64_t P, const double *v, const double *sigma, float2 *vs, int64_t nt,
+                        const float2 *me1df, const double2 *xi, const float4 *gdf, c128 *h, int m, int64_t N,
+                        int nrhs, cudaStream_t s);
 // sparse y = A x (CSR) and y = A^T x via the transpose CSR; beta-scaled accumulate
 void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,
                    int64_t rows, double alpha, double beta, cudaStream_t s);
@@ -312,10 +341,12 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 // Kernel classes that can be timed individually with CUDA events.
 enum KernelClass {
   KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT, KC_RESIDUAL, KC_REFINE_VEC, KC_JACOBIAN,
+  KC_NODAL, KC_NODAL_RHS, KC_NODAL_SWEEP, KC_NODAL_APPLY,
   KC_COUNT
 };
 struct Profiler {
   bool on = false;
+  bool muted = false;                  // inside a timed composite (the nodal correction)
   int cls = -1;                        // class being timed
   int level = -1;                      // tree level being timed (-1: all)
   int cur_level = -1;                  // level of the launches being issued

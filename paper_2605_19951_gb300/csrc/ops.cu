@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 
 namespace tem {
@@ -318,6 +319,69 @@ __global__ void k_dm_apply(const int64_t *__restrict__ inc_ptr, const int32_t *_
   }
 }
 
+// Refined-FP32 mode: the J v right-hand sides in double-float pairs, from the
+// forward solutions as pairs (gdf) and vs[t] = v_t sigma_t as pairs (zero on
+// cells that are not parameters): per unknown one Dot2 sum over its
+// tetrahedra and their six local unknowns, then times xi_p in FP64.
+__global__ void k_vsig_df(const int32_t *__restrict__ ptet, int64_t P, const double *__restrict__ v,
+                          const double *__restrict__ sigma, float2 *__restrict__ vs) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P; p += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t t = ptet[p];
+    const dfl d = split(v[p] * sigma[t]);
+    vs[t] = make_float2(d.hi, d.lo);
+  }
+}
+
+__global__ void k_dm_apply_df(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_tet,
+                              const int8_t *__restrict__ inc_loc, const int32_t *__restrict__ tdof,
+                              const float2 *__restrict__ vs, const float2 *__restrict__ me1df,
+                              const double2 *__restrict__ xi, const float4 *__restrict__ g, c128 *__restrict__ h,
+                              int64_t N, int nrhs) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int64_t d = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (d >= N) return;
+  const float4 *gp = g + p * N * nrhs;
+  const double2 s = xi[p];
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int x = c0 + lane;
+    if (x >= nrhs) break;
+    Dot2 ar, ai;
+    for (int64_t q = inc_ptr[d]; q < inc_ptr[d + 1]; q++) {
+      const int32_t t = inc_tet[q];
+      const float2 c2 = vs[t];
+      if (c2.x == 0.f) continue;
+      const dfl coef = {c2.x, c2.y};
+      const float2 *Me = me1df + int64_t(t) * 36 + inc_loc[q] * 6;
+      for (int b = 0; b < 6; b++) {
+        const int32_t db = tdof[int64_t(t) * 6 + b];
+        if (db < 0) continue;
+        const float2 m2 = Me[b];
+        const dfl cm = df_mul(coef, {m2.x, m2.y});
+        const float4 gv = gp[int64_t(db) * nrhs + x];
+        ar.add(cm, {gv.x, gv.y});
+        ai.add(cm, {gv.z, gv.w});
+      }
+    }
+    const double acx = df_to_double(ar.value()), acy = df_to_double(ai.value());
+    h[p * N * nrhs + d * nrhs + x] = mk<double>(s.x * acx - s.y * acy, s.x * acy + s.y * acx);
+  }
+}
+
+void launch_dm_apply_df(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc, const int32_t *tdof,
+                        const int32_t *ptet, int64_t P, const double *v, const double *sigma, float2 *vs, int64_t nt,
+                        const float2 *me1df, const double2 *xi, const float4 *gdf, c128 *h, int m, int64_t N,
+                        int nrhs, cudaStream_t s) {
+  cudaMemsetAsync(vs, 0, sizeof(float2) * nt, s);
+  if (P > 0) {
+    tem::count_launch();
+    k_vsig_df<<<(unsigned)std::min<int64_t>(div_up(P, 256), 4096), 256, 0, s>>>(ptet, P, v, sigma, vs);
+  }
+  dim3 gr(div_up(N, 8), m);
+  tem::count_launch();
+  k_dm_apply_df<<<gr, 256, 0, s>>>(inc_ptr, inc_tet, inc_loc, tdof, vs, me1df, xi, gdf, h, N, nrhs);
+}
+
 void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc,
                      const int32_t *tdof, const int32_t *pidx, const double *v, const double *sigma,
                      const double *me1, const double2 *xi, const c128 *g, c128 *h, int m, int64_t N,
@@ -327,10 +391,8 @@ void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_
   k_dm_apply<double><<<gr, 256, 0, s>>>(inc_ptr, inc_tet, inc_loc, tdof, pidx, v, sigma, me1, xi, g, h, N, nrhs);
 }
 
-// grad[pt] = 2 sigma_t Re sum_i xi_i sum_x (P_t z_ix)^T M1_t (P_t g_ix); one warp per cell.
-// T is the arithmetic type of the per-(pole, right-hand side) cell sums
-// (double in FP64 mode, float in refined-FP32 mode); the sums over right-hand
-// sides and poles run in FP64.
+// grad[pt] = 2 sigma_t Re sum_i xi_i sum_x (P_t z_ix)^T M1_t (P_t g_ix); one warp per cell
+// (FP64 mode: T = double).
 template <typename T>
 __global__ void k_bilinear(const int32_t *__restrict__ ptet, int64_t P, const int32_t *__restrict__ tdof,
                            const double *__restrict__ sigma, const double *__restrict__ me1,
@@ -377,13 +439,88 @@ __global__ void k_bilinear(const int32_t *__restrict__ ptet, int64_t P, const in
   if (lane == 0) grad[pt] = 2.0 * sigma[t] * total;
 }
 
+// Refined-FP32 mode: the same cell sums in double-float arithmetic on the FP32
+// pipes, one warp per (cell, pole): part[p][pt] = Re xi_p sum_x (P z_px)^T M1_t (P g_px),
+// with g, z the refined solutions as pairs [m][N][nrhs] (re.hi, re.lo, im.hi,
+// im.lo) and M1 as pairs, accumulated with Dot2.  The sums over poles cancel
+// (residue-like), so FP32 cell sums (relative 1e-7 each) would leave J^T w near
+// 1e-6; pairs leave it near 1e-12.
+__global__ void k_bilinear_df(const int32_t *__restrict__ ptet, int64_t P, const int32_t *__restrict__ tdof,
+                              const float2 *__restrict__ me1df, const double2 *__restrict__ xi,
+                              const float4 *__restrict__ g, const float4 *__restrict__ z, double *__restrict__ part,
+                              int64_t N, int nrhs) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int64_t pt = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (pt >= P) return;
+  const int32_t t = ptet[pt];
+  int32_t td[6];
+  for (int a = 0; a < 6; a++) td[a] = tdof[int64_t(t) * 6 + a];
+  const float2 *Me = me1df + int64_t(t) * 36;
+  const float4 *gp = g + p * N * nrhs;
+  const float4 *zp = z + p * N * nrhs;
+  double ar = 0, ai = 0;
+  for (int x = lane; x < nrhs; x += 32) {
+    float4 gl[6];
+    for (int b = 0; b < 6; b++) gl[b] = td[b] >= 0 ? gp[int64_t(td[b]) * nrhs + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+    Dot2 sr, si;
+    for (int a = 0; a < 6; a++) {
+      if (td[a] < 0) continue;
+      Dot2 mr, mi;
+      for (int b = 0; b < 6; b++) {
+        const float2 m2 = Me[a * 6 + b];
+        const dfl mab = {m2.x, m2.y};
+        mr.add(mab, {gl[b].x, gl[b].y});
+        mi.add(mab, {gl[b].z, gl[b].w});
+      }
+      const dfl Mr = mr.value(), Mi = mi.value();
+      const float4 zv = zp[int64_t(td[a]) * nrhs + x];
+      const dfl zr = {zv.x, zv.y}, zi = {zv.z, zv.w};
+      sr.add(zr, Mr);
+      sr.add(df_neg(zi), Mi);
+      si.add(zr, Mi);
+      si.add(zi, Mr);
+    }
+    ar += df_to_double(sr.value());
+    ai += df_to_double(si.value());
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
+    ai += __shfl_down_sync(0xffffffffu, ai, o);
+  }
+  if (lane == 0) {
+    const double2 s = xi[p];
+    part[p * P + pt] = s.x * ar - s.y * ai;
+  }
+}
+
+// grad[pt] = 2 sigma_t sum_p part[p][pt]  (poles summed in a fixed order)
+__global__ void k_bilinear_sum(const int32_t *__restrict__ ptet, int64_t P, const double *__restrict__ sigma,
+                               const double *__restrict__ part, double *__restrict__ grad, int m) {
+  for (int64_t pt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; pt < P; pt += int64_t(gridDim.x) * blockDim.x) {
+    double s = 0;
+    for (int p = 0; p < m; p++) s += part[p * P + pt];
+    grad[pt] = 2.0 * sigma[ptet[pt]] * s;
+  }
+}
+
 void launch_bilinear(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
                      const double *me1, const double2 *xi, const c128 *g, const c128 *z, double *grad,
-                     int m, int64_t N, int nrhs, bool fp32, cudaStream_t s) {
+                     int m, int64_t N, int nrhs, cudaStream_t s) {
   if (P == 0) return;
   tem::count_launch();
-  if (fp32) k_bilinear<float><<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
-  else k_bilinear<double><<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
+  k_bilinear<double><<<div_up(P, 8), 256, 0, s>>>(ptet, P, tdof, sigma, me1, xi, g, z, grad, m, N, nrhs);
+}
+
+void launch_bilinear_df(const int32_t *ptet, int64_t P, const int32_t *tdof, const double *sigma,
+                        const float2 *me1df, const double2 *xi, const float4 *gdf, const float4 *zdf, double *grad,
+                        int m, int64_t N, int nrhs, double *part, cudaStream_t s) {
+  if (P == 0) return;
+  dim3 gr(div_up(P, 8), m);
+  tem::count_launch();
+  k_bilinear_df<<<gr, 256, 0, s>>>(ptet, P, tdof, me1df, xi, gdf, zdf, part, N, nrhs);
+  tem::count_launch();
+  k_bilinear_sum<<<(unsigned)std::min<int64_t>(div_up(P, 256), 4096), 256, 0, s>>>(ptet, P, sigma, part, grad, m);
 }
 
 __global__ void k_csr_mv(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,

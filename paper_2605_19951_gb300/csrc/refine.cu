@@ -13,61 +13,11 @@
 // the end.  K x and M x are accumulated separately (the pair-valued K and M
 // are pole independent) and combined per row: r = b - K x + xi (M x).
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 
 namespace tem {
 
-namespace {
-
-// rounding-exact primitives (explicit _rn forms: no contraction or reassociation)
-struct dfl {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ dfl fast_two_sum(float a, float b) {   // |a| >= |b| (or a == 0)
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
-  const dfl s = two_sum(x.hi, y.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ dfl df_neg(dfl x) { return {-x.hi, -x.lo}; }
-
-// Dot2 accumulator: s + c, products of pairs added error-free into s
-struct Dot2 {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(dfl a, dfl b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const dfl t = two_sum(s, p);
-    s = t.hi;
-    c = __fadd_rn(c, __fadd_rn(t.lo, e));
-  }
-  __device__ __forceinline__ dfl value() const { return fast_two_sum(s, c); }
-};
-
-__device__ __forceinline__ dfl split(double d) {
-  const float h = __double2float_rn(d);
-  return {h, __double2float_rn(d - double(h))};
-}
-
-}  // namespace
 
 // pairs of a real FP64 array (K or M values)
 __global__ void k_split_real(const double *__restrict__ v, float2 *__restrict__ out, int64_t n) {
@@ -199,14 +149,18 @@ __global__ void k_scale_to_work(const T *__restrict__ v, int64_t vstride, c64 *_
 }
 
 // x (+)= colmax X as pairs: c X is formed exactly (TwoProduct) and added.
+// With the nodal part (Xn != nullptr) the gradient-space correction of the
+// same step is added too: x += -(psi[hi] - psi[lo]) / xi_p, psi = colmax_n Xn.
 __global__ void k_accumulate_df(const c64 *__restrict__ X, const float *__restrict__ colmax, float4 *__restrict__ x,
-                                int64_t N, int nrhs, int add, const int *__restrict__ pmap) {
+                                int64_t N, int nrhs, int add, const int *__restrict__ pmap, NodalPart nd) {
   const int p = pole_of(blockIdx.y, pmap);
   const c64 *Xp = X + p * N * nrhs;
   float4 *xp = x + p * N * nrhs;
   const int64_t cnt = N * nrhs;
+  const float2 w = nd.Xn ? nd.ninv_xi[p] : make_float2(0.f, 0.f);
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < cnt; e += int64_t(gridDim.x) * blockDim.x) {
-    const float cm = colmax[p * nrhs + e % nrhs];
+    const int j = int(e % nrhs);
+    const float cm = colmax[p * nrhs + j];
     const float c = cm > 0.f ? cm : 1.f;
     const c64 v = Xp[e];
     const float pr = __fmul_rn(c, v.x), pi = __fmul_rn(c, v.y);
@@ -215,6 +169,23 @@ __global__ void k_accumulate_df(const c64 *__restrict__ X, const float *__restri
       const float4 o = xp[e];
       ar = df_add({o.x, o.y}, ar);
       ai = df_add({o.z, o.w}, ai);
+    }
+    if (nd.Xn) {
+      const int64_t d = e / nrhs, col = int64_t(p) * nrhs + j;
+      const int lo = nd.e_lo[d], hi = nd.e_hi[d];
+      c64 g = mk<float>(0.f, 0.f);
+      if (hi >= 0) g = nd.Xn[int64_t(hi) * nd.ncol + col];
+      if (lo >= 0) {
+        const c64 l = nd.Xn[int64_t(lo) * nd.ncol + col];
+        g.x -= l.x;
+        g.y -= l.y;
+      }
+      const float cn = nd.colmax_n[col];
+      const float sc = cn > 0.f ? cn : 1.f;
+      g.x *= sc;
+      g.y *= sc;
+      ar = df_add(ar, {g.x * w.x - g.y * w.y, 0.f});
+      ai = df_add(ai, {g.x * w.y + g.y * w.x, 0.f});
     }
     xp[e] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
   }
@@ -245,6 +216,75 @@ __global__ void k_progress_df(const c64 *__restrict__ X, const float *__restrict
   if ((threadIdx.x & 31) == 0) {
     if (a > 0) atomicMax((unsigned long long *)&num[p], (unsigned long long)__double_as_longlong(double(a)));
     if (b > 0) atomicMax((unsigned long long *)&den[p], (unsigned long long)__double_as_longlong(double(b)));
+  }
+}
+
+// ---- gradient-space (nodal) correction of the refinement -------------------
+//
+// The floored factor leaves the gradient fields of the floored (air) cells
+// uncorrected: P_i^-1 A_i has eigenvalues sigma / s ~ 0 on them.  Each step
+// therefore also solves the residual equation on the gradient space
+// {G psi}: with K G = 0, G^T A_i G = -xi_i G^T M(sigma) G = -xi_i L_sigma, so
+//   psi = L_sigma^-1 G^T r,   x += -G psi / xi_i,   r -= M(sigma) G psi
+// (the residual update needs no K: (K - xi M) G psi / (-xi) = M G psi), one
+// pole-independent Laplacian for all poles and right-hand sides.
+
+// Yn[a][p nrhs + j] = (G^T r_p)[a][j] = sum over the edges at node a of +-r_p[e][j]
+// (one warp per node, lanes over right-hand sides); r complex FP32 [m][N][nrhs].
+__global__ void k_nodal_rhs(const int64_t *__restrict__ g_ptr, const int32_t *__restrict__ g_edge,
+                            const int8_t *__restrict__ g_sign, const c64 *__restrict__ r, c64 *__restrict__ Yn,
+                            int64_t Nn, int64_t N, int nrhs, int ncol, const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
+  const int lane = threadIdx.x & 31;
+  const int64_t a = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (a >= Nn) return;
+  const c64 *rp = r + p * N * nrhs;
+  const int64_t q0 = g_ptr[a], q1 = g_ptr[a + 1];
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int j = c0 + lane;
+    if (j >= nrhs) break;
+    float sr = 0.f, si = 0.f;
+    for (int64_t q = q0; q < q1; q++) {
+      const c64 v = rp[int64_t(g_edge[q]) * nrhs + j];
+      const float sg = float(g_sign[q]);
+      sr = fmaf(sg, v.x, sr);
+      si = fmaf(sg, v.y, si);
+    }
+    Yn[a * ncol + int64_t(p) * nrhs + j] = mk<float>(sr, si);
+  }
+}
+
+// With psi = colmax_n * Xn (the scaled nodal solution), for every edge unknown d:
+//   r_p[d][j] -= (C psi)[d],  C = M(sigma) G (sparse rows c_rp / c_ci / c_val, FP32);
+// the matching x update is added by k_accumulate_df after the edge sweeps.
+// One warp per edge unknown, lanes over right-hand sides.
+__global__ void k_nodal_apply(const int64_t *__restrict__ c_rp, const int32_t *__restrict__ c_ci,
+                              const float *__restrict__ c_val, const c64 *__restrict__ Xn,
+                              const float *__restrict__ colmax_n, c64 *__restrict__ r, int64_t N, int nrhs, int ncol,
+                              const int *__restrict__ pmap) {
+  const int p = pole_of(blockIdx.y, pmap);
+  const int lane = threadIdx.x & 31;
+  const int64_t d = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (d >= N) return;
+  const int64_t z0 = c_rp[d], z1 = c_rp[d + 1];
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int j = c0 + lane;
+    if (j >= nrhs) break;
+    const int64_t col = int64_t(p) * nrhs + j;
+    const float cm = colmax_n[col];
+    const float sc = cm > 0.f ? cm : 1.f;
+    float ar = 0.f, ai = 0.f;
+    for (int64_t q = z0; q < z1; q++) {
+      const float cv = c_val[q];
+      const c64 v = Xn[int64_t(c_ci[q]) * ncol + col];
+      ar = fmaf(cv, v.x, ar);
+      ai = fmaf(cv, v.y, ai);
+    }
+    const int64_t e = p * N * nrhs + d * nrhs + j;
+    c64 rv = r[e];
+    rv.x = fmaf(-sc, ar, rv.x);
+    rv.y = fmaf(-sc, ai, rv.y);
+    r[e] = rv;
   }
 }
 
@@ -298,10 +338,10 @@ template void launch_scale_to_work<float4>(const float4 *, int64_t, c64 *, float
                                            cudaStream_t);
 
 void launch_accumulate_df(const c64 *X, const float *colmax, float4 *x, int np, const int *pmap, int64_t N, int nrhs,
-                          bool add, cudaStream_t s) {
+                          bool add, cudaStream_t s, const NodalPart &nd) {
   dim3 g(grid_for(N * nrhs, 2048), np);
   tem::count_launch();
-  k_accumulate_df<<<g, 256, 0, s>>>(X, colmax, x, N, nrhs, add ? 1 : 0, pmap);
+  k_accumulate_df<<<g, 256, 0, s>>>(X, colmax, x, N, nrhs, add ? 1 : 0, pmap, nd);
 }
 
 void launch_progress_df(const c64 *X, const float *colmax, const float4 *x, const uint8_t *mask, double *num,
@@ -309,6 +349,23 @@ void launch_progress_df(const c64 *X, const float *colmax, const float4 *x, cons
   dim3 g(grid_for(N * nrhs, 1024), np);
   tem::count_launch();
   k_progress_df<<<g, 256, 0, s>>>(X, colmax, x, mask, num, den, N, nrhs, pmap);
+}
+
+void launch_nodal_rhs(const int64_t *g_ptr, const int32_t *g_edge, const int8_t *g_sign, const c64 *r, c64 *Yn,
+                      int64_t Nn, int np, const int *pmap, int m, int64_t N, int nrhs, cudaStream_t s) {
+  const int ncol = m * nrhs;
+  if (pmap) cudaMemsetAsync(Yn, 0, sizeof(c64) * Nn * ncol, s);   // poles not refining: zero columns
+  dim3 g((unsigned)div_up(Nn, 8), np);
+  tem::count_launch();
+  k_nodal_rhs<<<g, 256, 0, s>>>(g_ptr, g_edge, g_sign, r, Yn, Nn, N, nrhs, ncol, pmap);
+}
+
+void launch_nodal_apply(const int64_t *c_rp, const int32_t *c_ci, const float *c_val, const c64 *Xn,
+                        const float *colmax_n, c64 *r, int np, const int *pmap, int m, int64_t N, int nrhs,
+                        cudaStream_t s) {
+  dim3 g((unsigned)div_up(N, 8), np);
+  tem::count_launch();
+  k_nodal_apply<<<g, 256, 0, s>>>(c_rp, c_ci, c_val, Xn, colmax_n, r, N, nrhs, m * nrhs, pmap);
 }
 
 }  // namespace tem

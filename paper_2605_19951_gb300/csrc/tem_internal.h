@@ -44,6 +44,8 @@ struct Mesh {
   std::vector<int32_t> dof_old;     // [ne] interior index or -1 (PEC)
   std::vector<int32_t> tdof;        // [nt*6] elimination-numbered dof or -1
   std::vector<double> vol;          // [nt]
+  std::vector<double> cent;         // [nt*3] tetrahedron centroids
+  std::vector<uint8_t> vbnd;        // [nv] 1 = vertex of a boundary face (PEC)
   std::vector<double> Ke;           // [nt*36] curl-curl / mu0
   std::vector<double> Me1;          // [nt*36] unit-conductivity mass
   std::vector<double> sigma;        // [nt]
@@ -90,7 +92,51 @@ struct Symbolic {
   int32_t max_front = 0;
 };
 
+// Input of the ordering / assembly-tree builder: unknowns sitting on the
+// tetrahedra of a mesh, `per` slots per tetrahedron (6 edges or 4 vertices).
+struct SymIn {
+  const Mesh *m;                     // vertices, tetrahedra and their centroids
+  int64_t N;                         // unknowns, numbered 0..N-1 ("old" numbering)
+  int per;                           // slots per tetrahedron
+  const std::vector<int32_t> *tunk;  // [nt*per] old unknown of each slot, -1 = none
+  int32_t leaf_max;                  // largest leaf of the dissection (0 = default)
+};
+struct SymOut {
+  std::vector<int32_t> perm, iperm;  // new -> old, old -> new
+  std::vector<int32_t> tunk;         // [nt*per] elimination-numbered unknown of each slot, -1 = none
+  std::vector<int64_t> rp;           // full symmetric pattern, elimination numbering
+  std::vector<int32_t> ci;
+};
+
+// Gradient space of the edge unknowns (auxiliary nodal space of the FP32
+// refinement): the interior vertices (not on a boundary face) and the
+// sigma-weighted P1 Laplacian G^T M(sigma) G = sum_t sigma_t S_t on them,
+// S_t[a][b] = vol_t grad l_a . grad l_b.
+struct NodalMesh {
+  int64_t N = 0;                    // interior vertices
+  std::vector<int32_t> perm;        // elimination index -> vertex id
+  std::vector<int32_t> tnode;       // [nt*4] elimination-numbered node of each tet vertex, -1 on the boundary
+  std::vector<double> S;            // [nt*16] vol grad l_a . grad l_b (a, b = sorted local vertices)
+  std::vector<int64_t> rp;          // pattern of the Laplacian (elimination numbering)
+  std::vector<int32_t> ci;
+  std::vector<int64_t> mc_ptr;      // [nnz+1] contributions to each Laplacian entry ...
+  std::vector<uint32_t> mc_idx;     // ... as t*16 + 4a + b
+  std::vector<int32_t> e_lo, e_hi;  // [N_edge] nodes at the lower / higher end of each edge unknown (-1: boundary)
+  std::vector<int64_t> g_ptr;       // [N+1] node -> incident edge unknowns ...
+  std::vector<int32_t> g_edge;      // ... edge (elimination numbering)
+  std::vector<int8_t> g_sign;       // ... +1 at its higher end, -1 at its lower end
+  // C = M(sigma) G (edge unknowns x nodes): C[d][a] = sum_t sigma_t B_t[a][loc(d)],
+  // B_t[a][(i,j)] = int_t N_ij . grad l_a = (S_t[a][j] - S_t[a][i]) / 4
+  std::vector<double> B;            // [nt*24] at t*24 + 6a + local edge
+  std::vector<int64_t> c_rp;        // [N_edge+1] rows of C (edge unknowns, elimination numbering)
+  std::vector<int32_t> c_ci;        // node of each entry
+  std::vector<int64_t> c_mc_ptr;    // contributions to each entry ...
+  std::vector<uint32_t> c_mc_idx;   // ... as t*24 + 6a + local edge
+};
+
 // Host builders (host.cpp).  Return "" on success or an error message.
+std::string build_symbolic(const SymIn &in, SymOut &out, Symbolic &s);
+std::string build_nodal(const Mesh &m, int32_t leaf_max, NodalMesh &nm, Symbolic &s);
 std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt,
                        const int32_t *tets, const double *sigma,
                        const uint8_t *is_param, int32_t leaf_max, Symbolic &s);

@@ -22,7 +22,8 @@ ERRORS = {-1: "TEM_ERR_ARG", -2: "TEM_ERR_OOM", -3: "TEM_ERR_PIVOT", -4: "TEM_ER
           -5: "TEM_ERR_CUDA", -6: "TEM_ERR_STATE", -7: "TEM_ERR_MESH"}
 KERNEL_CLASSES = {"update": 0, "panel": 1, "fwd": 2, "bwd": 3, "bwd_upd": 4, "extend_add": 5, "fwd21": 6,
                   "fwd_sb": 7, "bwd_sb": 8, "invert": 9,
-                  "residual": 10, "refine_vec": 11, "jacobian": 12}
+                  "residual": 10, "refine_vec": 11, "jacobian": 12, "nodal": 13,
+                  "nodal_rhs": 14, "nodal_sweep": 15, "nodal_apply": 16}
 
 # C declarations, in include/tem.h order: name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -43,11 +44,13 @@ SIGNATURES = {
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
     "tem_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tem_set_nodal": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "tem_launch_count": (_I64, []),
     "tem_info": (ctypes.c_int, [_P, _P]),
     "tem_export_pattern": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P, _P, _P, _P]),
+    "tem_export_forward": (ctypes.c_int, [_P, _P]),
     "tem_export_dofs": (ctypes.c_int, [_P, _P]),
 }
 
@@ -60,7 +63,8 @@ class TemStats(ctypes.Structure):
                 ("precision", _I32), ("refine_steps", _I32), ("last_pivot_front", _I32),
                 ("min_pivot_abs", _D), ("nnz_l11", _I64), ("n_solve_launch", _I64),
                 ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("refine_steps_adjoint", _I32),
-                ("tc_prod_launches", _I64), ("simt_prod_launches", _I64)]
+                ("tc_prod_launches", _I64), ("simt_prod_launches", _I64),
+                ("n_nodes", _I64), ("nnz_l_nodal", _I64), ("nodal", _I32), ("reserved0", _I32)]
 
 
 class TemError(RuntimeError):
@@ -189,6 +193,10 @@ def tem_set_tensor_cores(ctx, enable):
     _check(ctx, load().tem_set_tensor_cores(ctx, int(bool(enable))))
 
 
+def tem_set_nodal(ctx, enable):
+    _check(ctx, load().tem_set_nodal(ctx, int(bool(enable))))
+
+
 def tem_set_profiling(ctx, kernel_class):
     kc = KERNEL_CLASSES.get(kernel_class, kernel_class) if kernel_class is not None else -1
     _check(ctx, load().tem_set_profiling(ctx, int(kc)))
@@ -229,6 +237,14 @@ def tem_export_dofs(ctx):
     ev = np.zeros((n, 2), dtype=np.int64)
     _check(ctx, load().tem_export_dofs(ctx, ev.ctypes.data_as(_P)))
     return ev
+
+
+def tem_export_forward(ctx):
+    """Forward solutions g [m, N, n_tx] complex, library numbering."""
+    info = tem_info(ctx)
+    g = np.zeros((info["m"], info["n_dof"], info["n_tx"], 2))
+    _check(ctx, load().tem_export_forward(ctx, g.ctypes.data_as(_P)))
+    return g[..., 0] + 1j * g[..., 1]
 
 
 # -- convenience wrapper ----------------------------------------------------------
