@@ -136,3 +136,20 @@ class LDLT:
         out = np.empty_like(X)
         out[self.perm] = X
         return out[:, 0] if vec else out
+
+
+def symbolic_nnz(A, perm):
+    """Entries of L (below the diagonal) of the up-looking factorisation of A's
+    pattern under the ordering perm, from the elimination tree alone."""
+    lib = _load()
+    n = A.shape[0]
+    Ap = sp.csr_matrix(A)[np.asarray(perm)][:, np.asarray(perm)]
+    U = sp.triu(Ap).tocsc()
+    U.sort_indices()
+    up = U.indptr.astype(np.int64)
+    ui = U.indices.astype(np.int64)
+    Lp = np.zeros(n + 1, dtype=np.int64)
+    parent = np.zeros(n, dtype=np.int64)
+    lnz = np.zeros(n, dtype=np.int64)
+    flag = np.zeros(n, dtype=np.int64)
+    return int(lib.ldl_symbolic(n, _ptr(up), _ptr(ui), _ptr(Lp), _ptr(parent), _ptr(lnz), _ptr(flag)))

@@ -14,7 +14,7 @@ chain-rule factor of the log parametrisation); A_i is complex symmetric
 (A^T = A, no conjugation), so A_i^-T = A_i^-1 and the same factors serve both
 products.  The solve step is the oracle's own plain sparse LDL^T (ldlt.c)
 under a coordinate-bisection ordering; the poles are independent, so they are
-factored on separate host threads.
+factored and solved on separate host threads (results combined in pole order).
 
 Array layouts match the GPU library: data d[x][r][j] (transmitter, receiver,
 time), model vectors over the earth cells in tet order.
@@ -106,26 +106,34 @@ class Oracle:
         loc = np.einsum("tab,tbx->tax", fe.Me1, gl) * (ve * self.sigma)[:, None, None]
         return self.xi[i] * (self.S @ loc.reshape(-1, gl.shape[2]))
 
+    def _per_pole(self, fn):
+        """fn(i) for every pole on the host threads, results in pole order (the
+        poles are independent; the solves release the GIL)."""
+        with ThreadPoolExecutor(self.threads) as ex:
+            return list(ex.map(fn, range(len(self.lu))))
+
     def jvp(self, v):
         """J v -> [n_x][n_r][K]."""
-        ys = []
-        for i, lu in enumerate(self.lu):
-            h = self.dM_apply(i, v)
-            ys.append(self.Q @ lu.solve(h))
-        return self._residue_sum(ys)
+        def one(i):
+            return self.Q @ self.lu[i].solve(self.dM_apply(i, v))
+        return self._residue_sum(self._per_pole(one))
 
     def jtvp(self, w):
         """J^T w, w[x][r][j] -> [P]."""
         w = np.asarray(w, dtype=np.float64)
         fe = self.fe
-        grad = np.zeros(fe.tdof.shape[0])
-        for i, lu in enumerate(self.lu):
+
+        def one(i):
             what = np.einsum("j,xrj->rx", self.alpha[i], w)          # [n_r, n_x] complex
-            z = lu.solve((self.Q.T @ what).astype(np.complex128))     # [N, n_x]
+            z = self.lu[i].solve((self.Q.T @ what).astype(np.complex128))     # [N, n_x]
             zl = self._local(z)
             gl = self._local(self.g[i])
             b = np.einsum("tax,tab,tbx->t", zl, fe.Me1, gl)
-            grad += 2.0 * np.real(self.xi[i] * b) * self.sigma
+            return 2.0 * np.real(self.xi[i] * b) * self.sigma
+
+        grad = np.zeros(fe.tdof.shape[0])
+        for part in self._per_pole(one):   # summed in pole order
+            grad += part
         return grad[self.pidx]
 
     def residual_norms(self, i, X, B):
