@@ -216,6 +216,14 @@ int tem_set_refine_adjoint(tem_ctx *ctx, int32_t steps);
  * TEM_ERR_TIMEOUT.  No effect in TEM_FP64 mode. */
 int tem_set_tensor_cores(tem_ctx *ctx, int enable);
 
+/* Limits of the bounded waits inside the tensor-core solve kernel (library
+ * wide; defaults 2^26 polls and 1 s).  A wait that runs out makes the kernel
+ * stop issuing work, drain its loads and MMAs in flight (with the default
+ * limits) and return; the call then fails with TEM_ERR_TIMEOUT, whose flag is
+ * cleared once reported.  For tests of that status: tiny limits make the
+ * waits run out on purpose.  max_polls >= 1, 0 < max_seconds <= 60. */
+int tem_set_wait_limit(tem_ctx *ctx, uint32_t max_polls, double max_seconds);
+
 /* TEM_FP32_REFINED mode: the gradient-space correction of every refinement
  * step (default 1).  The floored factor P_i leaves the gradient fields of the
  * floored cells almost uncorrected (P_i^-1 A_i ~ sigma / s ~ 0 there), so each

@@ -265,7 +265,12 @@ int check_solve_status(tem_ctx *c) {
   DevStatus h{};
   CK(cudaMemcpyAsync(&h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (h.tc_timeout) return fail(c, TEM_ERR_TIMEOUT, "a tensor-core completion wait expired in a solve");
+  if (h.tc_timeout) {
+    // reported once: the flag is cleared so that the context's next call starts clean
+    CK(cudaMemsetAsync(&c->status->tc_timeout, 0, sizeof(int32_t), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return fail(c, TEM_ERR_TIMEOUT, "a tensor-core completion wait expired in a solve");
+  }
   return TEM_OK;
 }
 
@@ -1229,6 +1234,13 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
   }
   TRY(sync(c, "tem_lsqr"));
   return check_solve_status(c);
+}
+
+int tem_set_wait_limit(tem_ctx *c, uint32_t max_polls, double max_seconds) {
+  if (!c) return TEM_ERR_ARG;
+  if (max_polls == 0 || !(max_seconds > 0) || max_seconds > 60) return fail(c, TEM_ERR_ARG, "bad wait limit");
+  set_tc_wait_limit(max_polls, uint64_t(max_seconds * 1e9));
+  return TEM_OK;
 }
 
 int tem_set_tensor_cores(tem_ctx *c, int enable) {

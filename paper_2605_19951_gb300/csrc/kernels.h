@@ -202,6 +202,8 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
 
 // Resident CTAs per SM of the tensor-core product kernel (0 before its first launch).
 int tc_ctas_per_sm();
+// Limits of the tensor-core pipeline waits (library-wide; defaults 2^26 polls, 1 s).
+void set_tc_wait_limit(uint32_t polls, uint64_t ns);
 // FP32 solve-product launches on the tensor cores (true) or the FP32 pipes, library-wide.
 int64_t prod_launches(bool tensor_cores);
 // Tensor maps of every front's factor block (4 per front, index 4 f + mode)

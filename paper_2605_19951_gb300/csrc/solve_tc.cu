@@ -67,6 +67,8 @@ struct ProdArgs {
   int nrhs, nchunk, np;
   const int *pmap;
   DevStatus *st;
+  uint32_t wait_iter;   // limits of the pipeline waits (polls, ns); the drains after an abort keep the defaults
+  uint64_t wait_ns;
 };
 
 // An item: task of pole p, RHS chunk ch (items are numbered per CTA).
@@ -175,10 +177,14 @@ struct KiShared {
 };
 constexpr size_t kKiSmem = sizeof(KiShared) + 1024;
 
-__device__ __forceinline__ bool ki_wait(KiShared &sh, uint64_t *bar, uint32_t parity, DevStatus *st) {
-  if (tc::mbar_wait_or_abort(bar, parity, kWaitIter, &sh.abort)) return true;
+// A pipeline wait; one that gives up raises the CTA's abort flag and the
+// status word.  Every role then stops issuing; the loader waits for its TMA
+// loads in flight and the MMA issuer for its MMAs (with the default limits)
+// before the CTA frees its TMEM and exits.
+__device__ __forceinline__ bool ki_wait(const ProdArgs &a, KiShared &sh, uint64_t *bar, uint32_t parity) {
+  if (tc::mbar_wait_or_abort(bar, parity, a.wait_iter, &sh.abort, a.wait_ns)) return true;
   sh.abort = 1;
-  atomicExch(&st->tc_timeout, 1);
+  atomicExch(&a.st->tc_timeout, 1);
   return false;
 }
 
@@ -237,7 +243,7 @@ __device__ void ki_loader(const ProdArgs &a, KiShared &sh, int lane) {
       }
       bool free = true;
       if (gc >= KI_SLOTS) {
-        if (lane == 0) free = ki_wait(sh, &sh.freeb[slot], ((gc / KI_SLOTS) - 1) & 1, a.st);
+        if (lane == 0) free = ki_wait(a, sh, &sh.freeb[slot], ((gc / KI_SLOTS) - 1) & 1);
         free = __shfl_sync(kFull, free, 0);
       }
       if (!free) {
@@ -277,7 +283,7 @@ __device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
 #pragma unroll 1
     for (int c = 0; c < it.nch; c++, g++) {
       const int slot = g % KI_SLOTS;
-      ok = ki_wait(sh, &sh.rawfull[slot], (g / KI_SLOTS) & 1, a.st);
+      ok = ki_wait(a, sh, &sh.rawfull[slot], (g / KI_SLOTS) & 1);
       if (!__all_sync(kFull, ok)) {
         ok = false;
         break;
@@ -346,13 +352,13 @@ __device__ void ki_mma(const ProdArgs &a, KiShared &sh) {
     const Item it = ki_begin(nxt);
     nxt = ki_item(a, j + 1);
     const int buf = j & 1, use = j >> 1;
-    if (use > 0 && !ki_wait(sh, &sh.acce[buf], (use - 1) & 1, a.st)) break;
+    if (use > 0 && !ki_wait(a, sh, &sh.acce[buf], (use - 1) & 1)) break;
     tc::fence_after();
     const uint32_t d = sh.tmem + 64 * buf;
 #pragma unroll 1
     for (int c = 0; c < it.nch; c++, g++) {
       const int slot = g % KI_SLOTS;
-      if (!ki_wait(sh, &sh.full[slot], (g / KI_SLOTS) & 1, a.st)) {
+      if (!ki_wait(a, sh, &sh.full[slot], (g / KI_SLOTS) & 1)) {
         ok = false;
         break;
       }
@@ -388,7 +394,7 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     const Item it = ki_begin(nxt);
     nxt = ki_item(a, j + 1);
     const int buf = j & 1, use = j >> 1;
-    const bool ok = ki_wait(sh, &sh.accf[buf], use & 1, a.st);
+    const bool ok = ki_wait(a, sh, &sh.accf[buf], use & 1);
     if (!__all_sync(kFull, ok)) break;
     tc::fence_after();
     float v[64];
@@ -537,6 +543,8 @@ __global__ void __launch_bounds__(256) k_prod_simt(const ProdArgs a, const SimtT
 
 namespace {
 int g_tc_occupancy = 0;
+uint32_t g_wait_iter = kWaitIter;   // pipeline-wait limits (tests of the timeout status shorten them)
+uint64_t g_wait_ns = 1000000000ull;
 std::atomic<int64_t> g_tc_launches{0}, g_simt_launches{0};
 
 template <int MODE>
@@ -573,6 +581,10 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
 }  // namespace
 
 int tc_ctas_per_sm() { return g_tc_occupancy; }
+void set_tc_wait_limit(uint32_t polls, uint64_t ns) {
+  g_wait_iter = polls;
+  g_wait_ns = ns;
+}
 int64_t prod_launches(bool tensor_cores) { return (tensor_cores ? g_tc_launches : g_simt_launches).load(); }
 
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
@@ -596,6 +608,8 @@ void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaSt
   a.np = P.np;
   a.pmap = P.pmap;
   a.st = P.status;
+  a.wait_iter = g_wait_iter;
+  a.wait_ns = g_wait_ns;
   a.dinv = P.dinv;
   a.tmaps = static_cast<const CUtensorMap *>(P.tmaps);
   const CUtensorMap *vm = static_cast<const CUtensorMap *>(P.vmaps);   // [0] Y, [1] X (nullptr: odd nrhs)

@@ -43,6 +43,7 @@ SIGNATURES = {
     "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
+    "tem_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint32, _D]),
     "tem_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_nodal": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -191,6 +192,10 @@ def tem_set_refine_adjoint(ctx, steps):
 
 def tem_set_tensor_cores(ctx, enable):
     _check(ctx, load().tem_set_tensor_cores(ctx, int(bool(enable))))
+
+
+def tem_set_wait_limit(ctx, max_polls, max_seconds):
+    _check(ctx, load().tem_set_wait_limit(ctx, int(max_polls), float(max_seconds)))
 
 
 def tem_set_nodal(ctx, enable):
