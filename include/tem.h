@@ -216,6 +216,16 @@ int tem_set_refine_adjoint(tem_ctx *ctx, int32_t steps);
  * TEM_ERR_TIMEOUT.  No effect in TEM_FP64 mode. */
 int tem_set_tensor_cores(tem_ctx *ctx, int enable);
 
+/* TEM_FP32_REFINED mode: the trailing updates of the dense fronts (Algorithm 1,
+ * factorise) on the tensor cores (default 1) or on the FP32 pipes (0).  On the
+ * tensor cores the pivots of a front go in blocks of 128: each 32-wide panel
+ * updates the rest of its block, and the block then updates the whole
+ * trailing part at once, F22 -= L21 D L21^T of rank 128, as tcgen05 TF32
+ * MMAs (hi / lo split, three MMAs per product, FP32 accumulation in TMEM)
+ * fed by TMA.  Takes effect at the next tem_factor (solves before it return
+ * TEM_ERR_STATE).  No effect in TEM_FP64 mode. */
+int tem_set_tc_fronts(tem_ctx *ctx, int enable);
+
 /* Limits of the bounded waits inside the tensor-core solve kernel (library
  * wide; defaults 2^26 polls and 1 s).  A wait that runs out makes the kernel
  * stop issuing work, drain its loads and MMAs in flight (with the default
@@ -245,8 +255,9 @@ int tem_set_nodal(tem_ctx *ctx, int enable);
  * 12 Jacobian kernels (J v right-hand sides, J^T w right-hand sides, residue
  * sums, cell sums), 13 gradient-space correction (G^T r, nodal sweeps,
  * M G psi; its sweeps count in no other class), and its parts: 14 G^T r and
- * scaling, 15 nodal sweeps, 16 M G psi and x update; -1 switches timing off
- * (the default).
+ * scaling, 15 nodal sweeps, 16 M G psi and x update; 17 tensor-core trailing
+ * updates of the factorisation (panel copies and rank-128 updates); -1
+ * switches timing off (the default).
  * class + 64 (h + 1) times only the launches of assembly-tree level h.
  * Timing adds an event pair around each launch of that class. */
 int tem_set_profiling(tem_ctx *ctx, int kernel_class);

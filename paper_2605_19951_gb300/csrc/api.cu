@@ -100,6 +100,14 @@ struct FactorSys {
   std::vector<int2> invdiag_h;
   int2 *invdiag = nullptr;
   int64_t yscr_stride = 0;                // inversion scratch per pole
+  // FP32: tensor-core trailing updates per kKB block (all levels)
+  std::vector<TcTask> upd_h;
+  TcTask *upd = nullptr;
+  std::vector<int4> ucopy_h;
+  int4 *ucopy = nullptr;
+  int64_t prows = 0;                      // rows of the panel copy (largest level block)
+  void *Pc = nullptr;                     // [m][prows][kKB] c64
+  void *cmaps = nullptr, *pcmap = nullptr;
   // device symbolic tables
   FrontDev *fronts = nullptr;
   int32_t *rows = nullptr, *rel = nullptr, *ea_child = nullptr, *ea_col = nullptr, *levfronts = nullptr;
@@ -138,6 +146,7 @@ struct tem_ctx {
   FactorSys ns;                           // FP32 mode: the nodal gradient-space Laplacian (one matrix)
   NodalMesh nodal;
   bool use_tc = true;                     // FP32 mode: front products on tcgen05
+  bool tc_fronts = true;                  // FP32 mode: trailing updates of the fronts on tcgen05
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -443,6 +452,9 @@ void build_steps(FactorSys &S_) {
   }
   S_.inv_h.clear();
   S_.invdiag_h.clear();
+  S_.upd_h.clear();
+  S_.ucopy_h.clear();
+  S_.prows = 0;
   S_.yscr_stride = 0;
   S_.max_level_fronts = 0;
   int64_t off = 0;
@@ -516,11 +528,58 @@ void build_steps(FactorSys &S_) {
         d.panel_tiles = std::max(d.panel_tiles, std::max(1, div_up(below, kPanelRT)));
         const int64_t T = div_up(below, UpdateTile<R>::TM);
         d.update_tiles = (int)std::max<int64_t>(d.update_tiles, std::max<int64_t>(1, T * (T + 1) / 2));
+        {   // restricted to the step's kKB block (tensor-core factor)
+          const int64_t pbeg = j0 + nb, s_end = std::min<int64_t>(F.k, (j0 / kKB + 1) * int64_t(kKB));
+          const int64_t TJ = s_end > pbeg ? div_up(s_end - pbeg, UpdateTile<R>::TM) : 0;
+          d.update_tiles_blk =
+              (int)std::max<int64_t>(d.update_tiles_blk, std::max<int64_t>(1, TJ * T - TJ * (TJ - 1) / 2));
+        }
         const int sb_end = std::min(F.k, (j0 / kSB + 1) * kSB), sb_beg = (j0 / kSB) * kSB;
         d.fwd_tiles = std::max(d.fwd_tiles, std::max(1, div_up(sb_end - j0 - nb, SolveTile<R>::RT)));
         d.bwd_tiles = std::max(d.bwd_tiles, std::max(1, div_up(j0 - sb_beg, SolveTile<R>::CT)));
       }
       lv.steps.push_back(d);
+    }
+    if constexpr (std::is_same<R, float>::value) {
+      // tensor-core trailing updates: per kKB block b, the fronts with pivots in it and rows below it
+      for (int b = 0; b * kKB < L.max_k; b++) {
+        UpdBlock ub;
+        const int j0 = b * kKB;
+        const size_t tb = S_.upd_h.size(), cb = S_.ucopy_h.size();
+        int64_t rows = 0;
+        for (int32_t fi : L.fronts) {
+          const Front &F = S.fronts[fi];
+          if (F.k <= j0) break;  // sorted by k descending
+          const int kb = std::min(kKB, F.k - j0), t0 = j0 + kb;
+          if (t0 >= F.n) continue;
+          const int64_t prow0 = rows - t0;   // panel-copy row of front row r: prow0 + r
+          S_.ucopy_h.push_back(make_int4(fi, int(prow0), t0, kb));
+          ub.copy_tiles = std::max(ub.copy_tiles, div_up(F.n - t0, 32));
+          for (int s0 = t0 & ~1; s0 < F.n; s0 += 32)
+            for (int r0 = t0 + std::max(0, (s0 - t0) / 128) * 128; r0 < F.n; r0 += 128) {
+              TcTask t;
+              t.map = fi;
+              t.x0 = int(prow0);
+              t.y0 = r0;
+              t.kdim = kb;
+              t.mrows = std::min(128, F.n - r0);
+              t.bbase = s0;
+              t.obase = j0;
+              t.mfirst = int16_t(std::max(0, t0 - s0));
+              t.kfirst = 0;
+              S_.upd_h.push_back(t);
+            }
+          rows += F.n - t0;
+        }
+        ub.ntask = int(S_.upd_h.size() - tb);
+        ub.ncopy = int(S_.ucopy_h.size() - cb);
+        std::stable_sort(S_.upd_h.begin() + tb, S_.upd_h.end(),
+                         [](const TcTask &x, const TcTask &y) { return x.kdim > y.kdim; });
+        ub.tasks = (const TcTask *)(uintptr_t)tb;   // offsets until the lists are on the device
+        ub.copies = (const int4 *)(uintptr_t)cb;
+        S_.prows = std::max(S_.prows, rows);
+        lv.upd.push_back(ub);
+      }
     }
     S_.max_level_fronts = std::max(S_.max_level_fronts, lv.nf);
     S_.levels.push_back(std::move(lv));
@@ -528,8 +587,13 @@ void build_steps(FactorSys &S_) {
 }
 
 template <typename R>
-FactorPlan<R> factor_plan(FactorSys &S, DevStatus *status) {
+FactorPlan<R> factor_plan(FactorSys &S, DevStatus *status, bool tc_update) {
   FactorPlan<R> P;
+  P.tc_update = tc_update && S.Pc != nullptr;
+  P.Pc = (cx<R> *)S.Pc;
+  P.pstride = std::max<int64_t>(1, S.prows) * kKB;
+  P.cmaps = S.cmaps;
+  P.pcmap = S.pcmap;
   P.m = S.m;
   P.L = (cx<R> *)S.L;
   P.lstride = S.sym.ltotal;
@@ -587,7 +651,7 @@ SolvePlan<R> solve_plan(const FactorSys &S) {
 // inverted in place and row-major copies written for the solves).
 template <typename R>
 void factor_sys(tem_ctx *c, FactorSys &S) {
-  FactorPlan<R> P = factor_plan<R>(S, c->status);
+  FactorPlan<R> P = factor_plan<R>(S, c->status, c->tc_fronts);
   const int H = (int)S.levels.size();
   for (int h = 0; h < H; h++) {
     P.level(h, S.levels[h], c->stream);
@@ -714,6 +778,39 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
   return TEM_OK;
 }
 
+// Host check of the tensor-core trailing-update tasks against the fronts and
+// the panel copy, before any of them reaches the device: every TMA x origin
+// even (16-byte aligned), every column and row inside its front, every copied
+// row inside the panel copy.  "" when all hold.
+std::string check_update_tasks(const FactorSys &Q) {
+  const auto &Fs = Q.sym.fronts;
+  for (const LevelDev &lv : Q.levels)
+    for (size_t b = 0; b < lv.upd.size(); b++) {
+      const UpdBlock &ub = lv.upd[b];
+      const size_t t0i = (uintptr_t)ub.tasks, c0i = (uintptr_t)ub.copies;
+      for (int q = 0; q < ub.ncopy; q++) {
+        const int4 cp = Q.ucopy_h[c0i + q];
+        if (cp.x < 0 || cp.x >= (int)Fs.size()) return "update copy: front out of range";
+        const Front &F = Fs[cp.x];
+        if (cp.w <= 0 || cp.w > kKB || cp.z - cp.w != int(b) * kKB || cp.z >= F.n || cp.z > F.k)
+          return "update copy: bad block";
+        if (int64_t(cp.y) + cp.z < 0 || int64_t(cp.y) + F.n > Q.prows) return "update copy: rows outside the copy";
+      }
+      for (int q = 0; q < ub.ntask; q++) {
+        const TcTask &t = Q.upd_h[t0i + q];
+        if (t.map < 0 || t.map >= (int)Fs.size()) return "update task: front out of range";
+        const Front &F = Fs[t.map];
+        const int t0 = t.obase + t.kdim;
+        if (t.obase != int(b) * kKB || t.kdim <= 0 || t.kdim > kKB || t0 > F.k) return "update task: bad block";
+        if (t.bbase & 1) return "update task: odd column origin";
+        if (t.bbase < 0 || t.bbase >= F.n || t.bbase + t.mfirst != std::max(t.bbase, t0)) return "update task: columns";
+        if (t.y0 < t0 || t.mrows <= 0 || t.mrows > 128 || t.y0 + t.mrows > F.n) return "update task: rows";
+        if (int64_t(t.x0) + t.y0 < 0 || int64_t(t.x0) + t.y0 + t.mrows > Q.prows) return "update task: copy rows";
+      }
+    }
+  return "";
+}
+
 // Device copies of a system's assembly tree and of its factor / solve task lists.
 int upload_sys(tem_ctx *c, FactorSys &Q, bool fp32) {
   const Symbolic &S = Q.sym;
@@ -748,6 +845,12 @@ int upload_sys(tem_ctx *c, FactorSys &Q, bool fp32) {
   TRY(upload(c, &Q.l21t_ofs, Q.l21t_ofs_h));
   TRY(upload(c, &Q.inv, Q.inv_h));
   TRY(upload(c, &Q.invdiag, Q.invdiag_h));
+  {
+    const std::string e = check_update_tasks(Q);
+    if (!e.empty()) return fail(c, TEM_ERR_MESH, "internal: " + e);
+  }
+  TRY(upload(c, &Q.upd, Q.upd_h));
+  TRY(upload(c, &Q.ucopy, Q.ucopy_h));
   for (LevelDev &lv : Q.levels) {
     lv.f21_tasks = Q.f21 + (uintptr_t)lv.f21_tasks;
     lv.b21_tasks = Q.b21 + (uintptr_t)lv.b21_tasks;
@@ -761,6 +864,10 @@ int upload_sys(tem_ctx *c, FactorSys &Q, bool fp32) {
     for (auto &sb : lv.sb) {
       sb.fwd = Q.sbf + (uintptr_t)sb.fwd;
       sb.bwd = Q.sbb + (uintptr_t)sb.bwd;
+    }
+    for (auto &ub : lv.upd) {
+      ub.tasks = Q.upd + (uintptr_t)ub.tasks;
+      ub.copies = Q.ucopy + (uintptr_t)ub.copies;
     }
   }
   for (const LevelDev &lv : Q.levels)
@@ -809,6 +916,14 @@ int alloc_sys(tem_ctx *c, FactorSys &S, bool fp32) {
       build_vector_maps({VecBuf{(const c64 *)S.Y, N}, VecBuf{(const c64 *)S.X, N}}, 1, nx, m, &S.vmaps);
   if (!e2.empty()) return fail(c, TEM_ERR_CUDA, e2);
   if (S.vmaps) c->allocs.push_back(S.vmaps);
+  // panel copy of the tensor-core trailing updates (zeroed once: rows a box reads past a front stay finite)
+  TRY(dalloc(c, (c64 **)&S.Pc, size_t(m) * std::max<int64_t>(1, S.prows) * kKB));
+  CK(cudaMemset(S.Pc, 0, sizeof(c64) * size_t(m) * std::max<int64_t>(1, S.prows) * kKB));
+  const std::string e3 = build_update_maps(geo, (const c64 *)S.L, S.sym.ltotal, (const c64 *)S.Pc,
+                                           std::max<int64_t>(1, S.prows), m, &S.cmaps, &S.pcmap);
+  if (!e3.empty()) return fail(c, TEM_ERR_CUDA, e3);
+  c->allocs.push_back(S.cmaps);
+  c->allocs.push_back(S.pcmap);
   return TEM_OK;
 }
 
@@ -1246,6 +1361,13 @@ int tem_set_wait_limit(tem_ctx *c, uint32_t max_polls, double max_seconds) {
 int tem_set_tensor_cores(tem_ctx *c, int enable) {
   if (!c) return TEM_ERR_ARG;
   c->use_tc = enable != 0;
+  return TEM_OK;
+}
+
+int tem_set_tc_fronts(tem_ctx *c, int enable) {
+  if (!c) return TEM_ERR_ARG;
+  if (c->tc_fronts != (enable != 0)) c->state &= ~(ST_FACTORED | ST_FORWARD);   // the next tem_factor decides
+  c->tc_fronts = enable != 0;
   return TEM_OK;
 }
 

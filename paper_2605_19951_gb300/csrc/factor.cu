@@ -12,6 +12,8 @@
 // extend-add the children, then a blocked right-looking partial LDL^T:
 // k_panel factors the NB x NB diagonal block and the panel rows below it,
 // k_update applies the rank-NB update to the trailing lower triangle.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -241,13 +243,16 @@ __global__ void __launch_bounds__(RT) k_panel(cx<R> *__restrict__ L, int64_t lst
 // Trailing update of step `step`: F[r][s] -= sum_c L[r][c] D_c L[s][c] over
 // the panel columns, for r >= s in the trailing part; tiles of TM x TM in the
 // lower triangle, 16 x 16 threads with (TM/16)^2 outputs each.  CTA 0 of
-// each front first copies the factored diagonal block into place.
+// each front first copies the factored diagonal block into place.  With
+// blk > 0 only the columns of the step's block of blk pivots are updated (the
+// rest of the trailing part gets the block's rank-blk update on the tensor
+// cores once the block is factored).
 template <typename R, int NB, int TM>
 __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t lstride,
                                                 cx<R> *__restrict__ U, int64_t ustride,
                                                 const FrontDev *__restrict__ F,
                                                 const int32_t *__restrict__ lev, int step,
-                                                const cx<R> *__restrict__ dscr) {
+                                                const cx<R> *__restrict__ dscr, int blk) {
   constexpr int PT = TM / 16;
   const int fi = blockIdx.y;
   const FrontDev f = F[lev[fi]];
@@ -270,11 +275,26 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
   if (tn <= 0) return;
   const int64_t T = (tn + TM - 1) / TM;
   const int64_t q = blockIdx.x;
-  if (q >= T * (T + 1) / 2) return;
-  int64_t ti = int64_t((sqrt(8.0 * double(q) + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= q) ti++;
-  while (ti * (ti + 1) / 2 > q) ti--;
-  const int64_t tj = q - ti * (ti + 1) / 2;
+  const int64_t s_end = blk > 0 ? min(int64_t(f.k), (int64_t(j0) / blk + 1) * blk) : n;
+  int64_t ti, tj;
+  if (blk > 0) {
+    // tiles (ti >= tj) of the first TJ tile columns, column by column
+    const int64_t TJ = s_end > pbeg ? (s_end - pbeg + TM - 1) / TM : 0;
+    int64_t qq = q;
+    tj = 0;
+    while (tj < TJ && qq >= T - tj) {
+      qq -= T - tj;
+      tj++;
+    }
+    if (tj >= TJ) return;
+    ti = tj + qq;
+  } else {
+    if (q >= T * (T + 1) / 2) return;
+    ti = int64_t((sqrt(8.0 * double(q) + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= q) ti++;
+    while (ti * (ti + 1) / 2 > q) ti--;
+    tj = q - ti * (ti + 1) / 2;
+  }
   const int64_t r0 = pbeg + ti * TM, s0 = pbeg + tj * TM;
   __shared__ cx<R> As[NB][TM];
   __shared__ cx<R> Bs[NB][TM];
@@ -318,7 +338,7 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
 #pragma unroll
   for (int j = 0; j < PT; j++) {
     const int64_t s = s0 + ty + 16 * j;
-    if (s >= n) continue;
+    if (s >= s_end) continue;
     // column s lives in the factor block (s < k) or in the update block
     cx<R> *col = (s < k) ? (A + s * ld) : (U + p * ustride + f.uofs + (s - k) * b);
     const int64_t roff = (s < k) ? 0 : k;
@@ -327,6 +347,34 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
       const int64_t r = r0 + tx + 16 * i;
       if (r < n && r >= s) col[r - roff] = col[r - roff] - acc[i][j];
     }
+  }
+}
+
+// Row-major copy of one kKB block of pivot columns for the tensor-core
+// trailing update: for the front of task (f, prow, t0, kb), rows t0..n-1 of
+// columns j0 = t0 - kb .. t0 - 1 go to rows prow + r of Pc (row pitch kKB,
+// columns kb..kKB-1 zero).  A CTA transposes 32 rows through shared memory.
+__global__ void __launch_bounds__(256) k_panel_copy(const c64 *__restrict__ L, int64_t lstride,
+                                                    const FrontDev *__restrict__ F, const int4 *__restrict__ tasks,
+                                                    c64 *__restrict__ Pc, int64_t pstride) {
+  const int4 tk = tasks[blockIdx.y];
+  const FrontDev f = F[tk.x];
+  const int p = blockIdx.z;
+  const int64_t t0 = tk.z, kb = tk.w, j0 = t0 - kb;
+  const int64_t r0 = t0 + int64_t(blockIdx.x) * 32;
+  if (r0 >= f.n) return;
+  __shared__ c64 tile[kKB][33];
+  const c64 *A = L + p * lstride + f.lofs;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
+  for (int c = wq; c < kKB; c += 8) {
+    const int64_t r = r0 + lane;
+    tile[c][lane] = (c < kb && r < f.n) ? A[(j0 + c) * f.ld + r] : mk<float>(0.f, 0.f);
+  }
+  __syncthreads();
+  c64 *out = Pc + p * pstride + (int64_t(tk.y) + r0) * kKB;
+  for (int idx = tid; idx < 32 * kKB; idx += 256) {
+    const int rr = idx / kKB, c = idx % kKB;
+    if (r0 + rr < f.n) out[int64_t(rr) * kKB + c] = tile[c][rr];
   }
 }
 
@@ -394,8 +442,15 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
                                        ea_col + lv.ea_beg[sl]);
     if (g_prof) g_prof->end(KC_EXTEND_ADD, s);
   }
-  // 4. blocked partial LDL^T
-  for (int step = 0; step < (int)lv.steps.size(); step++) {
+  // 4. blocked partial LDL^T.  With tc_update (FP32) the pivots go in blocks of
+  //    kKB: each 32-wide panel step updates only the rest of its block, and
+  //    after the block's last step the rest of the trailing part gets the
+  //    block's rank-kKB update on the tensor cores (from a row-major copy of
+  //    the block's rows below it).
+  constexpr int kPer = kKB / kNB;
+  const bool tc = tc_update && std::is_same<R, float>::value && !lv.upd.empty();
+  const int nsteps = (int)lv.steps.size();
+  for (int step = 0; step < nsteps; step++) {
     const StepDims &sd = lv.steps[step];
     dim3 gp(sd.panel_tiles, sd.nfronts, m);
     if (g_prof) g_prof->begin(KC_PANEL, s);
@@ -403,12 +458,25 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
     k_panel<R, kNB, kPanelRT><<<gp, kPanelRT, 0, s>>>(L, lstride, F, lv.fronts, step, dscr, linv, istride,
                                                       status);
     if (g_prof) g_prof->end(KC_PANEL, s);
-    dim3 gu(sd.update_tiles, sd.nfronts, m);
+    dim3 gu(tc ? sd.update_tiles_blk : sd.update_tiles, sd.nfronts, m);
     if (g_prof) g_prof->begin(KC_UPDATE, s);
     tem::count_launch();
     k_update<R, kNB, UpdateTile<R>::TM><<<gu, 256, 0, s>>>(L, lstride, U, ustride, F, lv.fronts, step,
-                                                            dscr);
+                                                            dscr, tc ? kKB : 0);
     if (g_prof) g_prof->end(KC_UPDATE, s);
+    if constexpr (std::is_same<R, float>::value) {
+      if (tc && ((step + 1) % kPer == 0 || step + 1 == nsteps)) {
+        const UpdBlock &ub = lv.upd[step / kPer];
+        if (ub.ncopy > 0) {
+          dim3 gc(ub.copy_tiles, ub.ncopy, m);
+          if (g_prof) g_prof->begin(KC_UPDATE_TC, s);
+          tem::count_launch();
+          k_panel_copy<<<gc, 256, 0, s>>>(L, lstride, F, ub.copies, Pc, pstride);
+          launch_tc_update(*this, ub, s);
+          if (g_prof) g_prof->end(KC_UPDATE_TC, s);
+        }
+      }
+    }
   }
 }
 

@@ -14,6 +14,7 @@ constexpr int kNB = 32;        // pivot block width of the blocked LDL^T and the
 constexpr int kPanelRT = 128;  // panel rows per CTA
 constexpr int kSB = 256;       // super-block of the solves' pivot blocks (multiple of kNB)
 constexpr int kSplitK = 512;   // inner-dimension chunk of one super-block product task
+constexpr int kKB = 128;       // FP32 factor: columns of one block of the tensor-core trailing update
 
 template <typename R>
 struct UpdateTile;
@@ -48,7 +49,8 @@ struct SolveTile<double> {
 struct StepDims {
   int nfronts;        // fronts of the level with k > step*NB (a prefix: sorted by k desc)
   int panel_tiles;
-  int update_tiles;
+  int update_tiles;   // trailing update of the whole trailing triangle
+  int update_tiles_blk;  // trailing update restricted to the step's kKB block (tensor-core factor)
   int fwd_tiles;
   int bwd_tiles;
 };
@@ -86,6 +88,22 @@ struct SimtTask {
 //   BWD21  Y[c0+c]      = Dinv_c X[c0+c] - sum_i L21[i][c] X[rows_i]   (store)
 //   TRI_B  X[c0+c]      = sum_i T11[i][c] Y[c0+i]              (store)
 enum ProdMode { PM_TRI_F = 0, PM_FWD21 = 1, PM_BWD21 = 2, PM_TRI_B = 3, PM_COUNT = 4 };
+// The same kernel's trailing update of the FP32 factorisation (Algorithm 1, factorise):
+//   F[r][s] -= sum_c L[r][j0 + c] D_c L[s][j0 + c],  c < kb (one kKB block), r >= s >= t0 = j0 + kb,
+// into the factor block (s < k) or the update block (s >= k).  TcTask fields in this mode:
+//   map = front, x0 = panel-copy row of front row 0 (A row = x0 + y0 + m), y0 = first row r0 of the
+//   tile, kdim = kb, mrows = rows of the tile, bbase = first column s0 (even), obase = j0,
+//   mfirst = t0 - s0 (leading columns left alone), kfirst = 0.
+constexpr int PM_UPD = 4;
+
+// The tensor-core trailing update after one kKB block of every front of a level.
+struct UpdBlock {
+  const TcTask *tasks = nullptr;   // 128-row x 32-column tiles (all fronts of the level)
+  int ntask = 0;
+  const int4 *copies = nullptr;    // (front, panel-copy row of front row 0, t0, kb): rows t0..n-1 copied
+  int ncopy = 0;
+  int copy_tiles = 0;              // 32-row tiles of the largest n - t0
+};
 
 // One tile task of the in-place inversion of L11 (merge of two diagonal
 // blocks A = [a0, a0+s), C = [a0+s, a0+s+sc)): 64 x 64 tile (ti, tj) of the
@@ -132,6 +150,8 @@ struct LevelDev {
   const int4 *rcopy = nullptr;
   int n_rcopy = 0;
   int max_k = 0;   // largest pivot count of the level's fronts
+  // FP32 factorisation on the tensor cores: one entry per kKB block of pivots
+  std::vector<UpdBlock> upd;
 };
 
 template <typename R>
@@ -163,6 +183,12 @@ struct FactorPlan {
   cx<R> *T11R = nullptr, *L21T = nullptr;   // row-major copies for the tensor-core products
   int64_t t11r_stride = 0, l21t_stride = 0;
   const int64_t *t11r_ofs = nullptr, *l21t_ofs = nullptr;   // per front
+  // FP32 trailing updates on the tensor cores (kKB blocks): row-major panel copies and tensor maps
+  bool tc_update = false;
+  cx<R> *Pc = nullptr;              // [m][prows][kKB] panel copy
+  int64_t pstride = 0;              // prows * kKB
+  const void *cmaps = nullptr;      // per front: column blocks of the factor store (B operand)
+  const void *pcmap = nullptr;      // the panel copy (A operand)
   void level(int h, const LevelDev &lv, cudaStream_t s);
   void invert_level(const LevelDev &lv, cudaStream_t s);
 };
@@ -199,6 +225,8 @@ struct SolvePlan {
 
 // FP32 front products (solve_tc.cu): tensor cores (P.use_tc) or SIMT.
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s);
+// Tensor-core trailing update of one kKB block of a level's fronts (solve_tc.cu).
+void launch_tc_update(const FactorPlan<float> &P, const UpdBlock &ub, cudaStream_t s);
 
 // Resident CTAs per SM of the tensor-core product kernel (0 before its first launch).
 int tc_ctas_per_sm();
@@ -231,6 +259,10 @@ struct VecBuf {
   int64_t rows;
 };
 std::string build_vector_maps(const std::vector<VecBuf> &bufs, int gather, int nrhs, int m, void **out);
+// Maps for it: per front a map over its column-major factor block (boxes of 32 complex rows x 16
+// columns), and one over the panel copy [m][prows][kKB] (boxes of 128 rows x 16 complex).
+std::string build_update_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, const c64 *Pc,
+                              int64_t prows, int m, void **cmaps, void **pcmap);
 
 void launch_sigma(const double *logs, const int32_t *ptet, int64_t P, double *sigma, cudaStream_t s);
 // mval[z] = sum over the contributions idx of entry z: sigma[idx / per] * me1[idx]
@@ -343,7 +375,7 @@ void launch_lsqr_scalars(LsqrScalars *sc, int which, cudaStream_t s);
 // Kernel classes that can be timed individually with CUDA events.
 enum KernelClass {
   KC_UPDATE = 0, KC_PANEL, KC_FWD, KC_BWD, KC_BWD_UPD, KC_EXTEND_ADD, KC_FWD21, KC_FWD_SB, KC_BWD_SB, KC_INVERT, KC_RESIDUAL, KC_REFINE_VEC, KC_JACOBIAN,
-  KC_NODAL, KC_NODAL_RHS, KC_NODAL_SWEEP, KC_NODAL_APPLY,
+  KC_NODAL, KC_NODAL_RHS, KC_NODAL_SWEEP, KC_NODAL_APPLY, KC_UPDATE_TC,
   KC_COUNT
 };
 struct Profiler {

@@ -69,6 +69,11 @@ struct ProdArgs {
   DevStatus *st;
   uint32_t wait_iter;   // limits of the pipeline waits (polls, ns); the drains after an abort keep the defaults
   uint64_t wait_ns;
+  // PM_UPD (trailing update of the factorisation): fronts, factor store and update arena
+  const FrontDev *F;
+  c64 *Lw;
+  c64 *Uw;
+  int64_t ustride;
 };
 
 // An item: task of pole p, RHS chunk ch (items are numbered per CTA).
@@ -255,8 +260,14 @@ __device__ void ki_loader(const ProdArgs &a, KiShared &sh, int lane) {
         sh.kval[slot] = min(KI_K, t.kdim - k0);
         sh.kfst[slot] = max(0, int(t.kfirst) - k0);
         tc::mbar_arrive_expect_tx(&sh.rawfull[slot], (128 * 32 + KI_K * 64) * 4);
-        tc::tma_load_3d(sh.sl[slot].A, a.tmaps + t.map, t.x0 + 2 * k0, t.y0, it.p, &sh.rawfull[slot]);
-        if (!kGather) tc::tma_load_3d(sh.sl[slot].Xr, a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
+        if (MODE == PM_UPD) {
+          // A: rows of the panel copy; B: columns j0 + k0 .. of the factor store, rows s0 .. s0 + 31
+          tc::tma_load_3d(sh.sl[slot].A, a.bmap, 2 * k0, t.x0 + t.y0, it.p, &sh.rawfull[slot]);
+          tc::tma_load_3d(sh.sl[slot].Xr, a.tmaps + t.map, 2 * t.bbase, t.obase + k0, it.p, &sh.rawfull[slot]);
+        } else {
+          tc::tma_load_3d(sh.sl[slot].A, a.tmaps + t.map, t.x0 + 2 * k0, t.y0, it.p, &sh.rawfull[slot]);
+          if (!kGather) tc::tma_load_3d(sh.sl[slot].Xr, a.bmap, 64 * it.ch, t.bbase + k0, it.p, &sh.rawfull[slot]);
+        }
       }
       if (kGather) {
         __syncwarp();   // the slot's byte count is posted before its row gathers are issued
@@ -280,6 +291,14 @@ __device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
     if (!nxt.valid) break;
     const Item it = ki_begin(nxt);
     nxt = ki_item(a, j + 1);
+    // PM_UPD: the B operand is D_c L[s][c]; D_c sits on the diagonal of the factor block
+    const c64 *dg = nullptr;
+    int64_t dstep = 0;
+    if (MODE == PM_UPD && it.nch > 0) {
+      const FrontDev f = a.F[it.t.map];
+      dstep = int64_t(f.ld) + 1;
+      dg = a.L + int64_t(it.p) * a.lstride + f.lofs + int64_t(it.t.obase) * dstep;
+    }
 #pragma unroll 1
     for (int c = 0; c < it.nch; c++, g++) {
       const int slot = g % KI_SLOTS;
@@ -312,6 +331,14 @@ __device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
       // inner indices 8w..8w+7 = complex rows i = 4w..4w+3
       {
         const int kv = sh.kval[slot], kf = sh.kfst[slot];
+        c64 dq[4];
+        if (MODE == PM_UPD) {
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int i = 4 * w + q;
+            dq[q] = i < kv ? dg[int64_t(c * KI_K + i) * dstep] : mk<float>(0.f, 0.f);
+          }
+        }
 #pragma unroll
         for (int half = 0; half < 2; half++) {
           const int n = 32 * half + l, jr = n >> 1;
@@ -321,7 +348,12 @@ __device__ void ki_producer(const ProdArgs &a, KiShared &sh, int tid) {
             const int i = 4 * w + q;
             const float2 x = *reinterpret_cast<const float2 *>(S.Xr + i * 64 + 2 * jr);
             const bool in = i < kv && i >= kf;
-            const float re = in ? x.x : 0.f, im = in ? x.y : 0.f;
+            float re = in ? x.x : 0.f, im = in ? x.y : 0.f;
+            if (MODE == PM_UPD) {
+              const c64 dx = dq[q] * mk<float>(re, im);
+              re = dx.x;
+              im = dx.y;
+            }
             r[2 * q] = (n & 1) ? im : re;
             r[2 * q + 1] = (n & 1) ? re : -im;
           }
@@ -408,6 +440,24 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     tc::mbar_arrive(&sh.acce[buf]);
     const int m = e;
     if (m >= it.t.mrows) continue;
+    if (MODE == PM_UPD) {
+      // F[r][s] -= acc for the tile's columns s >= t0 with r >= s: one column per step, the warp's
+      // 32 lanes on 32 consecutive rows of it
+      const FrontDev f = a.F[it.t.map];
+      const int64_t r = int64_t(it.t.y0) + m, k = f.k, n = f.n;
+      c64 *lp = a.Lw + int64_t(it.p) * a.lstride + f.lofs;
+      c64 *up = a.Uw + int64_t(it.p) * a.ustride + f.uofs;
+      const int q0 = int(it.t.mfirst);
+#pragma unroll
+      for (int q = 0; q < 32; q++) {   // fully unrolled: v stays in registers
+        const int64_t sc = int64_t(it.t.bbase) + q;
+        if (q < q0 || sc >= n || sc > r) continue;
+        c64 *dst = sc < k ? lp + sc * f.ld + r : up + (sc - k) * (n - k) + (r - k);
+        const c64 o = *dst;
+        *dst = mk<float>(o.x - v[2 * q], o.y - v[2 * q + 1]);
+      }
+      continue;
+    }
     const int ncols = min(32, a.nrhs - it.ch * 32);
     const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
     const int64_t row = MODE == PM_FWD21 ? int64_t(__ldg(a.rows + it.t.obase + m)) : int64_t(it.t.obase) + m;
@@ -571,7 +621,7 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
     tem::count_launch();
     g_tc_launches.fetch_add(1, std::memory_order_relaxed);
     k_tc_kint<MODE><<<grid, NTHR, kKiSmem, s>>>(a);
-  } else {
+  } else if constexpr (MODE != PM_UPD) {
     dim3 g(a.ntask_simt, a.np * a.nchunk);
     tem::count_launch();
     g_simt_launches.fetch_add(1, std::memory_order_relaxed);
@@ -586,6 +636,30 @@ void set_tc_wait_limit(uint32_t polls, uint64_t ns) {
   g_wait_ns = ns;
 }
 int64_t prod_launches(bool tensor_cores) { return (tensor_cores ? g_tc_launches : g_simt_launches).load(); }
+
+void launch_tc_update(const FactorPlan<float> &P, const UpdBlock &ub, cudaStream_t s) {
+  if (ub.ntask == 0 || P.m == 0) return;
+  ProdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.L = P.L;
+  a.lstride = P.lstride;
+  a.tasks = ub.tasks;
+  a.ntask = ub.ntask;
+  a.nrhs = 32;
+  a.nchunk = 1;
+  a.np = P.m;
+  a.pmap = nullptr;
+  a.st = P.status;
+  a.wait_iter = g_wait_iter;
+  a.wait_ns = g_wait_ns;
+  a.tmaps = static_cast<const CUtensorMap *>(P.cmaps);   // B: per front, its column-major block
+  a.bmap = static_cast<const CUtensorMap *>(P.pcmap);    // A: the panel copy
+  a.F = P.F;
+  a.Lw = P.L;
+  a.Uw = P.U;
+  a.ustride = P.ustride;
+  run_mode<PM_UPD>(a, nullptr, true, s);
+}
 
 void launch_prod(int mode, const SolvePlan<float> &P, const LevelDev &lv, cudaStream_t s) {
   // The tensor-core kernel loads B rows by TMA, which needs 16-byte rows (an
@@ -757,6 +831,68 @@ std::string build_vector_maps(const std::vector<VecBuf> &bufs, int gather, int n
     return "copy of tensor maps failed";
   }
   *out = d;
+  return "";
+}
+
+// Maps of the tensor-core trailing update: per front, 3-D over its column-major
+// factor block (floats along a column: 2 n; columns: k; poles), boxes of 64
+// floats (32 complex rows) x 16 columns, no swizzle (the B rows of a chunk);
+// and one 3-D map over the panel copy (floats along a row: 2 kKB; rows; poles),
+// boxes of 32 floats x 128 rows with the 128-byte swizzle (the A operand, like
+// the solves' row-major copies).  Entries outside the dims read as zero.
+std::string build_update_maps(const std::vector<FrontGeom> &fronts, const c64 *L, int64_t lstride, const c64 *Pc,
+                              int64_t prows, int m, void **cmaps, void **pcmap) {
+  *cmaps = *pcmap = nullptr;
+  EncodeTiledFn encode = nullptr;
+  {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return "cuTensorMapEncodeTiled is not available from the driver";
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  std::vector<CUtensorMap> maps(std::max<size_t>(1, fronts.size()));
+  memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+  for (size_t i = 0; i < fronts.size(); i++) {
+    const FrontGeom &f = fronts[i];
+    if (f.k <= 0) continue;
+    const cuuint64_t dims[3] = {cuuint64_t(2) * f.n, cuuint64_t(f.k), cuuint64_t(m)};
+    const cuuint64_t strides[2] = {cuuint64_t(f.ld) * sizeof(c64), cuuint64_t(lstride) * sizeof(c64)};
+    const cuuint32_t box[3] = {64u, 16u, 1u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(L + f.lofs), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return "cuTensorMapEncodeTiled failed for the column map of front " + std::to_string(i);
+  }
+  CUtensorMap pm;
+  {
+    const cuuint64_t dims[3] = {cuuint64_t(2) * kKB, cuuint64_t(std::max<int64_t>(1, prows)), cuuint64_t(m)};
+    const cuuint64_t strides[2] = {cuuint64_t(kKB) * sizeof(c64),
+                                   cuuint64_t(std::max<int64_t>(1, prows)) * kKB * sizeof(c64)};
+    const cuuint32_t box[3] = {32u, 128u, 1u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(&pm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<c64 *>(Pc), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return "cuTensorMapEncodeTiled failed for the panel-copy map";
+  }
+  void *d = nullptr, *e = nullptr;
+  if (cudaMalloc(&d, maps.size() * sizeof(CUtensorMap)) != cudaSuccess) return "cudaMalloc of tensor maps failed";
+  if (cudaMalloc(&e, sizeof(CUtensorMap)) != cudaSuccess) {
+    cudaFree(d);
+    return "cudaMalloc of tensor maps failed";
+  }
+  if (cudaMemcpy(d, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e, &pm, sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    cudaFree(e);
+    return "copy of tensor maps failed";
+  }
+  *cmaps = d;
+  *pcmap = e;
   return "";
 }
 

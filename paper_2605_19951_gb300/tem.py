@@ -23,7 +23,7 @@ ERRORS = {-1: "TEM_ERR_ARG", -2: "TEM_ERR_OOM", -3: "TEM_ERR_PIVOT", -4: "TEM_ER
 KERNEL_CLASSES = {"update": 0, "panel": 1, "fwd": 2, "bwd": 3, "bwd_upd": 4, "extend_add": 5, "fwd21": 6,
                   "fwd_sb": 7, "bwd_sb": 8, "invert": 9,
                   "residual": 10, "refine_vec": 11, "jacobian": 12, "nodal": 13,
-                  "nodal_rhs": 14, "nodal_sweep": 15, "nodal_apply": 16}
+                  "nodal_rhs": 14, "nodal_sweep": 15, "nodal_apply": 16, "update_tc": 17}
 
 # C declarations, in include/tem.h order: name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -43,6 +43,7 @@ SIGNATURES = {
     "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
+    "tem_set_tc_fronts": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint32, _D]),
     "tem_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_nodal": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -192,6 +193,10 @@ def tem_set_refine_adjoint(ctx, steps):
 
 def tem_set_tensor_cores(ctx, enable):
     _check(ctx, load().tem_set_tensor_cores(ctx, int(bool(enable))))
+
+
+def tem_set_tc_fronts(ctx, enable):
+    _check(ctx, load().tem_set_tc_fronts(ctx, int(bool(enable))))
 
 
 def tem_set_wait_limit(ctx, max_polls, max_seconds):

@@ -419,3 +419,25 @@ def test_timeout_is_a_status(c1):
         assert floored_err(jv, c1.jv).max() <= TOL_JV["fp32r"]
     finally:
         mdl.close()
+
+
+def test_c2_fronts_on_tensor_cores_or_fp32_pipes(c2):
+    """The FP32 factorisation with its trailing updates as rank-128 tcgen05
+    products (the default) and as rank-32 SIMT updates: both refine to the
+    oracle's data, J v and J^T w at the refined tolerance, and the default
+    factorisation launches the tensor-core kernel."""
+    tem = _tem()
+    for tcf in (1, 0):
+        mdl = _model(c2.s, c2.xi, c2.al, "fp32r")
+        try:
+            tem.tem_set_tc_fronts(mdl.ctx, tcf)
+            before = _prod_launches(mdl)[0]
+            mdl.factor(_cuda(c2.m0))
+            launched = _prod_launches(mdl)[0] - before
+            assert (launched > 0) == bool(tcf), (tcf, launched)
+            assert floored_err(mdl.forward().cpu().numpy(), c2.d).max() <= TOL["fp32r"]
+            assert floored_err(mdl.jvp(_cuda(c2.v)).cpu().numpy(), c2.jv).max() <= TOL_JV["fp32r"]
+            jtw = mdl.jtvp(_cuda(c2.w)).cpu().numpy()
+            assert np.linalg.norm(jtw - c2.jtw) <= TOL["fp32r"] * np.linalg.norm(c2.jtw)
+        finally:
+            mdl.close()
