@@ -88,6 +88,7 @@ typedef struct tem_stats {
   int64_t nnz_l_nodal;   /* FP32 mode: stored factor entries of the nodal Laplacian */
   int32_t nodal;         /* FP32 mode: 1 = gradient-space correction on */
   int32_t reserved0;
+  int64_t tc_update_launches; /* FP32 factor trailing updates run on the tensor cores, library-wide since load */
 } tem_stats;
 
 /* Create a context on the current CUDA device.  precision: TEM_FP64 or

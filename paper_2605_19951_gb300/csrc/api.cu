@@ -1443,6 +1443,7 @@ int tem_info(tem_ctx *c, tem_stats *o) {
   o->n_nodes = c->ns.N;
   o->nnz_l_nodal = c->ns.sym.nnz_l;
   o->nodal = c->precision != TEM_FP64 && c->use_nodal ? 1 : 0;
+  o->tc_update_launches = update_launches();
   return TEM_OK;
 }
 

@@ -234,6 +234,8 @@ int tc_ctas_per_sm();
 void set_tc_wait_limit(uint32_t polls, uint64_t ns);
 // FP32 solve-product launches on the tensor cores (true) or the FP32 pipes, library-wide.
 int64_t prod_launches(bool tensor_cores);
+// Tensor-core trailing-update launches of the FP32 factorisations, library-wide.
+int64_t update_launches();
 // Tensor maps of every front's factor block (4 per front, index 4 f + mode)
 // in a new device array (*out, cudaFree by the caller); "" on success.
 struct FrontGeom {

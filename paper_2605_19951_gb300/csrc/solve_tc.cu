@@ -595,7 +595,7 @@ namespace {
 int g_tc_occupancy = 0;
 uint32_t g_wait_iter = kWaitIter;   // pipeline-wait limits (tests of the timeout status shorten them)
 uint64_t g_wait_ns = 1000000000ull;
-std::atomic<int64_t> g_tc_launches{0}, g_simt_launches{0};
+std::atomic<int64_t> g_tc_launches{0}, g_simt_launches{0}, g_upd_launches{0};
 
 template <int MODE>
 void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t s) {
@@ -619,7 +619,7 @@ void run_mode(const ProdArgs &a, const SimtTask *simt, bool use_tc, cudaStream_t
     const int64_t total = int64_t(a.ntask) * a.np * a.nchunk;
     const int grid = int(total < grid_max ? total : grid_max);
     tem::count_launch();
-    g_tc_launches.fetch_add(1, std::memory_order_relaxed);
+    (MODE == PM_UPD ? g_upd_launches : g_tc_launches).fetch_add(1, std::memory_order_relaxed);
     k_tc_kint<MODE><<<grid, NTHR, kKiSmem, s>>>(a);
   } else if constexpr (MODE != PM_UPD) {
     dim3 g(a.ntask_simt, a.np * a.nchunk);
@@ -636,6 +636,7 @@ void set_tc_wait_limit(uint32_t polls, uint64_t ns) {
   g_wait_ns = ns;
 }
 int64_t prod_launches(bool tensor_cores) { return (tensor_cores ? g_tc_launches : g_simt_launches).load(); }
+int64_t update_launches() { return g_upd_launches.load(); }
 
 void launch_tc_update(const FactorPlan<float> &P, const UpdBlock &ub, cudaStream_t s) {
   if (ub.ntask == 0 || P.m == 0) return;

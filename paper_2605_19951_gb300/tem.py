@@ -66,7 +66,8 @@ class TemStats(ctypes.Structure):
                 ("min_pivot_abs", _D), ("nnz_l11", _I64), ("n_solve_launch", _I64),
                 ("pole_solves", _I64), ("solve_calls", _I64), ("tc_ctas_per_sm", _I32), ("refine_steps_adjoint", _I32),
                 ("tc_prod_launches", _I64), ("simt_prod_launches", _I64),
-                ("n_nodes", _I64), ("nnz_l_nodal", _I64), ("nodal", _I32), ("reserved0", _I32)]
+                ("n_nodes", _I64), ("nnz_l_nodal", _I64), ("nodal", _I32), ("reserved0", _I32),
+                ("tc_update_launches", _I64)]
 
 
 class TemError(RuntimeError):

@@ -431,9 +431,9 @@ def test_c2_fronts_on_tensor_cores_or_fp32_pipes(c2):
         mdl = _model(c2.s, c2.xi, c2.al, "fp32r")
         try:
             tem.tem_set_tc_fronts(mdl.ctx, tcf)
-            before = _prod_launches(mdl)[0]
+            before = mdl.info()["tc_update_launches"]
             mdl.factor(_cuda(c2.m0))
-            launched = _prod_launches(mdl)[0] - before
+            launched = mdl.info()["tc_update_launches"] - before
             assert (launched > 0) == bool(tcf), (tcf, launched)
             assert floored_err(mdl.forward().cpu().numpy(), c2.d).max() <= TOL["fp32r"]
             assert floored_err(mdl.jvp(_cuda(c2.v)).cpu().numpy(), c2.jv).max() <= TOL_JV["fp32r"]
