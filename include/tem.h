@@ -25,7 +25,9 @@
  *  - The library owns every factor, symbolic table and work buffer; all are
  *    released by tem_destroy().
  *  - Device work is issued on the stream given to tem_create(); calls return
- *    after the stream is synchronised (status words are read back).
+ *    after the stream is synchronised (status words are read back), unless
+ *    the context is asynchronous (tem_set_async): then calls return once
+ *    their work is issued and tem_status reports the device status.
  *  - Calls out of order (e.g. tem_jvp before tem_forward) return
  *    TEM_ERR_STATE.  Sizes that do not match the context return TEM_ERR_ARG.
  *  - Data vectors are laid out d[x][r][j] (transmitter, receiver, time),
@@ -216,6 +218,25 @@ int tem_set_refine_adjoint(tem_ctx *ctx, int32_t steps);
  * tensor-core completion wait that gives up makes the call return
  * TEM_ERR_TIMEOUT.  No effect in TEM_FP64 mode. */
 int tem_set_tensor_cores(tem_ctx *ctx, int enable);
+
+/* Asynchronous mode (default 0): tem_factor, tem_forward, tem_jvp, tem_jtvp,
+ * tem_lsqr and tem_lsqr_noalloc return as soon as their work is issued on the
+ * context's stream, without synchronising or reading the device status, so
+ * that a caller can overlap them with its own work or capture them into a
+ * CUDA graph (stream capture on the context's stream) and replay it.
+ * Arguments are checked as usual; device-side failures (a pivot underflow, an
+ * expired tensor-core wait) are reported by the next tem_status.  Calls that
+ * allocate on first use (tem_factor's first call allocates the numeric
+ * storage, tem_lsqr's first call its work vectors) must have run once before
+ * a capture.  A refinement tolerance (tem_set_refine tol > 0) needs host
+ * reads and is refused (TEM_ERR_ARG) in this mode.  Switching it off
+ * synchronises the stream. */
+int tem_set_async(tem_ctx *ctx, int enable);
+
+/* Synchronise the context's stream and report the device status words of the
+ * work issued so far: TEM_ERR_TIMEOUT (cleared once reported), TEM_ERR_PIVOT
+ * (the last tem_factor failed; solves need a new tem_factor), else TEM_OK. */
+int tem_status(tem_ctx *ctx);
 
 /* TEM_FP32_REFINED mode: the trailing updates of the dense fronts (Algorithm 1,
  * factorise) on the tensor cores (default 1) or on the FP32 pipes (0).  On the

@@ -147,6 +147,7 @@ struct tem_ctx {
   NodalMesh nodal;
   bool use_tc = true;                     // FP32 mode: front products on tcgen05
   bool tc_fronts = true;                  // FP32 mode: trailing updates of the fronts on tcgen05
+  bool async = false;                     // calls return once issued; tem_status reads the status words
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -281,6 +282,19 @@ int check_solve_status(tem_ctx *c) {
     return fail(c, TEM_ERR_TIMEOUT, "a tensor-core completion wait expired in a solve");
   }
   return TEM_OK;
+}
+
+// End of a call: in the default mode synchronise the stream and read the
+// solve status words; in asynchronous mode only check that the launches were
+// accepted (the caller reads the status with tem_status).
+int finish(tem_ctx *c, const char *where) {
+  if (c->async) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return TEM_OK;
+  }
+  TRY(sync(c, where));
+  return check_solve_status(c);
 }
 
 struct ProfScope {
@@ -1178,12 +1192,7 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
     launch_split_real(c->kval, c->kdf, (int64_t)M.kval.size(), s);
     launch_split_real(c->mval, c->mdf, (int64_t)M.kval.size(), s);
   }
-  DevStatus init{};
-  init.pivot_fail = 0;
-  init.pivot_front = -1;
-  double big = 1e308;
-  memcpy(&init.min_pivot_bits, &big, sizeof(double));
-  CK(cudaMemcpyAsync(c->status, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+  launch_status_init(c->status, s);   // a kernel, not a host copy: the call stays capturable
   if (c->precision == TEM_FP64) {
     factor_sys<double>(c, c->es);
   } else {
@@ -1195,9 +1204,15 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
       factor_sys<float>(c, c->ns);
     }
   }
+  c->state &= ~(ST_FACTORED | ST_FORWARD);
+  if (c->async) {   // a pivot failure is reported by tem_status
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "tem_factor");
+    c->state |= ST_FACTORED;
+    return TEM_OK;
+  }
   CK(cudaMemcpyAsync(&c->status_h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   TRY(sync(c, "tem_factor"));
-  c->state &= ~(ST_FACTORED | ST_FORWARD);
   if (c->status_h.pivot_fail) {
     char buf[160];
     snprintf(buf, sizeof buf, "pivot underflow in front %d", c->status_h.pivot_front);
@@ -1220,8 +1235,7 @@ int tem_forward(tem_ctx *c, double *d) {
     CK(cudaMemcpyAsync(c->gdf, c->xdf, sizeof(float4) * c->m * N * c->nrhs, cudaMemcpyDeviceToDevice, s));
   launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->g, d, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K, s);
   CK(cudaMemcpyAsync(c->d_cur, d, sizeof(double) * c->n_tx * c->n_rx * c->K, cudaMemcpyDeviceToDevice, s));
-  TRY(sync(c, "tem_forward"));
-  TRY(check_solve_status(c));
+  TRY(finish(c, "tem_forward"));
   c->state |= ST_FORWARD;
   return TEM_OK;
 }
@@ -1272,8 +1286,7 @@ int tem_jvp(tem_ctx *c, const double *v, double *jv) {
   if (!v || !jv) return fail(c, TEM_ERR_ARG, "NULL vector");
   ProfScope ps(c);
   TRY(jvp_async(c, v, jv));
-  TRY(sync(c, "tem_jvp"));
-  return check_solve_status(c);
+  return finish(c, "tem_jvp");
 }
 
 int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
@@ -1282,8 +1295,7 @@ int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
   if (!w || !jtw) return fail(c, TEM_ERR_ARG, "NULL vector");
   ProfScope ps(c);
   TRY(jtvp_async(c, w, jtw));
-  TRY(sync(c, "tem_jtvp"));
-  return check_solve_status(c);
+  return finish(c, "tem_jtvp");
 }
 
 int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref, double lambda,
@@ -1347,8 +1359,7 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
     launch_lsqr_scalars(sc, 3, s);  // rho, c, s, theta, phi
     launch_lsqr_kernel(4, sc, dm, c->ls_w, c->ls_v, nullptr, P, s);
   }
-  TRY(sync(c, "tem_lsqr"));
-  return check_solve_status(c);
+  return finish(c, "tem_lsqr");
 }
 
 int tem_set_wait_limit(tem_ctx *c, uint32_t max_polls, double max_seconds) {
@@ -1364,6 +1375,33 @@ int tem_set_tensor_cores(tem_ctx *c, int enable) {
   return TEM_OK;
 }
 
+int tem_set_async(tem_ctx *c, int enable) {
+  if (!c) return TEM_ERR_ARG;
+  if (enable && c->refine_tol > 0)
+    return fail(c, TEM_ERR_ARG, "asynchronous calls need a fixed correction count (tem_set_refine tol = 0)");
+  if (c->async && !enable) TRY(sync(c, "tem_set_async"));
+  c->async = enable != 0;
+  return TEM_OK;
+}
+
+int tem_status(tem_ctx *c) {
+  if (!c) return TEM_ERR_ARG;
+  TRY(sync(c, "tem_status"));
+  CK(cudaMemcpy(&c->status_h, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+  if (c->status_h.tc_timeout) {   // reported once
+    CK(cudaMemset(&c->status->tc_timeout, 0, sizeof(int32_t)));
+    c->status_h.tc_timeout = 0;
+    return fail(c, TEM_ERR_TIMEOUT, "a tensor-core completion wait expired");
+  }
+  if (c->status_h.pivot_fail) {
+    c->state &= ~(ST_FACTORED | ST_FORWARD);
+    char buf[160];
+    snprintf(buf, sizeof buf, "pivot underflow in front %d", c->status_h.pivot_front);
+    return fail(c, TEM_ERR_PIVOT, buf);
+  }
+  return TEM_OK;
+}
+
 int tem_set_tc_fronts(tem_ctx *c, int enable) {
   if (!c) return TEM_ERR_ARG;
   if (c->tc_fronts != (enable != 0)) c->state &= ~(ST_FACTORED | ST_FORWARD);   // the next tem_factor decides
@@ -1376,6 +1414,7 @@ int tem_set_refine(tem_ctx *c, int32_t steps, double floor_tau, double tol) {
   if (steps < 0 || steps > 40) return fail(c, TEM_ERR_ARG, "refine steps in 0..40");
   if (!(floor_tau >= 0) || floor_tau > 1.0) return fail(c, TEM_ERR_ARG, "floor_tau in [0, 1]");
   if (!(tol >= 0) || tol > 1.0) return fail(c, TEM_ERR_ARG, "tol in [0, 1]");
+  if (tol > 0 && c->async) return fail(c, TEM_ERR_ARG, "a refinement tolerance reads progress on the host: not in asynchronous mode");
   c->refine = steps;
   c->floor_tau = floor_tau;
   c->refine_tol = tol;
@@ -1615,6 +1654,5 @@ extern "C" int tem_lsqr_noalloc(tem_ctx *c, const double *d_obs, const double *w
     launch_lsqr_scalars(sc, 3, s);
     launch_lsqr_kernel(4, sc, dm, w, v, nullptr, P, s);
   }
-  TRY(sync(c, "tem_lsqr_noalloc"));
-  return check_solve_status(c);
+  return finish(c, "tem_lsqr_noalloc");
 }

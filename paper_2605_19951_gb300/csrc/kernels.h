@@ -363,6 +363,9 @@ void launch_dm_apply_df(const int64_t *inc_ptr, const int32_t *inc_tet, const in
 void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,
                    int64_t rows, double alpha, double beta, cudaStream_t s);
 
+// status words before a factorisation (a kernel, so that the call stays capturable)
+void launch_status_init(DevStatus *st, cudaStream_t s);
+
 // ---- LSQR helpers (ops.cu) ----
 struct LsqrScalars {
   double alpha, beta, rhobar, phibar, rho, c, sn, theta, phi;

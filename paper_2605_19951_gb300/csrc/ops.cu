@@ -656,4 +656,17 @@ template void launch_accumulate<double>(const c128 *, const double *, c128 *, in
 template void launch_progress<float>(const c64 *, const double *, const c128 *, const uint8_t *, double *,
                                      double *, int, const int *, int64_t, int, cudaStream_t);
 
+// Status words before a factorisation: no pivot failure, no timeout, smallest pivot +huge.
+__global__ void k_status_init(DevStatus *st) {
+  st->pivot_fail = 0;
+  st->pivot_front = -1;
+  st->tc_timeout = 0;
+  st->min_pivot_bits = (unsigned long long)__double_as_longlong(1e308);
+}
+
+void launch_status_init(DevStatus *st, cudaStream_t s) {
+  tem::count_launch();
+  k_status_init<<<1, 1, 0, s>>>(st);
+}
+
 }  // namespace tem

@@ -43,6 +43,8 @@ SIGNATURES = {
     "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
+    "tem_set_async": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tem_status": (ctypes.c_int, [_P]),
     "tem_set_tc_fronts": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint32, _D]),
     "tem_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -194,6 +196,14 @@ def tem_set_refine_adjoint(ctx, steps):
 
 def tem_set_tensor_cores(ctx, enable):
     _check(ctx, load().tem_set_tensor_cores(ctx, int(bool(enable))))
+
+
+def tem_set_async(ctx, enable):
+    _check(ctx, load().tem_set_async(ctx, int(bool(enable))))
+
+
+def tem_status(ctx):
+    _check(ctx, load().tem_status(ctx))
 
 
 def tem_set_tc_fronts(ctx, enable):

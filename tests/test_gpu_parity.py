@@ -441,3 +441,46 @@ def test_c2_fronts_on_tensor_cores_or_fp32_pipes(c2):
             assert np.linalg.norm(jtw - c2.jtw) <= TOL["fp32r"] * np.linalg.norm(c2.jtw)
         finally:
             mdl.close()
+
+
+def test_async_calls_capture_into_a_cuda_graph(c1):
+    """Asynchronous mode: tem_forward and a 3-iteration tem_lsqr (all poles x
+    transmitters, refinement and gradient-space corrections included) are
+    captured on the context's stream into one CUDA graph; two replays give the
+    synchronous results (the FWD21 atomics may reorder sums: 1e-9), and
+    tem_status reports a clean device status after each."""
+    tem = _tem()
+    s = c1.s
+    stream = torch.cuda.Stream()
+    mdl = tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, c1.xi, c1.al,
+                    precision=tem.TEM_FP32_REFINED, stream=stream.cuda_stream)
+    try:
+        d_obs = _cuda(c1.d * (1 + 0.03 * np.random.default_rng(3).standard_normal(c1.d.shape)))
+        wd = 1.0 / (0.03 * d_obs.abs() + 1e-4 * d_obs.abs().max())
+        m_ref = _cuda(s.log_sigma())
+        m0 = _cuda(c1.m0)
+        torch.cuda.synchronize()   # inputs made on the default stream, used on the context's
+        with torch.cuda.stream(stream):
+            mdl.factor(m0)
+            d_ref = mdl.forward()
+            dm_ref = mdl.lsqr(d_obs, wd, m_ref, 10.0, 3)
+        stream.synchronize()
+        assert floored_err(d_ref.cpu().numpy(), c1.d).max() <= TOL["fp32r"]
+        tem.tem_set_async(mdl.ctx, 1)
+        d_g = torch.full(mdl.shape, np.nan, dtype=torch.float64, device="cuda")
+        dm_g = torch.full((mdl.P,), np.nan, dtype=torch.float64, device="cuda")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            tem.tem_forward(mdl.ctx, d_g)
+            tem.tem_lsqr(mdl.ctx, d_obs, wd, m_ref, 10.0, 3, dm_g)
+        for _ in range(2):
+            d_g.fill_(np.nan)
+            dm_g.fill_(np.nan)
+            graph.replay()
+            tem.tem_status(mdl.ctx)
+            d, dm = d_g.cpu().numpy(), dm_g.cpu().numpy()
+            assert floored_err(d, d_ref.cpu().numpy()).max() <= 1e-9
+            assert np.linalg.norm(dm - dm_ref.cpu().numpy()) <= 1e-9 * np.linalg.norm(dm_ref.cpu().numpy())
+        tem.tem_set_async(mdl.ctx, 0)
+    finally:
+        mdl.close()
