@@ -184,6 +184,24 @@ int tem_lsqr(tem_ctx *ctx, const double *d_obs, const double *wd,
 int tem_lsqr_noalloc(tem_ctx *ctx, const double *d_obs, const double *wd,
                      const double *m_ref, double lambda, int32_t n_iter, double *dm);
 
+/* Gauss-Newton bookkeeping at the model of the last tem_factor and the data of
+ * the last tem_forward (Section 3, phi; Section 3.3, line search), on the
+ * device: the objective phi = 1/2 ||W_d (d - d_obs)||^2 + lambda R(m) with
+ * R = 1/2 ||W (m - m_ref)||^2 (W^T W = L), and optionally its gradient
+ *   grad = J^T W_d^2 (d - d_obs) + lambda L (m - m_ref)     (one J^T w)
+ * and the directional derivative grad . dm.
+ *   d_obs, wd dev [n_tx][n_rx][n_times]; m_ref dev [P]; grad dev [P] or NULL;
+ *   dm dev [P] or NULL (needs grad); out host [5]: phi, 1/2 ||W_d r||^2, R,
+ *   chi^2 = ||W_d r||^2 / (n_tx n_rx n_times), grad . dm (0 without dm).
+ * Synchronises (the scalars are returned): TEM_ERR_STATE in asynchronous
+ * mode. */
+int tem_gn_eval(tem_ctx *ctx, const double *d_obs, const double *wd, const double *m_ref,
+                double lambda, const double *dm, double *grad, double *out);
+
+/* out = m + eta dm over the parameter cells (the Gauss-Newton trial model,
+ * Section 3.3).  m, dm, out dev [P]; out may alias m. */
+int tem_model_step(tem_ctx *ctx, const double *m, const double *dm, double eta, double *out);
+
 /* TEM_FP32_REFINED mode: refinement corrections per forward and J v solve
  * (default 3) and the conductivity floor of the factored matrices (default
  * 1e-6).

@@ -941,6 +941,21 @@ int alloc_sys(tem_ctx *c, FactorSys &S, bool fp32) {
   return TEM_OK;
 }
 
+int ensure_lsqr_buffers(tem_ctx *c) {
+  if (c->ls_u) return TEM_OK;
+  const int64_t nd = int64_t(c->n_tx) * c->n_rx * c->K, P = c->mesh.P, nf = c->mesh.nf;
+  TRY(dalloc(c, &c->ls_u, nd + nf));
+  TRY(dalloc(c, &c->ls_v, P));
+  TRY(dalloc(c, &c->ls_w, P));
+  TRY(dalloc(c, &c->ls_jv, nd));
+  TRY(dalloc(c, &c->ls_jtw, P));
+  TRY(dalloc(c, &c->ls_tmpd, nd));
+  TRY(dalloc(c, &c->ls_tmpp, P));
+  TRY(dalloc(c, &c->ls_wv, std::max<int64_t>(nf, 1)));
+  TRY(dalloc(c, &c->ls_sc, 1));
+  return TEM_OK;
+}
+
 int ensure_numeric(tem_ctx *c) {
   if (c->es.L) return TEM_OK;
   const bool fp32 = c->precision != TEM_FP64;
@@ -1304,17 +1319,7 @@ int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!d_obs || !wd || !m_ref || !dm || n_iter < 0 || !(lambda >= 0)) return fail(c, TEM_ERR_ARG, "bad LSQR args");
   const int64_t nd = int64_t(c->n_tx) * c->n_rx * c->K, P = c->mesh.P, nf = c->mesh.nf;
-  if (!c->ls_u) {
-    TRY(dalloc(c, &c->ls_u, nd + nf));
-    TRY(dalloc(c, &c->ls_v, P));
-    TRY(dalloc(c, &c->ls_w, P));
-    TRY(dalloc(c, &c->ls_jv, nd));
-    TRY(dalloc(c, &c->ls_jtw, P));
-    TRY(dalloc(c, &c->ls_tmpd, nd));
-    TRY(dalloc(c, &c->ls_tmpp, P));
-    TRY(dalloc(c, &c->ls_wv, std::max<int64_t>(nf, 1)));
-    TRY(dalloc(c, &c->ls_sc, 1));
-  }
+  TRY(ensure_lsqr_buffers(c));
   ProfScope ps(c);
   cudaStream_t s = c->stream;
   const double sl = std::sqrt(lambda);
@@ -1367,6 +1372,49 @@ int tem_set_wait_limit(tem_ctx *c, uint32_t max_polls, double max_seconds) {
   if (max_polls == 0 || !(max_seconds > 0) || max_seconds > 60) return fail(c, TEM_ERR_ARG, "bad wait limit");
   set_tc_wait_limit(max_polls, uint64_t(max_seconds * 1e9));
   return TEM_OK;
+}
+
+
+int tem_gn_eval(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref, double lambda,
+                const double *dm, double *grad, double *out) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
+  if (!d_obs || !wd || !m_ref || !out || !(lambda >= 0) || (dm && !grad)) return fail(c, TEM_ERR_ARG, "bad arguments");
+  if (c->async) return fail(c, TEM_ERR_STATE, "tem_gn_eval returns host scalars: not in asynchronous mode");
+  TRY(ensure_lsqr_buffers(c));
+  ProfScope ps(c);
+  cudaStream_t s = c->stream;
+  const int64_t nd = int64_t(c->n_tx) * c->n_rx * c->K, P = c->mesh.P, nf = c->mesh.nf;
+  double *sums = reinterpret_cast<double *>(c->ls_sc);   // sum t^2, sum (W (m - m_ref))^2, grad . dm
+  CK(cudaMemsetAsync(sums, 0, 3 * sizeof(double), s));
+  double *t = c->ls_tmpd, *t2 = c->ls_jv, *wv = c->ls_wv;
+  launch_gn_res(c->d_cur, d_obs, wd, t, t2, nd, s);
+  launch_dot(t, t, nd, sums, s);
+  launch_csr_mv(c->w_rp, c->w_ci, c->w_val, c->m_cur, wv, nf, 1.0, 0.0, s);
+  launch_csr_mv(c->w_rp, c->w_ci, c->w_val, m_ref, wv, nf, -1.0, 1.0, s);
+  launch_dot(wv, wv, nf, sums + 1, s);
+  if (grad) {
+    // grad phi = J^T W_d^2 (d - d_obs) + lambda W^T W (m - m_ref)
+    TRY(jtvp_async(c, t2, grad));
+    launch_csr_mv(c->wt_rp, c->wt_ci, c->wt_val, wv, grad, P, lambda, 1.0, s);
+    if (dm) launch_dot(grad, dm, P, sums + 2, s);
+  }
+  double h[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(h, sums, sizeof h, cudaMemcpyDeviceToHost, s));
+  TRY(finish(c, "tem_gn_eval"));
+  out[1] = 0.5 * h[0];
+  out[2] = 0.5 * h[1];
+  out[0] = out[1] + lambda * out[2];
+  out[3] = nd > 0 ? h[0] / double(nd) : 0.0;
+  out[4] = h[2];
+  return TEM_OK;
+}
+
+int tem_model_step(tem_ctx *c, const double *m, const double *dm, double eta, double *out) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_MESH) || !m || !dm || !out || !std::isfinite(eta)) return fail(c, TEM_ERR_ARG, "bad arguments");
+  launch_axpy(m, dm, eta, out, c->mesh.P, c->stream);
+  return finish(c, "tem_model_step");
 }
 
 int tem_set_tensor_cores(tem_ctx *c, int enable) {

@@ -363,6 +363,12 @@ void launch_dm_apply_df(const int64_t *inc_ptr, const int32_t *inc_tet, const in
 void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,
                    int64_t rows, double alpha, double beta, cudaStream_t s);
 
+// Gauss-Newton bookkeeping: t = wd (d - d_obs), t2 = wd^2 (d - d_obs); *out += x . y; out = m + eta dm
+void launch_gn_res(const double *d, const double *d_obs, const double *wd, double *t, double *t2, int64_t n,
+                   cudaStream_t s);
+void launch_dot(const double *x, const double *y, int64_t n, double *out, cudaStream_t s);
+void launch_axpy(const double *m, const double *dm, double eta, double *out, int64_t n, cudaStream_t s);
+
 // status words before a factorisation (a kernel, so that the call stays capturable)
 void launch_status_init(DevStatus *st, cudaStream_t s);
 

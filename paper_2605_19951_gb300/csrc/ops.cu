@@ -669,4 +669,58 @@ void launch_status_init(DevStatus *st, cudaStream_t s) {
   k_status_init<<<1, 1, 0, s>>>(st);
 }
 
+// ---- Gauss-Newton bookkeeping (Section 3.3) ----------------------------------
+
+// t = wd (d - d_obs), t2 = wd^2 (d - d_obs)
+__global__ void k_gn_res(const double *__restrict__ d, const double *__restrict__ d_obs,
+                         const double *__restrict__ wd, double *__restrict__ t, double *__restrict__ t2, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double r = wd[i] * (d[i] - d_obs[i]);
+    t[i] = r;
+    t2[i] = wd[i] * r;
+  }
+}
+
+// *out += sum x y
+__global__ void k_dot(const double *__restrict__ x, const double *__restrict__ y, int64_t n, double *out) {
+  double acc = 0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    acc += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); w++) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
+// out = m + eta dm
+__global__ void k_axpy(const double *__restrict__ m, const double *__restrict__ dm, double eta,
+                       double *__restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = m[i] + eta * dm[i];
+}
+
+void launch_gn_res(const double *d, const double *d_obs, const double *wd, double *t, double *t2, int64_t n,
+                   cudaStream_t s) {
+  if (n <= 0) return;
+  tem::count_launch();
+  k_gn_res<<<(unsigned)std::min<int64_t>(div_up(n, 256), 4096), 256, 0, s>>>(d, d_obs, wd, t, t2, n);
+}
+
+void launch_dot(const double *x, const double *y, int64_t n, double *out, cudaStream_t s) {
+  if (n <= 0) return;
+  tem::count_launch();
+  k_dot<<<(unsigned)std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(x, y, n, out);
+}
+
+void launch_axpy(const double *m, const double *dm, double eta, double *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  tem::count_launch();
+  k_axpy<<<(unsigned)std::min<int64_t>(div_up(n, 256), 4096), 256, 0, s>>>(m, dm, eta, out, n);
+}
+
 }  // namespace tem

@@ -41,6 +41,8 @@ SIGNATURES = {
     "tem_jtvp": (ctypes.c_int, [_P, _P, _P]),
     "tem_lsqr": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
+    "tem_gn_eval": (ctypes.c_int, [_P, _P, _P, _P, _D, _P, _P, _P]),
+    "tem_model_step": (ctypes.c_int, [_P, _P, _P, _D, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
     "tem_set_async": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -186,7 +188,20 @@ def tem_lsqr_noalloc(ctx, d_obs, wd, m_ref, lam, n_iter, dm):
                                         _dev(dm)))
 
 
-def tem_set_refine(ctx, steps, floor_tau=1e-4, tol=0.0):
+def tem_gn_eval(ctx, d_obs, wd, m_ref, lam, dm=None, grad=None):
+    """(phi, data term, R, chi2, grad . dm) at the current model and data; fills grad if given."""
+    out = np.zeros(5)
+    _check(ctx, load().tem_gn_eval(ctx, _dev(d_obs), _dev(wd), _dev(m_ref), float(lam),
+                                   None if dm is None else _dev(dm), None if grad is None else _dev(grad),
+                                   out.ctypes.data_as(_P)))
+    return out
+
+
+def tem_model_step(ctx, m, dm, eta, out):
+    _check(ctx, load().tem_model_step(ctx, _dev(m), _dev(dm), float(eta), _dev(out)))
+
+
+def tem_set_refine(ctx, steps, floor_tau=1e-6, tol=0.0):
     _check(ctx, load().tem_set_refine(ctx, int(steps), float(floor_tau), float(tol)))
 
 

@@ -484,3 +484,81 @@ def test_async_calls_capture_into_a_cuda_graph(c1):
         tem.tem_set_async(mdl.ctx, 0)
     finally:
         mdl.close()
+
+
+def _gn_inputs(c1):
+    s = c1.s
+    m_ref = s.log_sigma()
+    # far from the start model; lambda 1 and 4 LSQR iterations keep the GN directions well
+    # determined (two oracle runs whose data differ by 1e-13 stay 1e-13 apart), and lambda cools
+    m_true = m_ref + 3.0 + 0.5 * np.random.default_rng(9).standard_normal(m_ref.shape)
+    from oracle.tem import Oracle
+    o = Oracle(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, c1.xi, c1.al)
+    o.set_model(m_true)
+    d_true = o.forward()
+    d_obs = d_true * (1 + 0.03 * np.random.default_rng(5).standard_normal(d_true.shape))
+    wd = 1.0 / (0.03 * np.abs(d_obs) + 1e-4 * np.abs(d_obs).max())
+    return o, m_ref, d_obs, wd
+
+
+def test_gauss_newton_matches_oracle(c1):
+    """Four Gauss-Newton iterations (Section 3.3: LSQR direction, Armijo line
+    search, lambda cooling) on the library's calls (FP64: tem_factor,
+    tem_forward, tem_lsqr, tem_gn_eval, tem_model_step) against the oracle's
+    own GN loop on the same data: objective, misfit, step lengths, trial
+    counts and lambda per iteration, and the final model.  The line-search
+    branches themselves are pinned on the CPU (tests/test_gn_logic.py)."""
+    from oracle.gn import gauss_newton
+    from paper_2605_19951_gb300.gn import GaussNewton
+    o, m_ref, d_obs, wd = _gn_inputs(c1)
+    W = regulariser(c1.s.xyz, c1.s.tets, c1.s.is_param)
+    m_o, hist_o = gauss_newton(o, W, d_obs, wd, m_ref, m_ref, lam=1.0, n_lsqr=4, n_iter=4, conv_tol=0.4)
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        gn = GaussNewton(mdl, _cuda(d_obs), _cuda(wd), _cuda(m_ref), _cuda(m_ref), lam=1.0, n_lsqr=4,
+                         conv_tol=0.4)
+        hist = gn.run(4)
+        m_g = gn.m.cpu().numpy()
+    finally:
+        mdl.close()
+    assert len(hist) == len(hist_o) == 4
+    assert hist_o[-1]["lam"] < hist_o[0]["lam"]                          # lambda cooled
+    assert min(abs(x) for h in hist_o for x in h["margins"]) > 1e-3     # no Armijo test near its bound
+    for a, b in zip(hist, hist_o):
+        assert a["trials"] == b["trials"] and a["lam"] == b["lam"], (a, b)
+        for k in ("phi0", "phi", "chi2", "eta"):
+            assert abs(a[k] - b[k]) <= 1e-8 * abs(b[k]), (k, a[k], b[k])
+    assert hist[-1]["phi"] < hist[0]["phi0"]
+    assert np.linalg.norm(m_g - m_o) <= 1e-8 * np.linalg.norm(m_o)
+
+
+def test_gauss_newton_checkpoint_resume(c1, tmp_path):
+    """The GN state written after every iteration restarts a run: two
+    iterations in one run equal one iteration, a checkpoint, and one more
+    iteration resumed from it in a fresh context."""
+    from paper_2605_19951_gb300.gn import GaussNewton
+    _, m_ref, d_obs, wd = _gn_inputs(c1)
+    args = (_cuda(d_obs), _cuda(wd), _cuda(m_ref))
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        gn = GaussNewton(mdl, *args, _cuda(m_ref), lam=1.0, n_lsqr=4, conv_tol=0.4)
+        gn.run(2)
+        m_straight = gn.m.cpu().numpy()
+    finally:
+        mdl.close()
+    ck = str(tmp_path / "gn_state.npz")
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        GaussNewton(mdl, *args, _cuda(m_ref), lam=1.0, n_lsqr=4, conv_tol=0.4, checkpoint=ck).run(1)
+    finally:
+        mdl.close()
+    mdl = _model(c1.s, c1.xi, c1.al, "fp64")
+    try:
+        gn = GaussNewton.resume(ck, mdl, *args, n_lsqr=4, conv_tol=0.4)
+        assert gn.it == 1 and len(gn.history) == 1
+        gn.run(1)
+        assert gn.it == 2
+        m_resumed = gn.m.cpu().numpy()
+    finally:
+        mdl.close()
+    assert np.linalg.norm(m_resumed - m_straight) <= 1e-10 * np.linalg.norm(m_straight)
