@@ -256,6 +256,25 @@ int tem_set_async(tem_ctx *ctx, int enable);
  * (the last tem_factor failed; solves need a new tem_factor), else TEM_OK. */
 int tem_status(tem_ctx *ctx);
 
+/* A batch of independent surveys (uneven meshes, each its own context):
+ * for every context i, in order, the operations of `ops` on its own stream:
+ *   TEM_BATCH_FACTOR  tem_factor(ctx[i], log_sigma[i])
+ *   TEM_BATCH_FORWARD tem_forward(ctx[i], d[i])
+ *   TEM_BATCH_JTVP    tem_jtvp(ctx[i], w[i], jtw[i])
+ * issued asynchronously, with no synchronisation between contexts, so that
+ * contexts on different streams run concurrently on the GPU.  Arrays are per
+ * context and follow the single calls' layouts (NULL where an operation is
+ * not requested).  Contexts in asynchronous mode stay unsynchronised (read
+ * their status with tem_status; the whole call can then be captured into one
+ * CUDA graph, whose branches are the contexts' streams); for the others the
+ * call synchronises each and returns the first failing status.  Each context
+ * must have run the requested calls once before a capture (allocation). */
+#define TEM_BATCH_FACTOR 1
+#define TEM_BATCH_FORWARD 2
+#define TEM_BATCH_JTVP 4
+int tem_batch(tem_ctx **ctx, int32_t n, int32_t ops, const double *const *log_sigma, double *const *d,
+              const double *const *w, double *const *jtw);
+
 /* TEM_FP32_REFINED mode: the trailing updates of the dense fronts (Algorithm 1,
  * factorise) on the tensor cores (default 1) or on the FP32 pipes (0).  On the
  * tensor cores the pivots of a front go in blocks of 128: each 32-wide panel

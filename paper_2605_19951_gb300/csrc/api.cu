@@ -1450,6 +1450,36 @@ int tem_status(tem_ctx *c) {
   return TEM_OK;
 }
 
+int tem_batch(tem_ctx **ctx, int32_t n, int32_t ops, const double *const *log_sigma, double *const *d,
+              const double *const *w, double *const *jtw) {
+  if (!ctx || n <= 0 || (ops & ~(TEM_BATCH_FACTOR | TEM_BATCH_FORWARD | TEM_BATCH_JTVP)) || ops == 0)
+    return fail(nullptr, TEM_ERR_ARG, "tem_batch: bad contexts or operations");
+  for (int i = 0; i < n; i++) {
+    tem_ctx *c = ctx[i];
+    if (!c) return fail(nullptr, TEM_ERR_ARG, "tem_batch: NULL context");
+    if (((ops & TEM_BATCH_FACTOR) && !(log_sigma && log_sigma[i])) || ((ops & TEM_BATCH_FORWARD) && !(d && d[i])) ||
+        ((ops & TEM_BATCH_JTVP) && !(w && w[i] && jtw && jtw[i])))
+      return fail(c, TEM_ERR_ARG, "tem_batch: missing array");
+  }
+  // every context's calls, issued asynchronously on its own stream (no synchronisation in between)
+  std::vector<char> was(n);
+  int st = TEM_OK;
+  for (int i = 0; i < n && st == TEM_OK; i++) {
+    tem_ctx *c = ctx[i];
+    was[i] = c->async;
+    c->async = true;
+    if (ops & TEM_BATCH_FACTOR) st = tem_factor(c, log_sigma[i]);
+    if (st == TEM_OK && (ops & TEM_BATCH_FORWARD)) st = tem_forward(c, d[i]);
+    if (st == TEM_OK && (ops & TEM_BATCH_JTVP)) st = tem_jtvp(c, w[i], jtw[i]);
+  }
+  for (int i = 0; i < n; i++) ctx[i]->async = was[i];
+  if (st != TEM_OK) return st;
+  // synchronous contexts: wait for all of them and report their status
+  for (int i = 0; i < n; i++)
+    if (!ctx[i]->async) TRY(tem_status(ctx[i]));
+  return TEM_OK;
+}
+
 int tem_set_tc_fronts(tem_ctx *c, int enable) {
   if (!c) return TEM_ERR_ARG;
   if (c->tc_fronts != (enable != 0)) c->state &= ~(ST_FACTORED | ST_FORWARD);   // the next tem_factor decides

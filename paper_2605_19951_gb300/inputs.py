@@ -266,6 +266,46 @@ def make_config(idx, m=None, n=None):
                   sigma_start=start)
 
 
+def make_c5_model(i, n=None, n_models=48):
+    """Model i of the uneven batch C5: n seeded uniform in 12..28 cubes per side
+    (a 500 m box), its own C3-style log-normal conductivity (log10 sigma = -2 +
+    0.5 z, z a Gaussian-filtered seeded field, 5-cell correlation), 2..8
+    square loops at seeded surface positions, 16 receivers on a 4 x 4
+    surface lattice, 24 times, 8 pole pairs.  n overrides the size (small
+    boxes for tests)."""
+    rng = np.random.default_rng(19951 + 5)
+    sizes = rng.integers(12, 29, size=n_models)
+    nloops = rng.integers(2, 9, size=n_models)
+    rng_i = np.random.default_rng(19951 + 5 * 1000 + i)
+    n = int(sizes[i]) if n is None else int(n)
+    h = 500.0 / n
+    n_air = (3 * n) // 8
+    xyz, tets = kuhn_box(n, h, n_air)
+    earth = _earth_mask(n, n_air)
+    ke = n - n_air
+    from scipy.ndimage import gaussian_filter
+    z = gaussian_filter(rng_i.standard_normal((n, n, ke)), sigma=5.0, mode="nearest")
+    z = (z - z.mean()) / max(z.std(), 1e-12)
+    cube = _cube_of_tet(n)
+    ci, cj, ck = cube % n, (cube // n) % n, cube // (n * n)
+    sig = np.full(tets.shape[0], SIGMA_AIR)
+    sig[earth] = 10.0 ** (-2.0 + 0.5 * z[ci[earth], cj[earth], ck[earth]])
+    side = max(2, n // 6)
+    loops = []
+    for _ in range(int(nloops[i])):
+        i0 = int(rng_i.integers(1, n - side))
+        j0 = int(rng_i.integers(1, n - side))
+        loops.append(square_loop(n, n_air, i0, j0, side))
+    lat = np.linspace(2, n - 2, 4).round().astype(int)
+    rx = np.array([[xyz[vertex_id(n, int(a), int(b), ke), 0], xyz[vertex_id(n, int(a), int(b), ke), 1], 0.0]
+                   for b in lat for a in lat])
+    start = np.full(tets.shape[0], SIGMA_AIR)
+    start[earth] = 0.01
+    return Survey(name=f"C5[{i}]", n=n, h=h, n_air=n_air, xyz=xyz, tets=tets, sigma=sig,
+                  is_param=earth.astype(np.uint8), loops=loops, rx=rx, times=times_log(24), m=8,
+                  sigma_start=start)
+
+
 def tiny_box(n=2, h=100.0, n_air=1, sigma_earth=0.01, sigma_air=SIGMA_AIR):
     """A very small box (2^3 .. 4^3 cubes) for brute-force checks."""
     xyz, tets = kuhn_box(n, h, n_air)

@@ -45,6 +45,7 @@ SIGNATURES = {
     "tem_model_step": (ctypes.c_int, [_P, _P, _P, _D, _P]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
+    "tem_batch": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P]),
     "tem_set_async": (ctypes.c_int, [_P, ctypes.c_int]),
     "tem_status": (ctypes.c_int, [_P]),
     "tem_set_tc_fronts": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -211,6 +212,24 @@ def tem_set_refine_adjoint(ctx, steps):
 
 def tem_set_tensor_cores(ctx, enable):
     _check(ctx, load().tem_set_tensor_cores(ctx, int(bool(enable))))
+
+
+TEM_BATCH_FACTOR, TEM_BATCH_FORWARD, TEM_BATCH_JTVP = 1, 2, 4
+
+
+def tem_batch(ctxs, ops, log_sigma=None, d=None, w=None, jtw=None):
+    """tem_batch over a list of contexts; the array lists match the contexts (None entries allowed)."""
+    n = len(ctxs)
+    arr = (_P * n)(*ctxs)
+
+    def ptrs(ts):
+        if ts is None:
+            return None
+        return (_P * n)(*[None if t is None else _dev(t).value for t in ts])
+
+    code = load().tem_batch(arr, n, int(ops), ptrs(log_sigma), ptrs(d), ptrs(w), ptrs(jtw))
+    if code != TEM_OK:
+        raise TemError(code, load().tem_last_error(ctxs[0]).decode(errors="replace"))
 
 
 def tem_set_async(ctx, enable):

@@ -562,3 +562,41 @@ def test_gauss_newton_checkpoint_resume(c1, tmp_path):
     finally:
         mdl.close()
     assert np.linalg.norm(m_resumed - m_straight) <= 1e-10 * np.linalg.norm(m_straight)
+
+
+def test_uneven_batch_in_one_graph():
+    """Configuration C5 at small sizes: five uneven models (6^3 .. 12^3 cubes,
+    their own log-normal conductivity and 2-8 loops) through one tem_batch call
+    and through one CUDA graph whose branches are the models' streams; both
+    equal each model computed alone (forward and J^T w), which the single-model
+    tests pin to the oracle; one model is also checked against the oracle."""
+    tem = _tem()
+    from paper_2605_19951_gb300.batch import Batch
+    sizes = [6, 10, 8, 12, 7]
+    surveys = [inputs.make_c5_model(i, n=n) for i, n in enumerate(sizes)]
+    xi, al = inputs.load_rational(8, surveys[0].times)
+    rng = np.random.default_rng(55)
+    ms = [_cuda(s.log_sigma()) for s in surveys]
+    ws = [_cuda(rng.standard_normal((len(s.loops), len(s.rx), len(s.times)))) for s in surveys]
+    refs = []
+    for s, m, w in zip(surveys, ms, ws):
+        mdl = _model(s, xi, al, "fp32r")
+        try:
+            mdl.factor(m)
+            refs.append((mdl.forward().cpu().numpy(), mdl.jtvp(w).cpu().numpy()))
+        finally:
+            mdl.close()
+    o = Oracle(surveys[1].xyz, surveys[1].tets, surveys[1].sigma, surveys[1].is_param, surveys[1].loops,
+               surveys[1].rx, xi, al)
+    o.set_model(surveys[1].log_sigma())
+    assert floored_err(refs[1][0], o.forward()).max() <= TOL["fp32r"]
+    jt_o = o.jtvp(ws[1].cpu().numpy())
+    assert np.linalg.norm(refs[1][1] - jt_o) <= TOL["fp32r"] * np.linalg.norm(jt_o)
+    b = Batch(surveys, xi, al)
+    try:
+        for d, jtw in [b.run(ms, ws), b.capture(ms, ws), b.replay(), b.replay()]:
+            for (dr, jr), dd, jj in zip(refs, d, jtw):
+                assert floored_err(dd.cpu().numpy(), dr).max() <= 1e-8
+                assert np.linalg.norm(jj.cpu().numpy() - jr) <= 1e-8 * np.linalg.norm(jr)
+    finally:
+        b.close()
