@@ -127,6 +127,29 @@ int tem_mesh(tem_ctx *ctx, int64_t n_vert, const double *xyz, int64_t n_tet,
 int tem_poles(tem_ctx *ctx, int32_t m, const double *xi, int32_t n_times,
               const double *alpha);
 
+/* New observation times for the poles of tem_poles (Section 2.3: the poles
+ * are shared by every time and only the residues alpha_i^[j] depend on t_j,
+ * so new times need no new factorisation).  The residues are fitted on the
+ * device in FP64 by penalised linear least squares, per time t_j:
+ *   min over alpha_.^[j] of  sum_z ( exp(-t_j z) - 2 Re sum_i alpha_i^[j] / (z - xi_i) )^2
+ *                            + mu^2 sum_i |alpha_i^[j]|^2 / |xi_i|^2
+ * over the sample set z in {0} and n_z log-spaced points in [z_min, z_max]
+ * (the spectrum of M^-1 K lies on z >= 0), by Householder QR of the
+ * (n_z + 1 + 2m) x 2m matrix once and one reduction and back-substitution per
+ * time.  The penalty bounds each partial fraction (max over z >= 0 of
+ * |alpha_i / (z - xi_i)| = |alpha_i| / |xi_i|).  Defaults of the stored tables:
+ * n_z = 2200, z_min = 1e-2, z_max = 1e9, mu = 1e-4.
+ *   t         host [n_times], every t_j > 0 (1 <= n_times <= 2^20)
+ *   alpha_out host [m][n_times][2] (re, im) of the fitted alpha_i^[j], or NULL
+ * The data, J v and J^T w shapes become [n_tx][n_rx][n_times].  The factors stay
+ * valid; the forward solutions too, but the next tem_jvp / tem_jtvp / tem_lsqr
+ * needs a tem_forward first (TEM_ERR_STATE until then).  Synchronises and
+ * reallocates the buffers sized by the data: not in asynchronous mode
+ * (TEM_ERR_STATE) and not inside a stream capture.  TEM_ERR_ARG for bad
+ * arguments or a rank-deficient fit (mu = 0 with too few samples). */
+int tem_times(tem_ctx *ctx, int32_t n_times, const double *t, int32_t n_z, double z_min,
+              double z_max, double mu, double *alpha_out);
+
 /* Transmitters and receivers (Section 2.1 source, Section 4.2 observation).
  *   loop_ptr  host [n_tx+1]  offsets into loop_verts
  *   loop_verts host          closed polylines of vertex ids; consecutive ids

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC"]
-SOURCES = ["api.cu", "factor.cu", "invert.cu", "solve.cu", "solve_tc.cu", "refine.cu", "ops.cu", "host.cpp"]
+SOURCES = ["api.cu", "factor.cu", "invert.cu", "solve.cu", "solve_tc.cu", "refine.cu", "ops.cu", "rational.cu", "host.cpp"]
 
 
 def _nvcc():

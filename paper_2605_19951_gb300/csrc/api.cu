@@ -245,6 +245,17 @@ int dalloc(tem_ctx *c, T **p, size_t count) {
   return TEM_OK;
 }
 
+// Free one allocation made by dalloc (count elements) and forget it.
+template <typename T>
+void dfree(tem_ctx *c, T **p, size_t count) {
+  if (!*p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), static_cast<void *>(*p));
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(*p);
+  c->bytes -= int64_t((count ? count : 1) * sizeof(T));
+  *p = nullptr;
+}
+
 template <typename T>
 int upload(tem_ctx *c, T **p, const std::vector<T> &v) {
   int st = dalloc(c, p, v.size());
@@ -1147,6 +1158,88 @@ int tem_poles(tem_ctx *c, int32_t m, const double *xi, int32_t n_times, const do
   CK(cudaMemcpyAsync(c->alpha, av.data(), sizeof(double2) * m * n_times, cudaMemcpyHostToDevice, c->stream));
   TRY(sync(c, "tem_poles"));
   c->state |= ST_POLES;
+  return TEM_OK;
+}
+
+int tem_times(tem_ctx *c, int32_t n_times, const double *t, int32_t n_z, double z_min, double z_max, double mu,
+              double *alpha_out) {
+  if (!c) return TEM_ERR_ARG;
+  if (!(c->state & ST_POLES)) return fail(c, TEM_ERR_STATE, "tem_poles first");
+  if (c->async) return fail(c, TEM_ERR_STATE, "tem_times synchronises: switch the asynchronous mode off first");
+  if (n_times <= 0 || n_times > (1 << 20) || !t) return fail(c, TEM_ERR_ARG, "bad times (1 <= n_times <= 2^20)");
+  for (int j = 0; j < n_times; j++)
+    if (!(t[j] > 0) || !std::isfinite(t[j])) return fail(c, TEM_ERR_ARG, "every time must be finite and > 0");
+  if (n_z < 2 || n_z > (1 << 20) || !(z_min > 0) || !(z_max > z_min) || !std::isfinite(z_max) || !(mu >= 0) ||
+      !std::isfinite(mu))
+    return fail(c, TEM_ERR_ARG, "bad sample set (2 <= n_z <= 2^20, 0 < z_min < z_max finite, mu >= 0)");
+  const int m = c->m, K = n_times;
+  const int64_t rows = int64_t(n_z) + 1 + 2 * m;
+  cudaStream_t s = c->stream;
+  // work arrays of this call, released on every return
+  struct Scratch {
+    std::vector<void *> p;
+    ~Scratch() {
+      for (void *q : p) cudaFree(q);
+    }
+  } w;
+  auto get = [&](size_t bytes, void **out) {
+    *out = nullptr;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+    w.p.push_back(*out);
+    return int(TEM_OK);
+  };
+  double *B, *Y, *rd, *cf, *td;
+  double2 *al;
+  TRY(get(sizeof(double) * rows * 2 * m, (void **)&B));
+  TRY(get(sizeof(double) * rows * K, (void **)&Y));
+  TRY(get(sizeof(double) * 2 * m, (void **)&rd));
+  TRY(get(sizeof(double) * 2 * m, (void **)&cf));
+  TRY(get(sizeof(double) * K, (void **)&td));
+  TRY(get(sizeof(double2) * m * K, (void **)&al));
+  const double lz0 = std::log10(z_min), lz1 = std::log10(z_max);
+  CK(cudaMemcpyAsync(td, t, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  launch_fit_qr(c->xi, m, n_z, lz0, lz1, mu, B, rd, cf, s);
+  std::vector<double> rdh(2 * m);
+  CK(cudaMemcpyAsync(rdh.data(), rd, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s));
+  TRY(sync(c, "tem_times"));
+  double rmax = 0;
+  for (double v : rdh) rmax = std::max(rmax, std::fabs(v));
+  for (double v : rdh)
+    if (!std::isfinite(v) || !(std::fabs(v) > 1e-14 * rmax))
+      return fail(c, TEM_ERR_ARG, "the sample set leaves the residue fit rank deficient (raise mu or n_z)");
+  launch_fit_solve(B, m, n_z, lz0, lz1, rd, cf, td, K, Y, al, s);
+  std::vector<double> ah(2 * size_t(m) * K);
+  CK(cudaMemcpyAsync(ah.data(), al, sizeof(double2) * m * K, cudaMemcpyDeviceToHost, s));
+  TRY(sync(c, "tem_times"));
+  for (double v : ah)
+    if (!std::isfinite(v)) return fail(c, TEM_ERR_ARG, "non-finite residue");
+  // install: alpha and every buffer sized by the data (n_tx n_rx K) follow the new K
+  const size_t nd_old = size_t(c->n_tx) * c->n_rx * c->K;
+  dfree(c, &c->alpha, size_t(m) * c->K);
+  TRY(dalloc(c, &c->alpha, size_t(m) * K));
+  CK(cudaMemcpyAsync(c->alpha, al, sizeof(double2) * m * K, cudaMemcpyDeviceToDevice, s));
+  if (c->d_cur) {
+    dfree(c, &c->d_cur, nd_old);
+    TRY(dalloc(c, &c->d_cur, size_t(c->n_tx) * c->n_rx * K));
+  }
+  if (c->ls_u) {   // LSQR work vectors: reallocated at the next LSQR call
+    const int64_t P = c->mesh.P, nf = c->mesh.nf;
+    dfree(c, &c->ls_u, nd_old + nf);
+    dfree(c, &c->ls_v, size_t(P));
+    dfree(c, &c->ls_w, size_t(P));
+    dfree(c, &c->ls_jv, nd_old);
+    dfree(c, &c->ls_jtw, size_t(P));
+    dfree(c, &c->ls_tmpd, nd_old);
+    dfree(c, &c->ls_tmpp, size_t(P));
+    dfree(c, &c->ls_wv, size_t(std::max<int64_t>(nf, 1)));
+    dfree(c, &c->ls_sc, 1);
+  }
+  TRY(sync(c, "tem_times"));
+  c->K = K;
+  c->alpha_h = ah;
+  c->state &= ~ST_FORWARD;   // the data of the last tem_forward had the old times; the factors stay
+  if (alpha_out) std::copy(ah.begin(), ah.end(), alpha_out);
   return TEM_OK;
 }
 

@@ -369,6 +369,13 @@ void launch_gn_res(const double *d, const double *d_obs, const double *wd, doubl
 void launch_dot(const double *x, const double *y, int64_t n, double *out, cudaStream_t s);
 void launch_axpy(const double *m, const double *dm, double eta, double *out, int64_t n, cudaStream_t s);
 
+// residues of the rational approximant for new observation times (rational.cu):
+// basis + Householder QR of the penalised least-squares matrix, then one solve per time
+void launch_fit_qr(const double2 *xi, int m, int64_t nz, double lz0, double lz1, double mu, double *B,
+                   double *rdiag, double *cf, cudaStream_t s);
+void launch_fit_solve(const double *B, int m, int64_t nz, double lz0, double lz1, const double *rdiag,
+                      const double *cf, const double *t, int K, double *Y, double2 *alpha, cudaStream_t s);
+
 // status words before a factorisation (a kernel, so that the call stays capturable)
 void launch_status_init(DevStatus *st, cudaStream_t s);
 

@@ -34,6 +34,7 @@ SIGNATURES = {
     "tem_last_error": (ctypes.c_char_p, [_P]),
     "tem_mesh": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _P, _I32]),
     "tem_poles": (ctypes.c_int, [_P, _I32, _P, _I32, _P]),
+    "tem_times": (ctypes.c_int, [_P, _I32, _P, _I32, _D, _D, _D, _P]),
     "tem_sources": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
     "tem_factor": (ctypes.c_int, [_P, _P]),
     "tem_forward": (ctypes.c_int, [_P, _P]),
@@ -149,6 +150,18 @@ def tem_poles(ctx, xi, alpha):
     a, pa = _host(np.stack([xi.real, xi.imag], axis=-1), np.float64)
     b, pb = _host(np.stack([alpha.real, alpha.imag], axis=-1), np.float64)
     _check(ctx, load().tem_poles(ctx, xi.shape[0], pa, alpha.shape[1], pb))
+
+
+def tem_times(ctx, times, n_z=2200, z_min=1e-2, z_max=1e9, mu=1e-4):
+    """Fit the residues alpha_i^[j] of the context's poles for new observation
+    times on the device (penalised least squares over {0} and n_z log-spaced
+    z in [z_min, z_max]); returns them as complex [m, K]."""
+    t, pt = _host(times, np.float64)
+    m = tem_info(ctx)["m"]
+    out = np.zeros((m, t.shape[0], 2))
+    _check(ctx, load().tem_times(ctx, t.shape[0], pt, int(n_z), float(z_min), float(z_max), float(mu),
+                                 out.ctypes.data_as(_P)))
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def tem_sources(ctx, loops, rx):
@@ -358,6 +371,13 @@ class Model:
         out = self._new(self.P)
         tem_jtvp(self.ctx, w.contiguous(), out)
         return out
+
+    def set_times(self, times, **fit):
+        """New observation times: residues fitted on the device, factors kept
+        (call forward() before jvp / jtvp / lsqr)."""
+        alpha = tem_times(self.ctx, times, **fit)
+        self.shape = (self.shape[0], self.shape[1], len(times))
+        return alpha
 
     def lsqr(self, d_obs, wd, m_ref, lam, n_iter):
         dm = self._new(self.P)
