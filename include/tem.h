@@ -225,6 +225,18 @@ int tem_gn_eval(tem_ctx *ctx, const double *d_obs, const double *wd, const doubl
  * Section 3.3).  m, dm, out dev [P]; out may alias m. */
 int tem_model_step(tem_ctx *ctx, const double *m, const double *dm, double eta, double *out);
 
+/* Supernode amalgamation of the assembly tree (Algorithm 1, factorise; no
+ * paper counterpart in its details): a child separator of at most
+ * max_pivots unknowns is merged into its parent front (its pivots first) and
+ * its children become the parent's, while the parent keeps at most four
+ * children.  The plane separators between two leaf boxes of the dissection
+ * are small (21 unknowns on the 46^3 box); merged, they cost some explicit
+ * zeros in the parent's dense front instead of a tree level of fronts that
+ * fill a fraction of the device tiles.  Default 32; 0 switches it off.  Call
+ * before tem_mesh, which builds the tree (TEM_ERR_STATE after it);
+ * max_pivots in 0..4096 (TEM_ERR_ARG otherwise). */
+int tem_set_amalgamation(tem_ctx *ctx, int32_t max_pivots);
+
 /* TEM_FP32_REFINED mode: refinement corrections per forward and J v solve
  * (default 3) and the conductivity floor of the factored matrices (default
  * 1e-6).

@@ -148,6 +148,7 @@ struct tem_ctx {
   bool use_tc = true;                     // FP32 mode: front products on tcgen05
   bool tc_fronts = true;                  // FP32 mode: trailing updates of the fronts on tcgen05
   bool async = false;                     // calls return once issued; tem_status reads the status words
+  SymOpts sym_opts;                       // dissection and amalgamation options of tem_mesh
 
   // mesh tables
   double *sigma_fixed = nullptr, *sigma = nullptr, *me1 = nullptr, *kval = nullptr, *mval = nullptr;
@@ -493,7 +494,8 @@ void build_steps(FactorSys &S_) {
     lv.lend = L.lend;
     lv.obeg = L.obeg;
     lv.oend = L.oend;
-    for (int s = 0; s < 2; s++) {
+    static_assert(kMaxChild == 4, "LevelDev holds four extend-add slots");
+    for (int s = 0; s < kMaxChild; s++) {
       lv.ea_beg[s] = L.ea_beg[s];
       lv.ea_end[s] = L.ea_end[s];
     }
@@ -1057,7 +1059,8 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
   if (!c) return TEM_ERR_ARG;
   if (c->state & ST_MESH) return fail(c, TEM_ERR_STATE, "mesh already set");
   if (!xyz || !tets || !sigma || !is_param) return fail(c, TEM_ERR_ARG, "NULL mesh array");
-  std::string msg = build_mesh(c->mesh, n_vert, xyz, n_tet, tets, sigma, is_param, leaf_max, c->es.sym);
+  c->sym_opts.leaf_max = leaf_max;
+  std::string msg = build_mesh(c->mesh, n_vert, xyz, n_tet, tets, sigma, is_param, c->sym_opts, c->es.sym);
   if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
   Mesh &M = c->mesh;
   TRY(upload(c, &c->sigma_fixed, M.sigma));
@@ -1099,7 +1102,7 @@ int tem_mesh(tem_ctx *c, int64_t n_vert, const double *xyz, int64_t n_tet, const
     }
     TRY(upload(c, &c->me1df, mp));
     // the gradient space of the refinement: interior vertices, P1 Laplacian
-    msg = build_nodal(M, leaf_max, c->nodal, c->ns.sym);
+    msg = build_nodal(M, c->sym_opts, c->nodal, c->ns.sym);
     if (!msg.empty()) return fail(c, TEM_ERR_MESH, msg);
     const NodalMesh &G = c->nodal;
     c->ns.N = G.N;
@@ -1508,6 +1511,14 @@ int tem_model_step(tem_ctx *c, const double *m, const double *dm, double eta, do
   if (!(c->state & ST_MESH) || !m || !dm || !out || !std::isfinite(eta)) return fail(c, TEM_ERR_ARG, "bad arguments");
   launch_axpy(m, dm, eta, out, c->mesh.P, c->stream);
   return finish(c, "tem_model_step");
+}
+
+int tem_set_amalgamation(tem_ctx *c, int32_t max_pivots) {
+  if (!c) return TEM_ERR_ARG;
+  if (c->state & ST_MESH) return fail(c, TEM_ERR_STATE, "the assembly tree is built by tem_mesh: set this before");
+  if (max_pivots < 0 || max_pivots > 4096) return fail(c, TEM_ERR_ARG, "max_pivots in 0..4096");
+  c->sym_opts.amalg_max = max_pivots;
+  return TEM_OK;
 }
 
 int tem_set_tensor_cores(tem_ctx *c, int enable) {

@@ -432,7 +432,7 @@ void FactorPlan<R>::level(int h, const LevelDev &lv, cudaStream_t s) {
   }
   // 3. extend-add, one child slot at a time (no two tasks of a launch hit
   //    the same parent entry)
-  for (int sl = 0; sl < 2; sl++) {
+  for (int sl = 0; sl < 4; sl++) {
     const int64_t nt = lv.ea_end[sl] - lv.ea_beg[sl];
     if (nt <= 0) continue;
     dim3 g((unsigned)nt, m);

@@ -76,8 +76,9 @@ void element_matrices(const double p[4][3], double *Ke, double *Me, double &vol)
 
 struct NDNode {
   std::vector<int32_t> piv;  // old interior indices
-  int32_t child[2] = {-1, -1};
+  int32_t child[kMaxChild] = {-1, -1, -1, -1};
   int32_t nchild = 0;
+  bool merged = false;       // amalgamated into its parent
 };
 
 struct NDState {
@@ -215,6 +216,52 @@ std::string build_symbolic(const SymIn &in, SymOut &out, Symbolic &s) {
     std::iota(dofs.begin(), dofs.end(), 0);
     std::iota(tt.begin(), tt.end(), 0);
     nd_recurse(st, dofs, tt);
+  }
+  // ---- amalgamation: a child separator of at most amalg_max unknowns is
+  //      merged into its parent front (its pivots first, in child order), and
+  //      its own children become the parent's, while the parent keeps at most
+  //      kMaxChild children.  Tiny separators (the planes between two leaf
+  //      boxes) otherwise make a level of fronts that fill a fraction of the
+  //      device tiles; merged, their unknowns cost some explicit zeros in the
+  //      parent's dense front instead. ----
+  if (in.amalg_max > 0) {
+    std::vector<NDNode> &nd = st.nodes;
+    for (size_t i = 0; i < nd.size(); i++) {   // postorder: every child is final before its parent
+      NDNode &P = nd[i];
+      int32_t kids[kMaxChild], nk = 0;
+      std::vector<int32_t> piv;
+      for (int q = 0; q < P.nchild; q++) {
+        NDNode &C = nd[P.child[q]];
+        const int rest = P.nchild - q - 1;   // later children, one slot each if kept
+        const bool merge = C.nchild > 0 && (int64_t)C.piv.size() <= in.amalg_max && nk + C.nchild + rest <= kMaxChild;
+        if (!merge) {
+          kids[nk++] = P.child[q];
+          continue;
+        }
+        piv.insert(piv.end(), C.piv.begin(), C.piv.end());
+        for (int g = 0; g < C.nchild; g++) kids[nk++] = C.child[g];
+        std::vector<int32_t>().swap(C.piv);
+        C.nchild = 0;
+        C.merged = true;
+      }
+      if (piv.empty()) continue;
+      piv.insert(piv.end(), P.piv.begin(), P.piv.end());
+      P.piv.swap(piv);
+      P.nchild = nk;
+      for (int q = 0; q < nk; q++) P.child[q] = kids[q];
+    }
+    // drop the merged nodes; postorder is kept
+    std::vector<int32_t> remap(nd.size(), -1);
+    std::vector<NDNode> keep;
+    keep.reserve(nd.size());
+    for (size_t i = 0; i < nd.size(); i++)
+      if (!nd[i].merged) {
+        remap[i] = (int32_t)keep.size();
+        keep.push_back(std::move(nd[i]));
+      }
+    for (NDNode &x : keep)
+      for (int q = 0; q < x.nchild; q++) x.child[q] = remap[x.child[q]];
+    nd.swap(keep);
   }
   std::vector<NDNode> &nodes = st.nodes;  // postorder: children precede parents
   const int32_t nn = (int32_t)nodes.size();
@@ -449,11 +496,11 @@ std::string build_symbolic(const SymIn &in, SymOut &out, Symbolic &s) {
       s.levels[h].oend = (int64_t)s.orig_nz.size();
     }
   }
-  // ---- extend-add task lists (child slot 0 and 1 kept apart) ----
+  // ---- extend-add task lists (child slots kept apart: one launch each) ----
   s.ea_child.clear();
   s.ea_col.clear();
   for (Level &L : s.levels)
-    for (int sl = 0; sl < 2; sl++) {
+    for (int sl = 0; sl < kMaxChild; sl++) {
       L.ea_beg[sl] = (int64_t)s.ea_child.size();
       for (int32_t f : L.fronts) {
         const Front &F = s.fronts[f];
@@ -470,7 +517,7 @@ std::string build_symbolic(const SymIn &in, SymOut &out, Symbolic &s) {
 }
 
 std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const int32_t *tets,
-                       const double *sigma, const uint8_t *is_param, int32_t leaf_max,
+                       const double *sigma, const uint8_t *is_param, const SymOpts &opt,
                        Symbolic &s) {
   if (nv <= 0 || nt <= 0) return "empty mesh";
   if (nv >= (int64_t(1) << 21)) return "more than 2^21 vertices are not supported";
@@ -573,7 +620,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
   {
     std::vector<int32_t> tu(6 * nt);
     for (int64_t q = 0; q < 6 * nt; q++) tu[q] = m.dof_old[m.tedge[q]];
-    SymIn in{&m, N, 6, &tu, leaf_max};
+    SymIn in{&m, N, 6, &tu, opt.leaf_max, opt.amalg_max};
     SymOut so;
     const std::string e = build_symbolic(in, so, s);
     if (!e.empty()) return e;
@@ -698,7 +745,7 @@ std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt, const
   return "";
 }
 
-std::string build_nodal(const Mesh &m, int32_t leaf_max, NodalMesh &nm, Symbolic &s) {
+std::string build_nodal(const Mesh &m, const SymOpts &opt, NodalMesh &nm, Symbolic &s) {
   const int64_t nt = m.nt, nv = m.nv;
   // interior vertices: the hat functions whose gradients are interior edge fields
   std::vector<int32_t> vold(nv, -1), vert_of;
@@ -711,7 +758,7 @@ std::string build_nodal(const Mesh &m, int32_t leaf_max, NodalMesh &nm, Symbolic
   if (N == 0) return "no interior vertices";
   std::vector<int32_t> tu(4 * nt);
   for (int64_t q = 0; q < 4 * nt; q++) tu[q] = vold[m.tv[q]];
-  SymIn in{&m, N, 4, &tu, leaf_max};
+  SymIn in{&m, N, 4, &tu, opt.leaf_max, opt.amalg_max};
   SymOut so;
   const std::string e = build_symbolic(in, so, s);
   if (!e.empty()) return e;

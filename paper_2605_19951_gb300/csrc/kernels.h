@@ -124,7 +124,7 @@ struct LevelDev {
   int n_b21 = 0;
   int bwd_upd_tiles = 0;            // ceil(max k / 8)
   int64_t lbeg = 0, lend = 0, obeg = 0, oend = 0;
-  int64_t ea_beg[2] = {0, 0}, ea_end[2] = {0, 0};
+  int64_t ea_beg[4] = {}, ea_end[4] = {};   // extend-add tasks per child slot
   std::vector<StepDims> steps;
   struct SuperBlock {
     const int4 *fwd = nullptr;   // (front, row tile, k begin, k end) of k_fwd_sb

@@ -7,6 +7,8 @@
 namespace tem {
 
 constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
+constexpr int kMaxChild = 4;       // children per front (two from the dissection, four after amalgamation)
+constexpr int kAmalgDefault = 32;  // separators of at most this many unknowns merge into their parent
 
 // Per-front description (one supernode of the assembly tree = one node of
 // the nested-dissection tree: a separator or a leaf subdomain).
@@ -18,7 +20,7 @@ struct Front {
   int32_t parent = -1;  // parent front (-1 = root)
   int32_t height = 0;   // 0 = leaf
   int32_t nchild = 0;
-  int32_t child[2] = {-1, -1};
+  int32_t child[kMaxChild] = {-1, -1, -1, -1};
   int64_t rows_off = 0; // offset of the update-row list in Symbolic::rows
   int64_t lofs = 0;     // offset of the n x k factor block (elements)
   int64_t uofs = -1;    // offset of the b x b update block in the arena
@@ -29,7 +31,7 @@ struct Level {
   std::vector<int32_t> fronts;  // sorted by k descending
   int64_t lbeg = 0, lend = 0;   // contiguous factor range [lbeg, lend)
   int64_t obeg = 0, oend = 0;   // original-entry range
-  int64_t ea_beg[2] = {0, 0}, ea_end[2] = {0, 0};  // extend-add tasks per child slot
+  int64_t ea_beg[kMaxChild] = {}, ea_end[kMaxChild] = {};  // extend-add tasks per child slot
   int32_t max_k = 0;
 };
 
@@ -100,6 +102,13 @@ struct SymIn {
   int per;                           // slots per tetrahedron
   const std::vector<int32_t> *tunk;  // [nt*per] old unknown of each slot, -1 = none
   int32_t leaf_max;                  // largest leaf of the dissection (0 = default)
+  int32_t amalg_max;                 // separators of at most this many unknowns merge into their parent (0: none)
+};
+
+// Options of the dissection and assembly tree.
+struct SymOpts {
+  int32_t leaf_max = 0;              // largest leaf of the dissection (0 = default, 128)
+  int32_t amalg_max = kAmalgDefault; // amalgamation threshold (0: none)
 };
 struct SymOut {
   std::vector<int32_t> perm, iperm;  // new -> old, old -> new
@@ -136,10 +145,10 @@ struct NodalMesh {
 
 // Host builders (host.cpp).  Return "" on success or an error message.
 std::string build_symbolic(const SymIn &in, SymOut &out, Symbolic &s);
-std::string build_nodal(const Mesh &m, int32_t leaf_max, NodalMesh &nm, Symbolic &s);
+std::string build_nodal(const Mesh &m, const SymOpts &opt, NodalMesh &nm, Symbolic &s);
 std::string build_mesh(Mesh &m, int64_t nv, const double *xyz, int64_t nt,
                        const int32_t *tets, const double *sigma,
-                       const uint8_t *is_param, int32_t leaf_max, Symbolic &s);
+                       const uint8_t *is_param, const SymOpts &opt, Symbolic &s);
 std::string build_sources(const Mesh &m, int32_t n_tx, const int64_t *loop_ptr,
                           const int32_t *loop_verts, int32_t n_rx, const double *rx,
                           std::vector<double> &f,          // [N][n_tx] elimination order

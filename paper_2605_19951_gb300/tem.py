@@ -44,6 +44,7 @@ SIGNATURES = {
     "tem_lsqr_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _D, _I32, _P]),
     "tem_gn_eval": (ctypes.c_int, [_P, _P, _P, _P, _D, _P, _P, _P]),
     "tem_model_step": (ctypes.c_int, [_P, _P, _P, _D, _P]),
+    "tem_set_amalgamation": (ctypes.c_int, [_P, _I32]),
     "tem_set_refine": (ctypes.c_int, [_P, _I32, _D, _D]),
     "tem_set_refine_adjoint": (ctypes.c_int, [_P, _I32]),
     "tem_batch": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P]),
@@ -223,6 +224,10 @@ def tem_set_refine_adjoint(ctx, steps):
     _check(ctx, load().tem_set_refine_adjoint(ctx, int(steps)))
 
 
+def tem_set_amalgamation(ctx, max_pivots):
+    _check(ctx, load().tem_set_amalgamation(ctx, int(max_pivots)))
+
+
 def tem_set_tensor_cores(ctx, enable):
     _check(ctx, load().tem_set_tensor_cores(ctx, int(bool(enable))))
 
@@ -321,11 +326,13 @@ class Model:
     """One survey on one GPU: mesh, poles, sources, and the current factors."""
 
     def __init__(self, xyz, tets, sigma, is_param, loops, rx, xi, alpha,
-                 precision=TEM_FP32_REFINED, leaf_max=0, stream=None):
+                 precision=TEM_FP32_REFINED, leaf_max=0, stream=None, amalgamation=None):
         import torch
         self.torch = torch
         self.ctx = tem_create(precision, stream)
         try:
+            if amalgamation is not None:
+                tem_set_amalgamation(self.ctx, amalgamation)
             tem_mesh(self.ctx, xyz, tets, sigma, is_param, leaf_max)
             tem_poles(self.ctx, xi, alpha)
             tem_sources(self.ctx, loops, rx)

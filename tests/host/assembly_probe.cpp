@@ -44,7 +44,7 @@ int main(int argc, char **argv) {
   if (!ok) return 2;
   tem::Mesh m;
   tem::Symbolic s;
-  std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), 0, s);
+  std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), tem::SymOpts{}, s);
   std::vector<double> fsrc, q_val, qt_val;
   std::vector<int64_t> q_rp, qt_rp;
   std::vector<int32_t> q_ci, qt_dof, qt_ci;

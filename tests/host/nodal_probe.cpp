@@ -40,8 +40,8 @@ int main(int argc, char **argv) {
   tem::Mesh m;
   tem::Symbolic s, sn;
   tem::NodalMesh nm;
-  std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), 0, s);
-  if (e.empty()) e = tem::build_nodal(m, 0, nm, sn);
+  std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), tem::SymOpts{}, s);
+  if (e.empty()) e = tem::build_nodal(m, tem::SymOpts{}, nm, sn);
   if (!e.empty()) {
     std::fprintf(stderr, "%s\n", e.c_str());
     return 1;

@@ -9,9 +9,9 @@
 //   the elimination order (int64 rp[N+1], int64 nnz, int32 ci[nnz]) and the
 //   map of A's lower-triangle entries to factor positions (int64 no,
 //   int64 orig_nz[no], int64 orig_dst[no]), then the levels (int64 nl; per
-//   level int64 nfront and int32 fronts[nfront], int64 ea_beg[2], ea_end[2]) and the
+//   level int64 nfront and int32 fronts[nfront], int64 ea_beg[4], ea_end[4]) and the
 //   extend-add tasks (int64 nea, int32 ea_child[nea], int32 ea_col[nea]).
-// Input (argv[1], native binary): int64 nv, int64 nt, int32 leaf_max,
+// Input (argv[1], native binary): int64 nv, int64 nt, int32 leaf_max, int32 amalg_max,
 // double xyz[nv*3], int32 tets[nt*4], double sigma[nt], uint8 is_param[nt].
 #include <cstdio>
 #include <vector>
@@ -22,8 +22,9 @@ int main(int argc, char **argv) {
   FILE *f = std::fopen(argv[1], "rb");
   if (!f) return 2;
   int64_t nv = 0, nt = 0;
-  int32_t leaf = 0;
-  bool ok = std::fread(&nv, 8, 1, f) == 1 && std::fread(&nt, 8, 1, f) == 1 && std::fread(&leaf, 4, 1, f) == 1;
+  int32_t leaf = 0, amalg = 0;
+  bool ok = std::fread(&nv, 8, 1, f) == 1 && std::fread(&nt, 8, 1, f) == 1 && std::fread(&leaf, 4, 1, f) == 1 &&
+            std::fread(&amalg, 4, 1, f) == 1;
   std::vector<double> xyz(3 * nv > 0 ? 3 * nv : 0), sig(nt > 0 ? nt : 0);
   std::vector<int32_t> tets(4 * nt > 0 ? 4 * nt : 0);
   std::vector<uint8_t> ip(nt > 0 ? nt : 0);
@@ -34,7 +35,7 @@ int main(int argc, char **argv) {
   if (!ok) return 2;
   tem::Mesh m;
   tem::Symbolic s;
-  const std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), leaf, s);
+  const std::string e = tem::build_mesh(m, nv, xyz.data(), nt, tets.data(), sig.data(), ip.data(), tem::SymOpts{leaf, amalg}, s);
   if (!e.empty()) {
     std::fprintf(stderr, "%s\n", e.c_str());
     return 1;
@@ -70,8 +71,8 @@ int main(int argc, char **argv) {
     const int64_t nfl = (int64_t)L.fronts.size();
     std::fwrite(&nfl, 8, 1, o);
     std::fwrite(L.fronts.data(), 4, L.fronts.size(), o);
-    std::fwrite(L.ea_beg, 8, 2, o);
-    std::fwrite(L.ea_end, 8, 2, o);
+    std::fwrite(L.ea_beg, 8, tem::kMaxChild, o);
+    std::fwrite(L.ea_end, 8, tem::kMaxChild, o);
   }
   std::fwrite(&nea, 8, 1, o);
   std::fwrite(s.ea_child.data(), 4, s.ea_child.size(), o);

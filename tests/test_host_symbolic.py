@@ -27,6 +27,8 @@ import pytest
 from paper_2605_19951_gb300 import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+MAX_CHILD = 4          # children per front (csrc/tem_internal.h kMaxChild)
+AMALG_DEFAULT = 32     # default amalgamation threshold (kAmalgDefault)
 CSRC = os.path.join(HERE, "..", "paper_2605_19951_gb300", "csrc")
 
 
@@ -43,12 +45,12 @@ def probe():
     shutil.rmtree(d, ignore_errors=True)
 
 
-def run_probe(probe, s, leaf):
+def run_probe(probe, s, leaf, amalg=AMALG_DEFAULT):
     exe, d = probe
     src, dst = os.path.join(d, "mesh.bin"), os.path.join(d, "sym.bin")
     with open(src, "wb") as f:
         np.array([s.xyz.shape[0], s.tets.shape[0]], np.int64).tofile(f)
-        np.array([leaf], np.int32).tofile(f)
+        np.array([leaf, amalg], np.int32).tofile(f)
         np.ascontiguousarray(s.xyz, np.float64).tofile(f)
         np.ascontiguousarray(s.tets, np.int32).tofile(f)
         np.ascontiguousarray(s.sigma, np.float64).tofile(f)
@@ -82,7 +84,7 @@ def run_probe(probe, s, leaf):
     levels = []
     for _ in range(int(take(np.int64, 1)[0])):
         lf = take(np.int32, int(take(np.int64, 1)[0])).copy()
-        beg, end = take(np.int64, 2).copy(), take(np.int64, 2).copy()
+        beg, end = take(np.int64, MAX_CHILD).copy(), take(np.int64, MAX_CHILD).copy()
         levels.append((lf, beg, end))
     nea = int(take(np.int64, 1)[0])
     ea = (take(np.int32, nea).copy(), take(np.int32, nea).copy())
@@ -167,7 +169,7 @@ def check_extend_add(fronts, layout, levels, ea):
     """Level h lists the fronts of height h.  Its extend-add tasks (child front,
     child update column) cover every update column of every child of those
     fronts exactly once, and no two children of one parent fall into the same
-    child slot (the two slots run as separate launches, so the children's
+    child slot (each slot runs as a launch of its own, so the children's
     scatter-adds into a parent never run concurrently)."""
     ea_child, ea_col = ea
     for h, (lf, beg, end) in enumerate(levels):
@@ -178,7 +180,7 @@ def check_extend_add(fronts, layout, levels, ea):
                 if fr[3] == f:
                     want |= {(c, j) for j in range(fr[1] - fr[0])}
         got = []
-        for sl in range(2):
+        for sl in range(MAX_CHILD):
             kids = ea_child[beg[sl]:end[sl]].tolist()
             got += list(zip(kids, ea_col[beg[sl]:end[sl]].tolist()))
             parents = [fronts[c][3] for c in sorted(set(kids))]
@@ -229,12 +231,33 @@ def check_structure(N, tdof, fronts, nnz_l, plan, entries, ea):
     assert nnz_l >= true_nnz
 
 
+@pytest.mark.parametrize("amalg", [0, AMALG_DEFAULT])
 @pytest.mark.parametrize("leaf", [0, 16, 64])
-def test_fronts_contain_symbolic_cholesky(probe, leaf):
+def test_fronts_contain_symbolic_cholesky(probe, leaf, amalg):
     s = inputs.make_config(1)
-    check_structure(*run_probe(probe, s, leaf))
+    check_structure(*run_probe(probe, s, leaf, amalg))
 
 
-def test_fronts_with_a_conductive_block(probe):
+@pytest.mark.parametrize("amalg", [0, AMALG_DEFAULT])
+def test_fronts_with_a_conductive_block(probe, amalg):
     s = inputs.make_config(2, n=6)
-    check_structure(*run_probe(probe, s, 24))
+    check_structure(*run_probe(probe, s, 24, amalg))
+
+
+def test_amalgamation_merges_small_separators(probe):
+    """With amalgamation every internal front of at most AMALG_DEFAULT
+    pivots is one whose parent had no room (four children already, counting
+    the merged grandchildren), there are fewer fronts, some fronts have three
+    or four children, and no front has more than four."""
+    s = inputs.make_config(1)
+    plain = run_probe(probe, s, 16, 0)[2]
+    merged = run_probe(probe, s, 16, AMALG_DEFAULT)[2]
+    assert len(merged) < len(plain)
+    nkids = np.zeros(len(merged), np.int64)
+    for k, n, c0, parent, rows, rel in merged:
+        if parent >= 0:
+            nkids[parent] += 1
+    assert nkids.max() <= MAX_CHILD and (nkids >= 3).any()
+    for q, (k, n, c0, parent, rows, rel) in enumerate(merged):
+        if nkids[q] > 0 and k <= AMALG_DEFAULT and parent >= 0:
+            assert nkids[parent] - 1 + nkids[q] > MAX_CHILD, q
