@@ -60,6 +60,14 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-kscale", action="store_true", help="skip the time-channel scaling study")
+    ap.add_argument("--levels", action="store_true",
+                    help="instead of the bench line: per-level times and rates of the four front-product "
+                         "classes in one J.v (CUDA events per class and tree level)")
+    ap.add_argument("--c5", action="store_true",
+                    help="instead of the bench line: configuration C5, 48 uneven surveys, forward + J^T.w each, "
+                         "one CUDA graph per wave of models")
+    ap.add_argument("--c5-budget-gb", type=float, default=110.0,
+                    help="device memory per C5 wave (estimated from the factor entries)")
     ap.add_argument("--n", type=int, default=46,
                     help="cubes per side (46 = the 700k-DoF workload; smaller only for profiling captures)")
     return ap.parse_args()
@@ -282,6 +290,8 @@ def run_ours(args):
 
     e2e_ms, _ = timed(torch, e2e)
     e2e_ms, = max_over_ranks(torch, dist, [e2e_ms], "cuda")
+    # one Gauss-Newton iteration measured as a whole: factor + forward + a 30-iteration LSQR call
+    gn_ms, _ = timed(torch, lambda: (mdl.factor(m0), mdl.forward(), mdl.lsqr(d_obs, wd, m0, LAMBDA, N_LSQR_GN)))
     h2d = (d_obs_p.numel() + wd_p.numel() + m0_p.numel()) * 8
     d2h = dm_p.numel() * 8
 
@@ -328,6 +338,9 @@ def run_ours(args):
         "forward_s": round(forward_ms / 1e3, 3),
         "gn_iteration_s": round((factor_ms + forward_ms + N_LSQR_GN * t_ms / args.steps) / 1e3, 2),
         "gn_iteration_note": "factor + forward + 30 LSQR pairs at the measured rates (linear model, Fig. 10)",
+        "gn_iteration_measured_s": round(gn_ms / 1e3, 2),
+        "gn_iteration_measured_note": "one tem_factor + tem_forward + tem_lsqr(30 iterations) timed as a whole "
+                                      "(CUDA events; includes LSQR's start-up J^T.w)",
         "roofline": roof,
         "e2e": {"value": round(whole_job_rate(args.steps, world, e2e_ms), 4), "unit": "pairs/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
@@ -441,9 +454,125 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_levels(args):
+    """One J.v on the workload, each front-product class timed level by level
+    (tem_set_profiling with a tree level); rate = the level's factor entries
+    of that class x 8 B x poles x launches / time."""
+    import numpy as np
+    import torch
+    from paper_2605_19951_gb300 import inputs, tem
+    torch.cuda.set_device(0)
+    s = inputs.make_config(CONFIG, n=args.n)
+    xi, al = inputs.load_rational(s.m, s.times)
+    mdl = tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al, precision=tem.TEM_FP32_REFINED)
+    m0 = torch.as_tensor(s.log_sigma(), device="cuda")
+    mdl.factor(m0)
+    mdl.forward()
+    lv = tem.tem_level_info(mdl.ctx)
+    m = mdl.info()["m"]
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    v = torch.randn(s.n_param, dtype=torch.float64, device="cuda", generator=gen)
+    for _ in range(2):
+        mdl.jvp(v)
+    names = {"fwd": "TRI_F", "fwd21": "FWD21", "bwd_upd": "BWD21", "bwd": "TRI_B"}
+    out = {"workload": f"{s.n}^3 Kuhn box, {mdl.info()['n_dof']} DoF, 10 pole pairs, 32 loops",
+           "call": "one tem_jvp (forward + 3 corrections = 4 sweep pairs)", "levels": []}
+    for h in range(lv.shape[0]):
+        row = {"level": h, "fronts": int(lv[h, 0]), "l11_entries": int(lv[h, 1]), "l21_entries": int(lv[h, 2]),
+               "max_k": int(lv[h, 3])}
+        for cls, name in names.items():
+            tem.tem_set_profiling(mdl.ctx, tem.KERNEL_CLASSES[cls] + 64 * (h + 1))
+            mdl.jvp(v)
+            ms, nl = tem.tem_kernel_time(mdl.ctx)
+            ent = lv[h, 1] if cls in ("fwd", "bwd") else lv[h, 2]
+            row[name + "_ms"] = round(ms, 3)
+            row[name + "_GBps"] = round(8.0 * ent * m * nl / (ms * 1e-3) / 1e9, 1) if ms > 0 and ent > 0 else None
+        out["levels"].append(row)
+    tem.tem_set_profiling(mdl.ctx, None)
+    mdl.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_c5(args):
+    """Configuration C5: 48 independent surveys on meshes of 12..28 cubes per
+    side (seeded), each with its own log-normal conductivity and 2..8 loops;
+    per survey one forward and one J^T.w with seeded w, refined FP32.  The
+    surveys are issued together by tem_batch on their own streams and the
+    whole call is captured into one CUDA graph per wave; waves are filled in
+    order of size up to a device-memory budget estimated from each survey's
+    factor entries.  Reported: the graph replays (median of 3 per wave, CUDA
+    events) against issuing the same calls without a graph."""
+    import numpy as np
+    import torch
+    from paper_2605_19951_gb300 import batch, inputs, tem
+    torch.cuda.set_device(0)
+    n_models = 48
+    surveys = [inputs.make_c5_model(i) for i in range(n_models)]
+    xi, al = inputs.load_rational(8, inputs.times_log(24))
+    est = []
+    for s in surveys:   # factor entries from the host analysis alone (no numeric storage)
+        ctx = tem.tem_create(tem.TEM_FP32_REFINED)
+        try:
+            tem.tem_mesh(ctx, s.xyz, s.tets, s.sigma, s.is_param)
+            # device bytes of a refined-FP32 context at C4 were 4.3x its c64 factor (row copies,
+            # update arena, vectors): 4.5 x leaves a margin
+            est.append(4.5 * 8.0 * 8 * tem.tem_info(ctx)["nnz_l"])
+        finally:
+            tem.tem_destroy(ctx)
+    order = sorted(range(n_models), key=lambda i: surveys[i].n)
+    waves, cur, used = [], [], 0.0
+    for i in order:
+        if cur and used + est[i] > args.c5_budget_gb * 1e9:
+            waves.append(cur)
+            cur, used = [], 0.0
+        cur.append(i)
+        used += est[i]
+    waves.append(cur)
+    rng = np.random.default_rng(19951 + 5)
+    graph_ms, eager_ms, dof = [], [], 0
+
+    def ev(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+    for wv in waves:
+        sv = [surveys[i] for i in wv]
+        b = batch.Batch(sv, xi, al)
+        try:
+            logs = [torch.as_tensor(s.log_sigma(), device="cuda") for s in sv]
+            ws = [torch.as_tensor(rng.standard_normal((len(s.loops), len(s.rx), len(s.times))), device="cuda")
+                  for s in sv]
+            b.run(logs, ws)                                   # allocations
+            eager_ms.append(statistics.median([ev(lambda: b.run(logs, ws)) for _ in range(3)]))
+            b.capture(logs, ws)
+            b.replay()
+            graph_ms.append(statistics.median([ev(b.replay) for _ in range(3)]))
+            dof += sum(m.info()["n_dof"] for m in b.models)
+        finally:
+            b.close()
+            del b
+            torch.cuda.empty_cache()
+    out = {"config": "C5: 48 surveys, meshes of 12..28 cubes per side (seeded), 2..8 loops, 16 rx, 24 times, "
+                     "8 pole pairs; forward + one J^T.w each, refined FP32",
+           "waves": [len(w) for w in waves], "total_dof": dof,
+           "graph_ms": round(sum(graph_ms), 1), "eager_ms": round(sum(eager_ms), 1),
+           "models_per_s": round(n_models / (sum(graph_ms) / 1e3), 2),
+           "per_wave_graph_ms": [round(x, 1) for x in graph_ms], "per_wave_eager_ms": [round(x, 1) for x in eager_ms],
+           "note": "factor + forward + J^T.w of every survey; one graph launch per wave (CUDA events, median of 3)"}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.c5:
+        run_c5(a)
+    elif a.levels:
+        run_levels(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -383,6 +383,12 @@ int tem_export_forward(tem_ctx *ctx, double *g);
  * length N and [N][2]. */
 int tem_export_dofs(tem_ctx *ctx, int64_t *edge_verts);
 
+/* Assembly-tree levels of the edge system (for per-level measurements with
+ * tem_set_profiling): out host [n_levels][4], per level h (0 = leaves) the
+ * number of fronts, the pivot-block entries sum k (k + 1) / 2, the
+ * update-row entries sum k b and the largest k.  After tem_mesh. */
+int tem_level_info(tem_ctx *ctx, int64_t *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,13 +13,16 @@ from . import tem
 
 
 class Batch:
-    def __init__(self, surveys, xi, alpha, precision=tem.TEM_FP32_REFINED):
+    def __init__(self, surveys, xi, alpha, precision=tem.TEM_FP32_REFINED, trees=None):
+        """trees: per survey (leaf_max, amalgamation) of its assembly tree, or
+        None for the library defaults (see tune_trees)."""
         import torch
         self.torch = torch
         self.streams = [torch.cuda.Stream() for _ in surveys]
+        trees = trees or [(0, None)] * len(surveys)
         self.models = [tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, alpha,
-                                 precision=precision, stream=st.cuda_stream)
-                       for s, st in zip(surveys, self.streams)]
+                                 precision=precision, stream=st.cuda_stream, leaf_max=tr[0], amalgamation=tr[1])
+                       for s, st, tr in zip(surveys, self.streams, trees)]
         self.graph = None
 
     def close(self):
@@ -71,3 +74,18 @@ class Batch:
         for c in self.ctxs:
             tem.tem_status(c)
         return self.d, self.jtw
+
+
+def tune_trees(surveys, xi, alpha, precision=tem.TEM_FP32_REFINED, cache=None, candidates=None):
+    """Assembly tree of every survey chosen by the autotuner: one measured
+    tuning per mesh size (surveys with the same number of cubes per side share
+    the choice: the tree depends on the mesh, not on the conductivities or the
+    loops).  Returns the per-survey (leaf_max, amalgamation) and the tables."""
+    from . import autotune
+    chosen, tables = {}, {}
+    for s in surveys:
+        if s.n in chosen:
+            continue
+        kw = {"cache": cache} if candidates is None else {"cache": cache, "candidates": candidates}
+        chosen[s.n], tables[s.n] = autotune.tune(s, xi, alpha, precision, **kw)
+    return [chosen[s.n] for s in surveys], tables

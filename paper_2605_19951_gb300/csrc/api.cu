@@ -734,7 +734,7 @@ void nodal_correct(tem_ctx *c, const int *pm, int np) {
 // refine_tol > 0 a pole stops once its correction on the unknowns the outputs
 // read (edges of parameter cells) is below refine_tol of the solution there,
 // and later sweeps run over the remaining poles only (a host read per step).
-int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
+int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps, bool join = true) {
   const int64_t N = c->mesh.N;
   const int nx = c->nrhs, m = c->m;
   cudaStream_t s = c->stream;
@@ -799,9 +799,11 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps) {
     pm = c->pmap;
     np = (int)keep.size();
   }
-  prof_begin(KC_REFINE_VEC);
-  launch_join_cx(c->xdf, x, int64_t(m) * N * nx, s);
-  prof_end(KC_REFINE_VEC);
+  if (join) {   // else the caller reads the pairs in xdf
+    prof_begin(KC_REFINE_VEC);
+    launch_join_cx(c->xdf, x, int64_t(m) * N * nx, s);
+    prof_end(KC_REFINE_VEC);
+  }
   return TEM_OK;
 }
 
@@ -1362,10 +1364,16 @@ int jvp_async(tem_ctx *c, const double *v, double *jv) {
     launch_dm_apply_df(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->ptet, c->mesh.P, v, c->sigma, c->vsdf,
                        c->mesh.nt, c->me1df, c->xi, c->gdf, c->b, c->m, N, c->nrhs, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
-  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine));
+  // FP32 mode: the residue sums read the refined pairs directly (no FP64 copy of the solutions)
+  const bool fp64 = c->precision == TEM_FP64;
+  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine, fp64));
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K,
-                 c->stream);
+  if (fp64)
+    launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K,
+                   c->stream);
+  else
+    launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->xdf, jv, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K,
+                   c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   return TEM_OK;
 }
@@ -1378,7 +1386,7 @@ int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
   // the adjoint solves feed only the cell sums over parameter cells, which
   // converge in fewer corrections than the receivers' fields (46^3 box: within
   // 1e-7 of the converged J^T w after 6)
-  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine_adj));
+  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine_adj, c->precision == TEM_FP64));   // FP32: pairs in xdf
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   if (c->precision == TEM_FP64)
     launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->nrhs,
@@ -1698,6 +1706,24 @@ int tem_export_forward(tem_ctx *c, double *g) {
         g[o] = v.x;
         g[o + 1] = v.y;
       }
+  return TEM_OK;
+}
+
+int tem_level_info(tem_ctx *c, int64_t *out) {
+  if (!c || !out) return TEM_ERR_ARG;
+  if (!(c->state & ST_MESH)) return fail(c, TEM_ERR_STATE, "tem_mesh first");
+  const Symbolic &S = c->es.sym;
+  for (size_t h = 0; h < S.levels.size(); h++) {
+    int64_t *o = out + 4 * h;
+    o[0] = (int64_t)S.levels[h].fronts.size();
+    o[1] = o[2] = o[3] = 0;
+    for (int32_t f : S.levels[h].fronts) {
+      const Front &F = S.fronts[f];
+      o[1] += int64_t(F.k) * (F.k + 1) / 2;
+      o[2] += int64_t(F.k) * (F.n - F.k);
+      o[3] = std::max<int64_t>(o[3], F.k);
+    }
+  }
   return TEM_OK;
 }
 

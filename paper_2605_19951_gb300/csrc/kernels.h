@@ -336,6 +336,10 @@ void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s
 void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_val,
                     const double2 *alpha, const c128 *y, double *d, int m, int64_t N, int nrhs,
                     int ntx, int n_rx, int K, cudaStream_t s);
+// the same from the refined iterate's double-float pairs [m][N][nrhs] (FP32 mode, no FP64 copy)
+void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_val,
+                    const double2 *alpha, const float4 *y, double *d, int m, int64_t N, int nrhs,
+                    int ntx, int n_rx, int K, cudaStream_t s);
 // rhs_p[dof][x] = sum_r Qt[dof][r] sum_j alpha_pj w[x][r][j], x < ntx (zeroes rhs first)
 void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
                    const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,

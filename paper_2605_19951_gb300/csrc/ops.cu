@@ -195,11 +195,18 @@ void launch_real_to_c128(const double *f, c128 *b, int64_t count, cudaStream_t s
 
 constexpr int kMaxPoles = 32;
 
+// an entry of y in FP64: complex FP64, or a double-float pair (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ c128 as_c128(c128 v) { return v; }
+__device__ __forceinline__ c128 as_c128(float4 v) {
+  return mk<double>(double(v.x) + double(v.y), double(v.z) + double(v.w));
+}
+
 // d[x][r][j] = 2 Re sum_p alpha[p][j] (Q y_p)[r][x] for the ntx transmitters
 // (y rows hold nrhs >= ntx right-hand sides; the rest are padding)
+template <typename T>
 __global__ void k_residue(const int64_t *__restrict__ q_rp, const int32_t *__restrict__ q_ci,
                           const double *__restrict__ q_val, const double2 *__restrict__ alpha,
-                          const c128 *__restrict__ y, double *__restrict__ d, int m, int64_t N,
+                          const T *__restrict__ y, double *__restrict__ d, int m, int64_t N,
                           int nrhs, int ntx, int n_rx, int K) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= int64_t(n_rx) * ntx) return;
@@ -207,9 +214,9 @@ __global__ void k_residue(const int64_t *__restrict__ q_rp, const int32_t *__res
   c128 yq[kMaxPoles];
   for (int p = 0; p < m; p++) {
     c128 acc = mk<double>(0.0, 0.0);
-    const c128 *yp = y + p * N * nrhs;
+    const T *yp = y + p * N * nrhs;
     for (int64_t z = q_rp[r]; z < q_rp[r + 1]; z++) {
-      const c128 v = yp[int64_t(q_ci[z]) * nrhs + x];
+      const c128 v = as_c128(yp[int64_t(q_ci[z]) * nrhs + x]);
       acc.x += q_val[z] * v.x;
       acc.y += q_val[z] * v.y;
     }
@@ -230,7 +237,15 @@ void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_va
                     int ntx, int n_rx, int K, cudaStream_t s) {
   const int64_t cnt = int64_t(n_rx) * ntx;
   tem::count_launch();
-  k_residue<<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, ntx, n_rx, K);
+  k_residue<c128><<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, ntx, n_rx, K);
+}
+
+void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_val,
+                    const double2 *alpha, const float4 *y, double *d, int m, int64_t N, int nrhs,
+                    int ntx, int n_rx, int K, cudaStream_t s) {
+  const int64_t cnt = int64_t(n_rx) * ntx;
+  tem::count_launch();
+  k_residue<float4><<<div_up(cnt, 128), 128, 0, s>>>(q_rp, q_ci, q_val, alpha, y, d, m, N, nrhs, ntx, n_rx, K);
 }
 
 // rhs_p[qdof][x] = sum_{r} Qt[qdof][r] * sum_j alpha[p][j] w[x][r][j], x < ntx

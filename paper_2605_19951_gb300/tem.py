@@ -61,6 +61,7 @@ SIGNATURES = {
     "tem_export_pattern": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P, _P, _P, _P]),
     "tem_export_forward": (ctypes.c_int, [_P, _P]),
     "tem_export_dofs": (ctypes.c_int, [_P, _P]),
+    "tem_level_info": (ctypes.c_int, [_P, _P]),
 }
 
 
@@ -310,6 +311,13 @@ def tem_export_dofs(ctx):
     ev = np.zeros((n, 2), dtype=np.int64)
     _check(ctx, load().tem_export_dofs(ctx, ev.ctypes.data_as(_P)))
     return ev
+
+
+def tem_level_info(ctx):
+    """Per assembly-tree level: fronts, pivot-block entries, update-row entries, largest k."""
+    out = np.zeros((tem_info(ctx)["n_levels"], 4), dtype=np.int64)
+    _check(ctx, load().tem_level_info(ctx, out.ctypes.data_as(_P)))
+    return out
 
 
 def tem_export_forward(ctx):
