@@ -150,6 +150,28 @@ int tem_poles(tem_ctx *ctx, int32_t m, const double *xi, int32_t n_times,
 int tem_times(tem_ctx *ctx, int32_t n_times, const double *t, int32_t n_z, double z_min,
               double z_max, double mu, double *alpha_out);
 
+/* Poles of the rational approximant fitted on the device (Section 2.3; the
+ * paper fits them with RKFIT).  Variable projection: for given poles the
+ * residues of every time are the penalised least-squares fit of tem_times
+ * (same sample set, same penalty), and the poles minimise the sum over the
+ * times of the squared residuals,
+ *   f(xi) = sum_j || (I - Q Q^T) [exp(-t_j z); 0] ||^2   (Q from the QR of the basis),
+ * by Levenberg-Marquardt steps on p = (log(-Re xi_i), log(Im xi_i)) (which
+ * keeps Re xi < 0 < Im xi) with Kaufman's Jacobian -(I - Q Q^T)(dB/dp) c_j,
+ * formed and reduced to the normal equations on the device (FP64); the host
+ * solves the 2m x 2m step, and at most a factor e^2 per step in any part of
+ * a pole.  Stops after max_iter steps, when no step decreases f, or when the
+ * relative decrease is below 1e-12.
+ *   t      host [n_times] fitting times (> 0; 1 <= n_times <= 4096), 1 <= m <= 32
+ *   xi     host [m][2] starting poles in (Re < 0 < Im), fitted poles out
+ *   obj    host [3] out: f at the start, f at the end, steps taken
+ *   stream cudaStream_t (NULL: the default stream) of the current device
+ * Needs no context (errors: tem_last_error(NULL)); allocates and frees its
+ * own work arrays and synchronises.  TEM_ERR_ARG for bad arguments or
+ * starting poles that leave the fit rank deficient. */
+int tem_fit_poles(int32_t m, int32_t n_times, const double *t, int32_t n_z, double z_min, double z_max,
+                  double mu, int32_t max_iter, double *xi, double *obj, void *stream);
+
 /* Transmitters and receivers (Section 2.1 source, Section 4.2 observation).
  *   loop_ptr  host [n_tx+1]  offsets into loop_verts
  *   loop_verts host          closed polylines of vertex ids; consecutive ids

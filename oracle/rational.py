@@ -69,6 +69,24 @@ def _xi_of(p, m):
     return -np.exp(p[:m]) + 1j * np.exp(p[m:])
 
 
+def seed_poles(m, t0=1e-5, t1=1e-2, seed_angle=0.7):
+    """Starting poles of the fit: moduli log-spaced over [0.3 / t1, 30 / t0]
+    (the decay rates the time range resolves) at the angle seed_angle * pi
+    from the positive real axis (Re < 0 < Im)."""
+    rho = np.logspace(np.log10(0.3 / t1), np.log10(30.0 / t0), m)
+    th = np.pi * seed_angle
+    return rho * np.cos(th) + 1j * rho * np.sin(th)
+
+
+def vp_objective(xi, times, z=None, mu=MU):
+    """Variable-projection objective of a pole set: sum over the times of the
+    squared residual of the penalised least-squares residue fit."""
+    z = sample_points() if z is None else z
+    Ba, Ea = _augmented(z, xi, np.exp(-np.outer(z, times)), mu)
+    coef, *_ = np.linalg.lstsq(Ba, Ea, rcond=None)
+    return float(np.sum((Ba @ coef - Ea) ** 2))
+
+
 def fit_poles(m, t0=1e-5, t1=1e-2, n_times=40, seed_angle=0.7, max_nfev=300, mu=MU):
     """Shared poles for t in [t0, t1] by variable projection."""
     z = sample_points()
@@ -80,9 +98,8 @@ def fit_poles(m, t0=1e-5, t1=1e-2, n_times=40, seed_angle=0.7, max_nfev=300, mu=
         coef, *_ = np.linalg.lstsq(Ba, Ea, rcond=None)
         return (Ba @ coef - Ea).ravel()
 
-    rho = np.logspace(np.log10(0.3 / t1), np.log10(30.0 / t0), m)
-    th = np.pi * seed_angle
-    p0 = np.concatenate([np.log(-rho * np.cos(th)), np.log(rho * np.sin(th))])
+    x0 = seed_poles(m, t0, t1, seed_angle)
+    p0 = np.concatenate([np.log(-x0.real), np.log(x0.imag)])
     sol = least_squares(resid, p0, method="trf", max_nfev=max_nfev, x_scale=1.0)
     xi = _xi_of(sol.x, m)
     return xi[np.argsort(np.abs(xi))]

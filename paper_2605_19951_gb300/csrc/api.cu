@@ -1248,6 +1248,164 @@ int tem_times(tem_ctx *c, int32_t n_times, const double *t, int32_t n_z, double 
   return TEM_OK;
 }
 
+int tem_fit_poles(int32_t m, int32_t n_times, const double *t, int32_t n_z, double z_min, double z_max, double mu,
+                  int32_t max_iter, double *xi, double *obj, void *stream) {
+  tem_ctx *c = nullptr;   // no context: errors go to tem_last_error(NULL)
+  if (m <= 0 || m > 32 || n_times <= 0 || n_times > 4096 || !t || !xi || !obj || max_iter < 0 || max_iter > 100000)
+    return fail(c, TEM_ERR_ARG, "bad pole-fit arguments (1 <= m <= 32, 1 <= n_times <= 4096)");
+  for (int j = 0; j < n_times; j++)
+    if (!(t[j] > 0) || !std::isfinite(t[j])) return fail(c, TEM_ERR_ARG, "every time must be finite and > 0");
+  if (n_z < 2 || n_z > (1 << 20) || !(z_min > 0) || !(z_max > z_min) || !std::isfinite(z_max) || !(mu >= 0) ||
+      !std::isfinite(mu))
+    return fail(c, TEM_ERR_ARG, "bad sample set (2 <= n_z <= 2^20, 0 < z_min < z_max finite, mu >= 0)");
+  for (int i = 0; i < m; i++)
+    if (!(xi[2 * i] < 0) || !(xi[2 * i + 1] > 0) || !std::isfinite(xi[2 * i]) || !std::isfinite(xi[2 * i + 1]))
+      return fail(c, TEM_ERR_ARG, "starting poles need Re xi < 0 < Im xi");
+  const int K = n_times, nc = 2 * m;
+  const int64_t rows = int64_t(n_z) + 1 + nc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  struct Scratch {
+    std::vector<void *> p;
+    ~Scratch() {
+      for (void *q : p) cudaFree(q);
+    }
+  } w;
+  auto get = [&](size_t bytes, void **out) {
+    *out = nullptr;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+    w.p.push_back(*out);
+    return int(TEM_OK);
+  };
+  double *B, *Y, *rd, *cf, *td, *coef, *tail, *T, *G;
+  double2 *xd;
+  TRY(get(sizeof(double) * rows * nc, (void **)&B));
+  TRY(get(sizeof(double) * rows * K, (void **)&Y));
+  TRY(get(sizeof(double) * nc, (void **)&rd));
+  TRY(get(sizeof(double) * nc, (void **)&cf));
+  TRY(get(sizeof(double) * K, (void **)&td));
+  TRY(get(sizeof(double) * nc * K, (void **)&coef));
+  TRY(get(sizeof(double) * K, (void **)&tail));
+  TRY(get(sizeof(double) * rows * nc * K, (void **)&T));
+  TRY(get(sizeof(double) * nc * (nc + 1), (void **)&G));
+  TRY(get(sizeof(double2) * m, (void **)&xd));
+  const double lz0 = std::log10(z_min), lz1 = std::log10(z_max);
+  CK(cudaMemcpyAsync(td, t, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  auto poles_of = [&](const std::vector<double> &p) {
+    std::vector<double> x(2 * m);
+    for (int i = 0; i < m; i++) {
+      x[2 * i] = -std::exp(p[i]);
+      x[2 * i + 1] = std::exp(p[m + i]);
+    }
+    return x;
+  };
+  // objective sum_j ||(I - Q Q^T) e_j||^2 at p (leaves B, Y and coef of p on the device); +inf if singular
+  auto eval = [&](const std::vector<double> &p, double *f) {
+    const std::vector<double> x = poles_of(p);
+    CK(cudaMemcpyAsync(xd, x.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, s));
+    launch_fit_qr(xd, m, n_z, lz0, lz1, mu, B, rd, cf, s);
+    std::vector<double> rdh(nc), th(K);
+    CK(cudaMemcpyAsync(rdh.data(), rd, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double rmax = 0;
+    for (double v : rdh) rmax = std::max(rmax, std::fabs(v));
+    for (double v : rdh)
+      if (!std::isfinite(v) || !(std::fabs(v) > 1e-14 * rmax)) {
+        *f = INFINITY;
+        return int(TEM_OK);
+      }
+    launch_fit_solve(B, m, n_z, lz0, lz1, rd, cf, td, K, Y, nullptr, s, coef, tail);
+    CK(cudaMemcpyAsync(th.data(), tail, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double sum = 0;
+    for (double v : th) sum += v;
+    *f = std::isfinite(sum) ? sum : INFINITY;
+    return int(TEM_OK);
+  };
+  std::vector<double> p(nc);
+  for (int i = 0; i < m; i++) {
+    p[i] = std::log(-xi[2 * i]);
+    p[m + i] = std::log(xi[2 * i + 1]);
+  }
+  double f = 0;
+  TRY(eval(p, &f));
+  if (!std::isfinite(f)) return fail(c, TEM_ERR_ARG, "the starting poles leave the residue fit rank deficient");
+  const double f0 = f;
+  double lam = 1e-3;
+  int it = 0;
+  std::vector<double> Gh(size_t(nc) * (nc + 1));
+  for (; it < max_iter; it++) {
+    // Levenberg-Marquardt step on the Kaufman normal equations (T^T T + lam diag) d = T^T y
+    launch_vp_normal(B, m, n_z, lz0, lz1, mu, xd, cf, coef, K, Y, T, G, s);
+    CK(cudaMemcpyAsync(Gh.data(), G, sizeof(double) * Gh.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    auto gel = [&](int a, int b) { return Gh[size_t(std::min(a, b)) * (nc + 1) + std::max(a, b)]; };
+    bool accepted = false;
+    double fn = f;
+    std::vector<double> pn(nc);
+    for (int tries = 0; tries < 30 && !accepted; tries++) {
+      // Cholesky of A = G + lam (diag(G) + 1e-9 trace(G) / nc): Marquardt's scaling, kept
+      // positive for parameters whose columns vanish (a residue of zero)
+      std::vector<double> A(size_t(nc) * nc), d(nc);
+      double tr = 0;
+      for (int a = 0; a < nc; a++) tr += gel(a, a);
+      for (int a = 0; a < nc; a++) {
+        for (int b = 0; b < nc; b++) A[size_t(a) * nc + b] = gel(a, b);
+        A[size_t(a) * nc + a] += lam * (gel(a, a) + 1e-9 * tr / nc);
+        d[a] = Gh[size_t(a) * (nc + 1) + nc];
+      }
+      bool spd = true;
+      for (int a = 0; a < nc && spd; a++) {
+        for (int b = 0; b <= a; b++) {
+          double v = A[size_t(a) * nc + b];
+          for (int q = 0; q < b; q++) v -= A[size_t(a) * nc + q] * A[size_t(b) * nc + q];
+          if (a == b) {
+            if (!(v > 0)) { spd = false; break; }
+            A[size_t(a) * nc + a] = std::sqrt(v);
+          } else {
+            A[size_t(a) * nc + b] = v / A[size_t(b) * nc + b];
+          }
+        }
+      }
+      if (spd) {
+        for (int a = 0; a < nc; a++) {   // L z = d, then L^T x = z
+          for (int q = 0; q < a; q++) d[a] -= A[size_t(a) * nc + q] * d[q];
+          d[a] /= A[size_t(a) * nc + a];
+        }
+        for (int a = nc - 1; a >= 0; a--) {
+          for (int q = a + 1; q < nc; q++) d[a] -= A[size_t(q) * nc + a] * d[q];
+          d[a] /= A[size_t(a) * nc + a];
+        }
+        double dmax = 0;   // at most a factor e^2 per step in any pole's real or imaginary part
+        for (int a = 0; a < nc; a++) dmax = std::max(dmax, std::fabs(d[a]));
+        const double sc = dmax > 2.0 ? 2.0 / dmax : 1.0;
+        for (int a = 0; a < nc; a++) pn[a] = p[a] + sc * d[a];
+        TRY(eval(pn, &fn));
+        if (fn < f) accepted = true;
+      }
+      if (!accepted) lam *= 4.0;
+    }
+    if (!accepted) {   // no descent left: restore the device state of p and stop
+      TRY(eval(p, &f));
+      break;
+    }
+    const double rel = (f - fn) / f;
+    p = pn;
+    f = fn;
+    lam = std::max(lam / 3.0, 1e-12);
+    if (rel < 1e-12) {
+      it++;
+      break;
+    }
+  }
+  const std::vector<double> x = poles_of(p);
+  std::copy(x.begin(), x.end(), xi);
+  obj[0] = f0;
+  obj[1] = f;
+  obj[2] = double(it);
+  return TEM_OK;
+}
+
 int tem_sources(tem_ctx *c, int32_t n_tx, const int64_t *loop_ptr, const int32_t *loop_verts, int32_t n_rx,
                 const double *rx) {
   if (!c) return TEM_ERR_ARG;

@@ -378,7 +378,13 @@ void launch_axpy(const double *m, const double *dm, double eta, double *out, int
 void launch_fit_qr(const double2 *xi, int m, int64_t nz, double lz0, double lz1, double mu, double *B,
                    double *rdiag, double *cf, cudaStream_t s);
 void launch_fit_solve(const double *B, int m, int64_t nz, double lz0, double lz1, const double *rdiag,
-                      const double *cf, const double *t, int K, double *Y, double2 *alpha, cudaStream_t s);
+                      const double *cf, const double *t, int K, double *Y, double2 *alpha, cudaStream_t s,
+                      double *coef = nullptr, double *tail_sq = nullptr);
+// variable projection: Kaufman Jacobian tails T [K][2m][rows] and the normal
+// equations G [2m][2m + 1] (J^T J | J^T r up to sign) of the pole fit
+void launch_vp_normal(const double *B, int m, int64_t nz, double lz0, double lz1, double mu, const double2 *xi,
+                      const double *cf, const double *coef, int K, const double *Y, double *T, double *G,
+                      cudaStream_t s);
 
 // status words before a factorisation (a kernel, so that the call stays capturable)
 void launch_status_init(DevStatus *st, cudaStream_t s);

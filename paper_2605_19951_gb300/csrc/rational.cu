@@ -113,7 +113,9 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_solve(const double *__restr
                                                            const double *__restrict__ rdiag,
                                                            const double *__restrict__ cf,
                                                            const double *__restrict__ t, int K,
-                                                           double *__restrict__ Y, double2 *__restrict__ alpha) {
+                                                           double *__restrict__ Y, double2 *__restrict__ alpha,
+                                                           double *__restrict__ coef_out,
+                                                           double *__restrict__ tail_sq) {
   __shared__ double red[kFitThreads / 32];
   __shared__ double coef[64];
   const int j = blockIdx.x, ncol = 2 * m;
@@ -130,14 +132,92 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_solve(const double *__restr
     for (int64_t r = q + threadIdx.x; r < rows; r += kFitThreads) y[r] -= d * v[r];
     __syncthreads();
   }
+  if (tail_sq) {   // the least-squares residual: the part of Q^T e beyond the first ncol rows
+    double ss = 0.0;
+    for (int64_t r = ncol + threadIdx.x; r < rows; r += kFitThreads) ss += y[r] * y[r];
+    ss = block_sum(ss, red);
+    if (threadIdx.x == 0) tail_sq[j] = ss;
+  }
   if (threadIdx.x == 0) {
     for (int i = ncol - 1; i >= 0; i--) {
       double s = y[i];
       for (int q = i + 1; q < ncol; q++) s -= B[int64_t(q) * rows + i] * coef[q];
       coef[i] = s / rdiag[i];
     }
-    for (int i = 0; i < m; i++) alpha[int64_t(i) * K + j] = make_double2(coef[i], coef[m + i]);
+    if (alpha)
+      for (int i = 0; i < m; i++) alpha[int64_t(i) * K + j] = make_double2(coef[i], coef[m + i]);
+    if (coef_out)
+      for (int i = 0; i < ncol; i++) coef_out[int64_t(i) * K + j] = coef[i];
   }
+}
+
+// Variable projection (the poles as the unknowns, the residues eliminated by
+// least squares): Kaufman's Jacobian of the residual r_j = (I - Q Q^T) e_j
+// with respect to parameter q is -(I - Q Q^T) (dB/dp_q) c_j, c_j the
+// coefficients of time j.  With p_i = log(-Re xi_i) and p_{m+i} = log(Im xi_i),
+// dxi_i/dp_i = Re xi_i and dxi_i/dp_{m+i} = i Im xi_i; only the two columns of
+// pole i depend on them: d(2 Re c)/dp = 2 Re(c^2 dxi), d(-2 Im c)/dp =
+// -2 Im(c^2 dxi) with c = 1/(z - xi), and the penalty rows mu / |xi_i| give
+// -mu Re(conj(xi_i) dxi) / |xi_i|^3.  One CTA per (parameter q, time j): the
+// vector (dB/dp_q) c_j, reduced by Q^T, keeps its rows beyond ncol (the
+// projection's range, in the rotated basis) in T[(j * 2m + q) * rows ...].
+__global__ void __launch_bounds__(kFitThreads) k_vp_jac(const double *__restrict__ B, int64_t rows, int m,
+                                                        int64_t nz, double lz0, double lz1, double mu,
+                                                        const double2 *__restrict__ xi,
+                                                        const double *__restrict__ cf,
+                                                        const double *__restrict__ coef, int K,
+                                                        double *__restrict__ T) {
+  __shared__ double red[kFitThreads / 32];
+  const int ncol = 2 * m, q = blockIdx.x, j = blockIdx.y, i = q % m;
+  double *g = T + (int64_t(j) * ncol + q) * rows;
+  const double xr = xi[i].x, xq = xi[i].y;
+  // dxi/dp = (dr, di)
+  const double dr = q < m ? xr : 0.0, di = q < m ? 0.0 : xq;
+  const double ca = coef[int64_t(i) * K + j], cb = coef[int64_t(m + i) * K + j];
+  for (int64_t r = threadIdx.x; r < rows; r += kFitThreads) {
+    double v = 0.0;
+    if (r <= nz) {
+      const double z = sample_z(r, nz, lz0, lz1);
+      const double a = z - xr, b = -xq, d = a * a + b * b;   // z - xi = a + i b, c = (a - i b) / d
+      const double cr = a / d, ci = -b / d;
+      const double sr = cr * cr - ci * ci, si = 2.0 * cr * ci;   // c^2
+      const double wr = sr * dr - si * di, wi = sr * di + si * dr;   // c^2 dxi
+      v = 2.0 * wr * ca - 2.0 * wi * cb;
+    } else if (r - nz - 1 == i || r - nz - 1 == m + i) {
+      const double n2 = xr * xr + xq * xq;
+      const double dpen = -mu * (xr * dr + xq * di) / (n2 * sqrt(n2));
+      v = dpen * (r - nz - 1 == i ? ca : cb);
+    }
+    g[r] = v;
+  }
+  __syncthreads();
+  for (int h = 0; h < ncol; h++) {
+    const double *v = B + int64_t(h) * rows;
+    double d = 0.0;
+    for (int64_t r = h + threadIdx.x; r < rows; r += kFitThreads) d += v[r] * g[r];
+    d = cf[h] * block_sum(d, red);
+    for (int64_t r = h + threadIdx.x; r < rows; r += kFitThreads) g[r] -= d * v[r];
+    __syncthreads();
+  }
+}
+
+// Normal equations of the Levenberg-Marquardt step from the projected tails:
+// G[a][b] = sum_j <T_aj, T_bj> (a, b < ncol) and G[a][ncol] = sum_j <T_aj, Y_j>
+// over the rows beyond ncol; one CTA per (a, b) with b <= ncol.
+__global__ void __launch_bounds__(kFitThreads) k_vp_gram(const double *__restrict__ T,
+                                                         const double *__restrict__ Y, int64_t rows, int ncol,
+                                                         int K, double *__restrict__ G) {
+  __shared__ double red[kFitThreads / 32];
+  const int a = blockIdx.x, b = blockIdx.y;
+  if (b < a && b < ncol) return;
+  double s = 0.0;
+  for (int j = 0; j < K; j++) {
+    const double *ta = T + (int64_t(j) * ncol + a) * rows;
+    const double *tb = b < ncol ? T + (int64_t(j) * ncol + b) * rows : Y + int64_t(j) * rows;
+    for (int64_t r = ncol + threadIdx.x; r < rows; r += kFitThreads) s += ta[r] * tb[r];
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) G[a * (ncol + 1) + b] = s;
 }
 
 void launch_fit_qr(const double2 *xi, int m, int64_t nz, double lz0, double lz1, double mu, double *B,
@@ -151,9 +231,21 @@ void launch_fit_qr(const double2 *xi, int m, int64_t nz, double lz0, double lz1,
 }
 
 void launch_fit_solve(const double *B, int m, int64_t nz, double lz0, double lz1, const double *rdiag,
-                      const double *cf, const double *t, int K, double *Y, double2 *alpha, cudaStream_t s) {
+                      const double *cf, const double *t, int K, double *Y, double2 *alpha, cudaStream_t s,
+                      double *coef, double *tail_sq) {
   tem::count_launch();
-  k_fit_solve<<<K, kFitThreads, 0, s>>>(B, nz + 1 + 2 * m, m, nz, lz0, lz1, rdiag, cf, t, K, Y, alpha);
+  k_fit_solve<<<K, kFitThreads, 0, s>>>(B, nz + 1 + 2 * m, m, nz, lz0, lz1, rdiag, cf, t, K, Y, alpha, coef,
+                                        tail_sq);
+}
+
+void launch_vp_normal(const double *B, int m, int64_t nz, double lz0, double lz1, double mu, const double2 *xi,
+                      const double *cf, const double *coef, int K, const double *Y, double *T, double *G,
+                      cudaStream_t s) {
+  const int64_t rows = nz + 1 + 2 * m;
+  tem::count_launch();
+  k_vp_jac<<<dim3(2 * m, K), kFitThreads, 0, s>>>(B, rows, m, nz, lz0, lz1, mu, xi, cf, coef, K, T);
+  tem::count_launch();
+  k_vp_gram<<<dim3(2 * m, 2 * m + 1), kFitThreads, 0, s>>>(T, Y, rows, 2 * m, K, G);
 }
 
 }  // namespace tem

@@ -35,6 +35,7 @@ SIGNATURES = {
     "tem_mesh": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _P, _I32]),
     "tem_poles": (ctypes.c_int, [_P, _I32, _P, _I32, _P]),
     "tem_times": (ctypes.c_int, [_P, _I32, _P, _I32, _D, _D, _D, _P]),
+    "tem_fit_poles": (ctypes.c_int, [_I32, _I32, _P, _I32, _D, _D, _D, _I32, _P, _P, _P]),
     "tem_sources": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
     "tem_factor": (ctypes.c_int, [_P, _P]),
     "tem_forward": (ctypes.c_int, [_P, _P]),
@@ -164,6 +165,21 @@ def tem_times(ctx, times, n_z=2200, z_min=1e-2, z_max=1e9, mu=1e-4):
     _check(ctx, load().tem_times(ctx, t.shape[0], pt, int(n_z), float(z_min), float(z_max), float(mu),
                                  out.ctypes.data_as(_P)))
     return out[..., 0] + 1j * out[..., 1]
+
+
+def tem_fit_poles(xi0, times, n_z=2200, z_min=1e-2, z_max=1e9, mu=1e-4, max_iter=300, stream=None):
+    """Poles fitted on the device by variable projection from the starting
+    poles xi0 (complex, Re < 0 < Im) for the fitting times; returns
+    (poles, (f_start, f_end, steps))."""
+    xi0 = np.asarray(xi0, dtype=np.complex128)
+    x = np.ascontiguousarray(np.stack([xi0.real, xi0.imag], axis=-1), dtype=np.float64)
+    t, pt = _host(times, np.float64)
+    obj = np.zeros(3)
+    code = load().tem_fit_poles(xi0.shape[0], t.shape[0], pt, int(n_z), float(z_min), float(z_max), float(mu),
+                                int(max_iter), x.ctypes.data_as(_P), obj.ctypes.data_as(_P),
+                                None if stream is None else _P(int(stream)))
+    _check(None, code)
+    return x[:, 0] + 1j * x[:, 1], tuple(obj)
 
 
 def tem_sources(ctx, loops, rx):

@@ -163,3 +163,41 @@ def test_times_arguments_are_checked():
         assert mdl.info()["n_times"] == 16   # a refused call changes nothing
     finally:
         mdl.close()
+
+
+@pytest.mark.parametrize("m", [8, 10])
+def test_pole_fit_matches_the_stored_fit(m):
+    """Poles fitted on the device by variable projection (tem_fit_poles) from
+    the oracle fit's starting poles, on the same 40 times, sample set and
+    penalty as the stored tables (which the oracle's fit wrote: scipy's
+    trust-region least squares on the same objective).  A nonlinear fit has no
+    unique answer, so the test compares what the method fixes: the device's
+    objective is the oracle's objective evaluated at the device's poles, it is
+    no worse than the stored poles' (within 0.1%), the approximant's max error
+    against exp on the check grid is within 10% of the stored one's, the
+    poles stay in Re < 0 < Im, and their imaginary parts (sorted) agree with
+    the stored poles' within 1%."""
+    tem = _tem()
+    t = inputs.times_log(40)
+    xs, _ = inputs.load_rational(m, t)
+    xi, (f0, f1, steps) = tem.tem_fit_poles(rational.seed_poles(m), t, max_iter=400)
+    f_ref = rational.vp_objective(xs, t)
+    assert f1 < f0 and steps > 0
+    assert abs(f1 - rational.vp_objective(xi, t)) <= 1e-8 * f1
+    assert f1 <= 1.001 * f_ref, (f1, f_ref)
+    e_dev = rational.max_error(xi, rational.fit_alpha(xi, t), t).max()
+    e_ref = rational.max_error(xs, rational.fit_alpha(xs, t), t).max()
+    assert e_dev <= 1.1 * e_ref, (e_dev, e_ref)
+    assert np.all(xi.real < 0) and np.all(xi.imag > 0)
+    im_dev, im_ref = np.sort(xi.imag), np.sort(xs.imag)
+    assert np.all(np.abs(im_dev - im_ref) <= 1e-2 * im_ref), (im_dev, im_ref)
+
+
+def test_pole_fit_arguments_are_checked():
+    tem = _tem()
+    t = inputs.times_log(8)
+    for bad in (np.array([1.0 + 1.0j]), np.array([-1.0 - 1.0j])):   # Re >= 0, Im <= 0
+        with pytest.raises(tem.TemError, match="TEM_ERR_ARG"):
+            tem.tem_fit_poles(bad, t)
+    with pytest.raises(tem.TemError, match="TEM_ERR_ARG"):
+        tem.tem_fit_poles(rational.seed_poles(4), np.array([-1.0]))
