@@ -68,6 +68,11 @@ def parse():
                          "one CUDA graph per wave of models")
     ap.add_argument("--c5-budget-gb", type=float, default=110.0,
                     help="device memory per C5 wave (estimated from the factor entries)")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the bench line: factor / forward / pair times of C1-C3 on the GPU in both "
+                         "precisions and of the oracle on this host for C1-C2")
+    ap.add_argument("--peaks", action="store_true",
+                    help="instead of the bench line: cuBLAS FP64, FP32 and TF32 GEMM rates (torch.matmul)")
     ap.add_argument("--n", type=int, default=46,
                     help="cubes per side (46 = the 700k-DoF workload; smaller only for profiling captures)")
     return ap.parse_args()
@@ -566,9 +571,85 @@ def run_c5(args):
     print(json.dumps(out), flush=True)
 
 
+def run_peaks(args):
+    """Dense-GEMM rates of the pipes the method uses, measured with cuBLAS
+    through torch.matmul (square n^3 products, 2 n^3 flops, best of 10 after
+    warm-up, CUDA events): FP64, FP32 with TF32 off (the SIMT FP32 pipe) and
+    TF32 (the tensor pipe the solve products and front updates run on)."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {"how": "torch.matmul n^3, 2 n^3 flops, best of 10 (CUDA events)"}
+    for name, dt, tf32, n in (("fp64", torch.float64, False, 4096), ("fp32_simt", torch.float32, False, 8192),
+                              ("tf32", torch.float32, True, 8192)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = min(timed(torch, lambda: torch.matmul(a, b))[0] for _ in range(10))
+        out[name + "_tflops"] = round(2.0 * n ** 3 / (best * 1e-3) / 1e12, 2)
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    print(json.dumps(out), flush=True)
+
+
+def run_configs(args):
+    """Configurations C1-C3: GPU factor, forward and J.v + J^T.w pair times
+    (CUDA events, median of 3) in both precisions, and the oracle on this host
+    (factor + forward + one pair, poles on parallel threads) for C1 and C2."""
+    import numpy as np
+    import torch
+    from oracle.tem import Oracle
+    from paper_2605_19951_gb300 import inputs, tem
+    torch.cuda.set_device(0)
+    rows = []
+    for cfg in (1, 2, 3):
+        s = inputs.make_config(cfg)
+        xi, al = inputs.load_rational(s.m, s.times)
+        rng = np.random.default_rng(cfg)
+        v = rng.standard_normal(s.n_param)
+        w = rng.standard_normal((len(s.loops), len(s.rx), len(s.times)))
+        row = {"config": f"C{cfg}", "n": s.n, "poles": s.m, "loops": len(s.loops)}
+        for prec, name in ((tem.TEM_FP64, "fp64"), (tem.TEM_FP32_REFINED, "fp32r")):
+            mdl = tem.Model(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al, precision=prec)
+            try:
+                m0 = torch.as_tensor(s.log_sigma(), device="cuda")
+                vv, ww = torch.as_tensor(v, device="cuda"), torch.as_tensor(w, device="cuda")
+                mdl.factor(m0)
+                mdl.forward()
+                mdl.jvp(vv), mdl.jtvp(ww)
+                row[name + "_factor_ms"] = round(statistics.median([timed(torch, lambda: mdl.factor(m0))[0]
+                                                                    for _ in range(3)]), 2)
+                row[name + "_forward_ms"] = round(statistics.median([timed(torch, lambda: mdl.forward())[0]
+                                                                     for _ in range(3)]), 2)
+                row[name + "_pair_ms"] = round(statistics.median([timed(torch, lambda: (mdl.jvp(vv), mdl.jtvp(ww)))[0]
+                                                                  for _ in range(3)]), 2)
+                row["dof"] = mdl.info()["n_dof"]
+            finally:
+                mdl.close()
+            torch.cuda.empty_cache()
+        if cfg <= 2:
+            t0 = time.perf_counter()
+            o = Oracle(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al)
+            o.set_model(s.log_sigma())
+            o.forward()
+            t1 = time.perf_counter()
+            o.jvp(v)
+            o.jtvp(w)
+            t2 = time.perf_counter()
+            row.update({"oracle_factor_forward_s": round(t1 - t0, 2), "oracle_pair_s": round(t2 - t1, 2),
+                        "oracle_threads": int(o.threads), "nproc": os.cpu_count()})
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.c5:
+    if a.peaks:
+        run_peaks(a)
+    elif a.configs:
+        run_configs(a)
+    elif a.c5:
         run_c5(a)
     elif a.levels:
         run_levels(a)

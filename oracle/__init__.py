@@ -13,7 +13,9 @@ Modules
   fem       Kuhn-mesh edges, PEC mask, Whitney element matrices, K and M(sigma)
   survey    source vectors f (loop line integrals) and observation operator Q
   tem       shifted solves, residue sums, J.v, J^T.w
-  rational  pole/coefficient fit of exp(-t z) and its error
+  rational  pole/coefficient fit of exp(-t z), its seed poles, objective and error
   inversion RT0 two-point regulariser and LSQR (Paige-Saunders)
+  gn        Gauss-Newton loop (Armijo backtracking, lambda cooling) on the oracle's products
+  fit_poles script writing the stored pole / residue tables (calls rational only)
   halfspace closed-form step-off dB_z/dt of a loop on a half-space
 """
