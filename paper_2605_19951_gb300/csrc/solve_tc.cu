@@ -429,6 +429,56 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     const bool ok = ki_wait(a, sh, &sh.accf[buf], use & 1);
     if (!__all_sync(kFull, ok)) break;
     tc::fence_after();
+    if constexpr (MODE == PM_UPD) {
+      // F[r][s] -= acc for the tile's columns s >= t0 with r >= s, r = row m of the tile (lane):
+      // the accumulator is read in two halves of 16 columns (32 registers each), and within a
+      // half four columns at a time have all their loads issued before their stores, so a
+      // batch waits for one memory latency rather than four (distinct entries; the compiler
+      // cannot prove it and would keep each load behind the previous store).  The buffer is
+      // released after both halves.
+      const int m = e;
+      const FrontDev f = a.F[it.t.map];
+      const int64_t r = int64_t(it.t.y0) + m, k = f.k, n = f.n;
+      c64 *lp = a.Lw + int64_t(it.p) * a.lstride + f.lofs;
+      c64 *up = a.Uw + int64_t(it.p) * a.ustride + f.uofs;
+      const int q0 = int(it.t.mfirst);
+      const bool row_ok = m < it.t.mrows;
+      auto col = [&](int64_t sc) { return sc < k ? lp + sc * f.ld + r : up + (sc - k) * (n - k) + (r - k); };
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        float v[32];
+        if (it.nch > 0) {
+          tc::tmem_ld16(sh.tmem + (uint32_t(we * 32) << 16) + 64 * buf + 32 * h, v);
+          tc::tmem_ld16(sh.tmem + (uint32_t(we * 32) << 16) + 64 * buf + 32 * h + 16, v + 16);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; q++) v[q] = 0.f;
+        }
+        if (!row_ok) continue;
+#pragma unroll
+        for (int qb = 0; qb < 16; qb += 4) {
+          c64 o[4];
+          unsigned msk = 0;
+#pragma unroll
+          for (int x = 0; x < 4; x++) {
+            const int q = 16 * h + qb + x;
+            const int64_t sc = int64_t(it.t.bbase) + q;
+            if (q < q0 || sc >= n || sc > r) continue;
+            msk |= 1u << x;
+            o[x] = *col(sc);
+          }
+#pragma unroll
+          for (int x = 0; x < 4; x++)
+            if ((msk >> x) & 1u) {
+              const int q = 16 * h + qb + x, c = qb + x;
+              *col(int64_t(it.t.bbase) + q) = mk<float>(o[x].x - v[2 * c], o[x].y - v[2 * c + 1]);
+            }
+        }
+      }
+      tc::fence_before();
+      tc::mbar_arrive(&sh.acce[buf]);
+      continue;
+    }
     float v[64];
     if (it.nch > 0) {
       tc::tmem_ld64(sh.tmem + (uint32_t(we * 32) << 16) + 64 * buf, v);
@@ -440,24 +490,7 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     tc::mbar_arrive(&sh.acce[buf]);
     const int m = e;
     if (m >= it.t.mrows) continue;
-    if (MODE == PM_UPD) {
-      // F[r][s] -= acc for the tile's columns s >= t0 with r >= s: one column per step, the warp's
-      // 32 lanes on 32 consecutive rows of it
-      const FrontDev f = a.F[it.t.map];
-      const int64_t r = int64_t(it.t.y0) + m, k = f.k, n = f.n;
-      c64 *lp = a.Lw + int64_t(it.p) * a.lstride + f.lofs;
-      c64 *up = a.Uw + int64_t(it.p) * a.ustride + f.uofs;
-      const int q0 = int(it.t.mfirst);
-#pragma unroll
-      for (int q = 0; q < 32; q++) {   // fully unrolled: v stays in registers
-        const int64_t sc = int64_t(it.t.bbase) + q;
-        if (q < q0 || sc >= n || sc > r) continue;
-        c64 *dst = sc < k ? lp + sc * f.ld + r : up + (sc - k) * (n - k) + (r - k);
-        const c64 o = *dst;
-        *dst = mk<float>(o.x - v[2 * q], o.y - v[2 * q + 1]);
-      }
-      continue;
-    }
+
     const int ncols = min(32, a.nrhs - it.ch * 32);
     const int64_t pv = int64_t(it.p) * a.vstride + it.ch * 32;
     const int64_t row = MODE == PM_FWD21 ? int64_t(__ldg(a.rows + it.t.obase + m)) : int64_t(it.t.obase) + m;
