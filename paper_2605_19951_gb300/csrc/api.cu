@@ -734,7 +734,8 @@ void nodal_correct(tem_ctx *c, const int *pm, int np) {
 // refine_tol > 0 a pole stops once its correction on the unknowns the outputs
 // read (edges of parameter cells) is below refine_tol of the solution there,
 // and later sweeps run over the remaining poles only (a host read per step).
-int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps, bool join = true) {
+int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps, bool join = true,
+              bool b_in_pairs = false) {
   const int64_t N = c->mesh.N;
   const int nx = c->nrhs, m = c->m;
   cudaStream_t s = c->stream;
@@ -751,7 +752,8 @@ int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps, bo
   auto prof_begin = [&](int k) { if (g_prof) g_prof->begin(k, s); };
   auto prof_end = [&](int k) { if (g_prof) g_prof->end(k, s); };
   prof_begin(KC_REFINE_VEC);
-  launch_split_cx(b, bdf, (bstride ? int64_t(m) : int64_t(1)) * N * nx, s);
+  if (!b_in_pairs)   // else the caller wrote b as pairs into c->r already
+    launch_split_cx(b, bdf, (bstride ? int64_t(m) : int64_t(1)) * N * nx, s);
   c64 *Y = (c64 *)c->es.Y;
   launch_scale_to_work<float4>(bdf, bsd, Y, c->colmax_f, m, nullptr, N, nx, s);
   prof_end(KC_REFINE_VEC);
@@ -1520,11 +1522,12 @@ int jvp_async(tem_ctx *c, const double *v, double *jv) {
                     c->m, N, c->nrhs, c->stream);
   else
     launch_dm_apply_df(c->inc_ptr, c->inc_tet, c->inc_loc, c->tdof, c->ptet, c->mesh.P, v, c->sigma, c->vsdf,
-                       c->mesh.nt, c->me1df, c->xi, c->gdf, c->b, c->m, N, c->nrhs, c->stream);
+                       c->mesh.nt, c->me1df, c->xi, c->gdf, reinterpret_cast<float4 *>(c->r), c->m, N, c->nrhs,
+                       c->stream);   // as the pairs the refinement takes
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   // FP32 mode: the residue sums read the refined pairs directly (no FP64 copy of the solutions)
   const bool fp64 = c->precision == TEM_FP64;
-  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine, fp64));
+  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine, fp64, !fp64));
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   if (fp64)
     launch_residue(c->q_rp, c->q_ci, c->q_val, c->alpha, c->x, jv, c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K,
@@ -1538,13 +1541,18 @@ int jvp_async(tem_ctx *c, const double *v, double *jv) {
 int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
   const int64_t N = c->mesh.N;
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
-  launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->nrhs, c->n_tx,
-                c->n_rx, c->K, c->stream);
+  const bool fp64 = c->precision == TEM_FP64;
+  if (fp64)
+    launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w, c->b, c->m, N, c->nrhs,
+                  c->n_tx, c->n_rx, c->K, c->stream);
+  else   // straight into the pairs the refinement takes
+    launch_qt_rhs(c->qt_dof, c->qt_rp, c->qt_ci, c->qt_val, c->n_qdof, c->alpha, w,
+                  reinterpret_cast<float4 *>(c->r), c->m, N, c->nrhs, c->n_tx, c->n_rx, c->K, c->stream);
   if (g_prof) g_prof->end(KC_JACOBIAN, c->stream);
   // the adjoint solves feed only the cell sums over parameter cells, which
   // converge in fewer corrections than the receivers' fields (46^3 box: within
   // 1e-7 of the converged J^T w after 6)
-  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine_adj, c->precision == TEM_FP64));   // FP32: pairs in xdf
+  TRY(solve_all(c, c->b, N * c->nrhs, c->x, c->refine_adj, fp64, !fp64));   // FP32: b and x as pairs
   if (g_prof) g_prof->begin(KC_JACOBIAN, c->stream);
   if (c->precision == TEM_FP64)
     launch_bilinear(c->ptet, c->mesh.P, c->tdof, c->sigma, c->me1, c->xi, c->g, c->x, jtw, c->m, N, c->nrhs,

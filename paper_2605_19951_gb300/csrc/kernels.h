@@ -344,6 +344,10 @@ void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_va
 void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
                    const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,
                    int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s);
+// the same as the double-float pairs of the FP32 refinement
+void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
+                   const double *qt_val, int n_qdof, const double2 *alpha, const double *w, float4 *rhs,
+                   int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s);
 // h_p[d][x] = xi_p sum_{(t,a) at d} v_t sigma_t sum_b M1_t[a][b] g_p[tdof_t[b]][x]
 void launch_dm_apply(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc,
                      const int32_t *tdof, const int32_t *pidx, const double *v, const double *sigma,
@@ -361,7 +365,7 @@ void launch_bilinear_df(const int32_t *ptet, int64_t P, const int32_t *tdof, con
 // J v right-hand sides from pairs (vs: scratch [nt] for v_t sigma_t as pairs)
 void launch_dm_apply_df(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc, const int32_t *tdof,
                         const int32_t *ptet, int64_t P, const double *v, const double *sigma, float2 *vs, int64_t nt,
-                        const float2 *me1df, const double2 *xi, const float4 *gdf, c128 *h, int m, int64_t N,
+                        const float2 *me1df, const double2 *xi, const float4 *gdf, float4 *h, int m, int64_t N,
                         int nrhs, cudaStream_t s);
 // sparse y = A x (CSR) and y = A^T x via the transpose CSR; beta-scaled accumulate
 void launch_csr_mv(const int64_t *rp, const int32_t *ci, const double *val, const double *x, double *y,

@@ -250,10 +250,18 @@ void launch_residue(const int64_t *q_rp, const int32_t *q_ci, const double *q_va
 
 // rhs_p[qdof][x] = sum_{r} Qt[qdof][r] * sum_j alpha[p][j] w[x][r][j], x < ntx
 // (the padding right-hand sides x >= ntx stay zero)
+// an FP64 complex value stored as is, or as the double-float pairs the FP32 refinement takes
+__device__ __forceinline__ void store_cx(c128 *dst, c128 v) { *dst = v; }
+__device__ __forceinline__ void store_cx(float4 *dst, c128 v) {
+  const dfl a = split(v.x), b = split(v.y);
+  *dst = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+template <typename T>
 __global__ void k_qt_rhs(const int32_t *__restrict__ qt_dof, const int64_t *__restrict__ qt_rp,
                          const int32_t *__restrict__ qt_ci, const double *__restrict__ qt_val,
                          int n_qdof, const double2 *__restrict__ alpha, const double *__restrict__ w,
-                         c128 *__restrict__ rhs, int64_t N, int nrhs, int ntx, int n_rx, int K) {
+                         T *__restrict__ rhs, int64_t N, int nrhs, int ntx, int n_rx, int K) {
   const int p = blockIdx.y;
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= int64_t(n_qdof) * ntx) return;
@@ -271,18 +279,29 @@ __global__ void k_qt_rhs(const int32_t *__restrict__ qt_dof, const int64_t *__re
     acc.x += qt_val[z] * sr;
     acc.y += qt_val[z] * si;
   }
-  rhs[p * N * nrhs + int64_t(qt_dof[q]) * nrhs + x] = acc;
+  store_cx(rhs + p * N * nrhs + int64_t(qt_dof[q]) * nrhs + x, acc);
 }
 
-void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
-                   const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,
-                   int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s) {
-  cudaMemsetAsync(rhs, 0, sizeof(c128) * m * N * nrhs, s);
+template <typename T>
+void qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci, const double *qt_val, int n_qdof,
+            const double2 *alpha, const double *w, T *rhs, int m, int64_t N, int nrhs, int ntx, int n_rx, int K,
+            cudaStream_t s) {
+  cudaMemsetAsync(rhs, 0, sizeof(T) * m * N * nrhs, s);
   const int64_t cnt = int64_t(n_qdof) * ntx;
   if (cnt == 0) return;
   dim3 g(div_up(cnt, 128), m);
   tem::count_launch();
-  k_qt_rhs<<<g, 128, 0, s>>>(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, N, nrhs, ntx, n_rx, K);
+  k_qt_rhs<T><<<g, 128, 0, s>>>(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, N, nrhs, ntx, n_rx, K);
+}
+void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
+                   const double *qt_val, int n_qdof, const double2 *alpha, const double *w, c128 *rhs,
+                   int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s) {
+  qt_rhs(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, m, N, nrhs, ntx, n_rx, K, s);
+}
+void launch_qt_rhs(const int32_t *qt_dof, const int64_t *qt_rp, const int32_t *qt_ci,
+                   const double *qt_val, int n_qdof, const double2 *alpha, const double *w, float4 *rhs,
+                   int m, int64_t N, int nrhs, int ntx, int n_rx, int K, cudaStream_t s) {
+  qt_rhs(qt_dof, qt_rp, qt_ci, qt_val, n_qdof, alpha, w, rhs, m, N, nrhs, ntx, n_rx, K, s);
 }
 
 // ---- mass-derivative products ------------------------------------------------
@@ -350,14 +369,14 @@ __global__ void k_vsig_df(const int32_t *__restrict__ ptet, int64_t P, const dou
 __global__ void k_dm_apply_df(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_tet,
                               const int8_t *__restrict__ inc_loc, const int32_t *__restrict__ tdof,
                               const float2 *__restrict__ vs, const float2 *__restrict__ me1df,
-                              const double2 *__restrict__ xi, const float4 *__restrict__ g, c128 *__restrict__ h,
+                              const double2 *__restrict__ xi, const float4 *__restrict__ g, float4 *__restrict__ h,
                               int64_t N, int nrhs) {
   const int p = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int64_t d = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (d >= N) return;
   const float4 *gp = g + p * N * nrhs;
-  const double2 s = xi[p];
+  const dfl sr = split(xi[p].x), si = split(xi[p].y);
   for (int c0 = 0; c0 < nrhs; c0 += 32) {
     const int x = c0 + lane;
     if (x >= nrhs) break;
@@ -378,14 +397,17 @@ __global__ void k_dm_apply_df(const int64_t *__restrict__ inc_ptr, const int32_t
         ai.add(cm, {gv.z, gv.w});
       }
     }
-    const double acx = df_to_double(ar.value()), acy = df_to_double(ai.value());
-    h[p * N * nrhs + d * nrhs + x] = mk<double>(s.x * acx - s.y * acy, s.x * acy + s.y * acx);
+    // h = xi (ar + i ai), kept as pairs: the refinement takes its right-hand side in this form
+    const dfl acx = ar.value(), acy = ai.value();
+    const dfl hr = df_add(df_mul(sr, acx), df_neg(df_mul(si, acy)));
+    const dfl hi = df_add(df_mul(sr, acy), df_mul(si, acx));
+    h[p * N * nrhs + d * nrhs + x] = make_float4(hr.hi, hr.lo, hi.hi, hi.lo);
   }
 }
 
 void launch_dm_apply_df(const int64_t *inc_ptr, const int32_t *inc_tet, const int8_t *inc_loc, const int32_t *tdof,
                         const int32_t *ptet, int64_t P, const double *v, const double *sigma, float2 *vs, int64_t nt,
-                        const float2 *me1df, const double2 *xi, const float4 *gdf, c128 *h, int m, int64_t N,
+                        const float2 *me1df, const double2 *xi, const float4 *gdf, float4 *h, int m, int64_t N,
                         int nrhs, cudaStream_t s) {
   cudaMemsetAsync(vs, 0, sizeof(float2) * nt, s);
   if (P > 0) {
@@ -474,7 +496,8 @@ __global__ void k_bilinear_df(const int32_t *__restrict__ ptet, int64_t P, const
   const float2 *Me = me1df + int64_t(t) * 36;
   const float4 *gp = g + p * N * nrhs;
   const float4 *zp = z + p * N * nrhs;
-  double ar = 0, ai = 0;
+  // sums over the right-hand sides in double-float pairs (FP64 runs at 1/64 of the FP32 rate here)
+  dfl ar = {0.f, 0.f}, ai = {0.f, 0.f};
   for (int x = lane; x < nrhs; x += 32) {
     float4 gl[6];
     for (int b = 0; b < 6; b++) gl[b] = td[b] >= 0 ? gp[int64_t(td[b]) * nrhs + x] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -496,16 +519,16 @@ __global__ void k_bilinear_df(const int32_t *__restrict__ ptet, int64_t P, const
       si.add(zr, Mi);
       si.add(zi, Mr);
     }
-    ar += df_to_double(sr.value());
-    ai += df_to_double(si.value());
+    ar = df_add(ar, sr.value());
+    ai = df_add(ai, si.value());
   }
   for (int o = 16; o > 0; o >>= 1) {
-    ar += __shfl_down_sync(0xffffffffu, ar, o);
-    ai += __shfl_down_sync(0xffffffffu, ai, o);
+    ar = df_add(ar, {__shfl_down_sync(0xffffffffu, ar.hi, o), __shfl_down_sync(0xffffffffu, ar.lo, o)});
+    ai = df_add(ai, {__shfl_down_sync(0xffffffffu, ai.hi, o), __shfl_down_sync(0xffffffffu, ai.lo, o)});
   }
   if (lane == 0) {
     const double2 s = xi[p];
-    part[p * P + pt] = s.x * ar - s.y * ai;
+    part[p * P + pt] = s.x * df_to_double(ar) - s.y * df_to_double(ai);
   }
 }
 
