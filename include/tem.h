@@ -145,7 +145,9 @@ int tem_poles(tem_ctx *ctx, int32_t m, const double *xi, int32_t n_times,
  * valid; the forward solutions too, but the next tem_jvp / tem_jtvp / tem_lsqr
  * needs a tem_forward first (TEM_ERR_STATE until then).  Synchronises and
  * reallocates the buffers sized by the data: not in asynchronous mode
- * (TEM_ERR_STATE) and not inside a stream capture.  TEM_ERR_ARG for bad
+ * (TEM_ERR_STATE) and not inside a stream capture, and a CUDA graph captured
+ * before the call still refers to the old buffers, so it must not be replayed
+ * after it.  TEM_ERR_ARG for bad
  * arguments or a rank-deficient fit (mu = 0 with too few samples). */
 int tem_times(tem_ctx *ctx, int32_t n_times, const double *t, int32_t n_z, double z_min,
               double z_max, double mu, double *alpha_out);
