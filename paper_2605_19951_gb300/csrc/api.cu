@@ -1,6 +1,7 @@
 // C ABI of libtem (see include/tem.h): context, device memory, and the
 // orchestration of factor / forward / J v / J^T w / LSQR on one GPU.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -308,6 +309,16 @@ int finish(tem_ctx *c, const char *where) {
   TRY(sync(c, where));
   return check_solve_status(c);
 }
+
+// NVTX range around a library call or phase (header-only NVTX v3: free unless
+// a profiler injects itself), so that timelines and ncu --nvtx filters can
+// select the factorisation, the solves and the products.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 struct ProfScope {
   explicit ProfScope(tem_ctx *c) { g_prof = c->prof.on ? &c->prof : nullptr; }
@@ -736,6 +747,7 @@ void nodal_correct(tem_ctx *c, const int *pm, int np) {
 // and later sweeps run over the remaining poles only (a host read per step).
 int solve_all(tem_ctx *c, const c128 *b, int64_t bstride, c128 *x, int steps, bool join = true,
               bool b_in_pairs = false) {
+  Range nvtx_range("solve");
   const int64_t N = c->mesh.N;
   const int nx = c->nrhs, m = c->m;
   cudaStream_t s = c->stream;
@@ -1170,6 +1182,7 @@ int tem_poles(tem_ctx *c, int32_t m, const double *xi, int32_t n_times, const do
 
 int tem_times(tem_ctx *c, int32_t n_times, const double *t, int32_t n_z, double z_min, double z_max, double mu,
               double *alpha_out) {
+  Range nvtx_range("tem_times");
   if (!c) return TEM_ERR_ARG;
   if (!(c->state & ST_POLES)) return fail(c, TEM_ERR_STATE, "tem_poles first");
   if (c->async) return fail(c, TEM_ERR_STATE, "tem_times synchronises: switch the asynchronous mode off first");
@@ -1252,6 +1265,7 @@ int tem_times(tem_ctx *c, int32_t n_times, const double *t, int32_t n_z, double 
 
 int tem_fit_poles(int32_t m, int32_t n_times, const double *t, int32_t n_z, double z_min, double z_max, double mu,
                   int32_t max_iter, double *xi, double *obj, void *stream) {
+  Range nvtx_range("tem_fit_poles");
   tem_ctx *c = nullptr;   // no context: errors go to tem_last_error(NULL)
   if (m <= 0 || m > 32 || n_times <= 0 || n_times > 4096 || !t || !xi || !obj || max_iter < 0 || max_iter > 100000)
     return fail(c, TEM_ERR_ARG, "bad pole-fit arguments (1 <= m <= 32, 1 <= n_times <= 4096)");
@@ -1444,6 +1458,7 @@ int tem_sources(tem_ctx *c, int32_t n_tx, const int64_t *loop_ptr, const int32_t
 }
 
 int tem_factor(tem_ctx *c, const double *log_sigma) {
+  Range nvtx_range("tem_factor");
   if (!c) return TEM_ERR_ARG;
   const int need = ST_MESH | ST_POLES | ST_SOURCES;
   if ((c->state & need) != need) return fail(c, TEM_ERR_STATE, "tem_mesh, tem_poles and tem_sources first");
@@ -1496,6 +1511,7 @@ int tem_factor(tem_ctx *c, const double *log_sigma) {
 }
 
 int tem_forward(tem_ctx *c, double *d) {
+  Range nvtx_range("tem_forward");
   if (!c) return TEM_ERR_ARG;
   if (!(c->state & ST_FACTORED)) return fail(c, TEM_ERR_STATE, "tem_factor first");
   if (!d) return fail(c, TEM_ERR_ARG, "d is NULL");
@@ -1566,6 +1582,7 @@ int jtvp_async(tem_ctx *c, const double *w, double *jtw) {
 }  // namespace
 
 int tem_jvp(tem_ctx *c, const double *v, double *jv) {
+  Range nvtx_range("tem_jvp");
   if (!c) return TEM_ERR_ARG;
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!v || !jv) return fail(c, TEM_ERR_ARG, "NULL vector");
@@ -1575,6 +1592,7 @@ int tem_jvp(tem_ctx *c, const double *v, double *jv) {
 }
 
 int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
+  Range nvtx_range("tem_jtvp");
   if (!c) return TEM_ERR_ARG;
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!w || !jtw) return fail(c, TEM_ERR_ARG, "NULL vector");
@@ -1585,6 +1603,7 @@ int tem_jtvp(tem_ctx *c, const double *w, double *jtw) {
 
 int tem_lsqr(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref, double lambda,
              int32_t n_iter, double *dm) {
+  Range nvtx_range("tem_lsqr");
   if (!c) return TEM_ERR_ARG;
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!d_obs || !wd || !m_ref || !dm || n_iter < 0 || !(lambda >= 0)) return fail(c, TEM_ERR_ARG, "bad LSQR args");
@@ -1647,6 +1666,7 @@ int tem_set_wait_limit(tem_ctx *c, uint32_t max_polls, double max_seconds) {
 
 int tem_gn_eval(tem_ctx *c, const double *d_obs, const double *wd, const double *m_ref, double lambda,
                 const double *dm, double *grad, double *out) {
+  Range nvtx_range("tem_gn_eval");
   if (!c) return TEM_ERR_ARG;
   if (!(c->state & ST_FORWARD)) return fail(c, TEM_ERR_STATE, "tem_forward first");
   if (!d_obs || !wd || !m_ref || !out || !(lambda >= 0) || (dm && !grad)) return fail(c, TEM_ERR_ARG, "bad arguments");
@@ -1730,6 +1750,7 @@ int tem_status(tem_ctx *c) {
 
 int tem_batch(tem_ctx **ctx, int32_t n, int32_t ops, const double *const *log_sigma, double *const *d,
               const double *const *w, double *const *jtw) {
+  Range nvtx_range("tem_batch");
   if (!ctx || n <= 0 || (ops & ~(TEM_BATCH_FACTOR | TEM_BATCH_FORWARD | TEM_BATCH_JTVP)) || ops == 0)
     return fail(nullptr, TEM_ERR_ARG, "tem_batch: bad contexts or operations");
   for (int i = 0; i < n; i++) {
