@@ -596,13 +596,28 @@ def run_peaks(args):
     print(json.dumps(out), flush=True)
 
 
+def oracle_config_baseline(s, xi, al, v, w):
+    """CPU baseline leg of --configs: the oracle as it stands on this host
+    (poles on parallel threads), factor + forward, then one J.v + J^T.w pair."""
+    from oracle.tem import Oracle
+    t0 = time.perf_counter()
+    o = Oracle(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al)
+    o.set_model(s.log_sigma())
+    o.forward()
+    t1 = time.perf_counter()
+    o.jvp(v)
+    o.jtvp(w)
+    t2 = time.perf_counter()
+    return {"oracle_factor_forward_s": round(t1 - t0, 2), "oracle_pair_s": round(t2 - t1, 2),
+            "oracle_threads": int(o.threads), "nproc": os.cpu_count()}
+
+
 def run_configs(args):
     """Configurations C1-C3: GPU factor, forward and J.v + J^T.w pair times
     (CUDA events, median of 3) in both precisions, and the oracle on this host
     (factor + forward + one pair, poles on parallel threads) for C1 and C2."""
     import numpy as np
     import torch
-    from oracle.tem import Oracle
     from paper_2605_19951_gb300 import inputs, tem
     torch.cuda.set_device(0)
     rows = []
@@ -632,16 +647,7 @@ def run_configs(args):
                 mdl.close()
             torch.cuda.empty_cache()
         if cfg <= 2:
-            t0 = time.perf_counter()
-            o = Oracle(s.xyz, s.tets, s.sigma, s.is_param, s.loops, s.rx, xi, al)
-            o.set_model(s.log_sigma())
-            o.forward()
-            t1 = time.perf_counter()
-            o.jvp(v)
-            o.jtvp(w)
-            t2 = time.perf_counter()
-            row.update({"oracle_factor_forward_s": round(t1 - t0, 2), "oracle_pair_s": round(t2 - t1, 2),
-                        "oracle_threads": int(o.threads), "nproc": os.cpu_count()})
+            row.update(oracle_config_baseline(s, xi, al, v, w))
         rows.append(row)
         print(json.dumps(row), flush=True)
 
