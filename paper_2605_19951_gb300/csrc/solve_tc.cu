@@ -430,12 +430,11 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
     if (!__all_sync(kFull, ok)) break;
     tc::fence_after();
     if constexpr (MODE == PM_UPD) {
-      // F[r][s] -= acc for the tile's columns s >= t0 with r >= s, r = row m of the tile (lane):
-      // the accumulator is read in two halves of 16 columns (32 registers each), and within a
-      // half four columns at a time have all their loads issued before their stores, so a
-      // batch waits for one memory latency rather than four (distinct entries; the compiler
-      // cannot prove it and would keep each load behind the previous store).  The buffer is
-      // released after both halves.
+      // F[r][s] -= acc for the tile's columns s >= t0 with r >= s, r = row m of the tile (lane),
+      // as an atomic add of -acc: every entry is updated by exactly one item of a launch, so
+      // the result is the same as load, subtract, store (o + (-v) == o - v), but nothing waits
+      // for the load (the L2 does the update), which a read-modify-write per column did at
+      // one memory latency per batch.  The accumulator is read in two halves of 16 columns.
       const int m = e;
       const FrontDev f = a.F[it.t.map];
       const int64_t r = int64_t(it.t.y0) + m, k = f.k, n = f.n;
@@ -443,7 +442,6 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
       c64 *up = a.Uw + int64_t(it.p) * a.ustride + f.uofs;
       const int q0 = int(it.t.mfirst);
       const bool row_ok = m < it.t.mrows;
-      auto col = [&](int64_t sc) { return sc < k ? lp + sc * f.ld + r : up + (sc - k) * (n - k) + (r - k); };
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         float v[32];
@@ -456,23 +454,12 @@ __device__ void ki_epilogue(const ProdArgs &a, KiShared &sh, int e) {
         }
         if (!row_ok) continue;
 #pragma unroll
-        for (int qb = 0; qb < 16; qb += 4) {
-          c64 o[4];
-          unsigned msk = 0;
-#pragma unroll
-          for (int x = 0; x < 4; x++) {
-            const int q = 16 * h + qb + x;
-            const int64_t sc = int64_t(it.t.bbase) + q;
-            if (q < q0 || sc >= n || sc > r) continue;
-            msk |= 1u << x;
-            o[x] = *col(sc);
-          }
-#pragma unroll
-          for (int x = 0; x < 4; x++)
-            if ((msk >> x) & 1u) {
-              const int q = 16 * h + qb + x, c = qb + x;
-              *col(int64_t(it.t.bbase) + q) = mk<float>(o[x].x - v[2 * c], o[x].y - v[2 * c + 1]);
-            }
+        for (int x = 0; x < 16; x++) {
+          const int q = 16 * h + x;
+          const int64_t sc = int64_t(it.t.bbase) + q;
+          if (q < q0 || sc >= n || sc > r) continue;
+          c64 *dst = sc < k ? lp + sc * f.ld + r : up + (sc - k) * (n - k) + (r - k);
+          atomicAdd(reinterpret_cast<float2 *>(dst), make_float2(-v[2 * x], -v[2 * x + 1]));
         }
       }
       tc::fence_before();
