@@ -148,7 +148,8 @@ int tem_poles(tem_ctx *ctx, int32_t m, const double *xi, int32_t n_times,
  * (TEM_ERR_STATE) and not inside a stream capture, and a CUDA graph captured
  * before the call still refers to the old buffers, so it must not be replayed
  * after it.  TEM_ERR_ARG for bad
- * arguments or a rank-deficient fit (mu = 0 with too few samples). */
+ * arguments, a fit larger than (n_z + 1 + 2m) n_times = 2^31, or a rank-deficient
+ * fit (mu = 0 with too few samples). */
 int tem_times(tem_ctx *ctx, int32_t n_times, const double *t, int32_t n_z, double z_min,
               double z_max, double mu, double *alpha_out);
 
@@ -169,8 +170,9 @@ int tem_times(tem_ctx *ctx, int32_t n_times, const double *t, int32_t n_z, doubl
  *   obj    host [3] out: f at the start, f at the end, steps taken
  *   stream cudaStream_t (NULL: the default stream) of the current device
  * Needs no context (errors: tem_last_error(NULL)); allocates and frees its
- * own work arrays and synchronises.  TEM_ERR_ARG for bad arguments or
- * starting poles that leave the fit rank deficient. */
+ * own work arrays and synchronises.  TEM_ERR_ARG for bad arguments, a fit
+ * larger than (n_z + 1 + 2m) 2m n_times = 2^31, or starting poles that leave
+ * the fit rank deficient. */
 int tem_fit_poles(int32_t m, int32_t n_times, const double *t, int32_t n_z, double z_min, double z_max,
                   double mu, int32_t max_iter, double *xi, double *obj, void *stream);
 

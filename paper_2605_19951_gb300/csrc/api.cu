@@ -1194,6 +1194,8 @@ int tem_times(tem_ctx *c, int32_t n_times, const double *t, int32_t n_z, double 
     return fail(c, TEM_ERR_ARG, "bad sample set (2 <= n_z <= 2^20, 0 < z_min < z_max finite, mu >= 0)");
   const int m = c->m, K = n_times;
   const int64_t rows = int64_t(n_z) + 1 + 2 * m;
+  if (rows * K > (int64_t(1) << 31))   // the right-hand sides of the fit: 16 GB at this bound
+    return fail(c, TEM_ERR_ARG, "residue fit too large: (n_z + 1 + 2m) n_times must stay below 2^31");
   cudaStream_t s = c->stream;
   // work arrays of this call, released on every return
   struct Scratch {
@@ -1279,6 +1281,8 @@ int tem_fit_poles(int32_t m, int32_t n_times, const double *t, int32_t n_z, doub
       return fail(c, TEM_ERR_ARG, "starting poles need Re xi < 0 < Im xi");
   const int K = n_times, nc = 2 * m;
   const int64_t rows = int64_t(n_z) + 1 + nc;
+  if (rows * nc * K > (int64_t(1) << 31))   // the Jacobian tails: 16 GB at this bound
+    return fail(c, TEM_ERR_ARG, "pole fit too large: (n_z + 1 + 2m) 2m n_times must stay below 2^31");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   struct Scratch {
     std::vector<void *> p;

@@ -160,6 +160,8 @@ def test_times_arguments_are_checked():
                 mdl.set_times(np.array(bad, dtype=np.float64))
         with pytest.raises(tem.TemError, match="TEM_ERR_ARG"):
             mdl.set_times(inputs.times_log(8), z_min=1e3, z_max=1e2)
+        with pytest.raises(tem.TemError, match="too large"):   # refused before anything is allocated
+            mdl.set_times(inputs.times_log(4096), n_z=1 << 20)
         assert mdl.info()["n_times"] == 16   # a refused call changes nothing
     finally:
         mdl.close()
@@ -201,3 +203,5 @@ def test_pole_fit_arguments_are_checked():
             tem.tem_fit_poles(bad, t)
     with pytest.raises(tem.TemError, match="TEM_ERR_ARG"):
         tem.tem_fit_poles(rational.seed_poles(4), np.array([-1.0]))
+    with pytest.raises(tem.TemError, match="too large"):
+        tem.tem_fit_poles(rational.seed_poles(8), inputs.times_log(200), n_z=1 << 20)
