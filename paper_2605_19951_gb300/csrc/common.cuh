@@ -68,6 +68,11 @@ __device__ __forceinline__ void atomic_add_cx(cx<R> *p, cx<R> v) {
   atomicAdd(&p->x, v.x);
   atomicAdd(&p->y, v.y);
 }
+// complex FP32: one 8-byte vector atomic (sm_90 and later)
+template <>
+__device__ __forceinline__ void atomic_add_cx<float>(cx<float> *p, cx<float> v) {
+  atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v.x, v.y));
+}
 
 // Front metadata as seen by the kernels.
 struct FrontDev {

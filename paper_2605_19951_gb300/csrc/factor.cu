@@ -111,22 +111,16 @@ __global__ void k_extend_add(cx<R> *__restrict__ L, int64_t lstride, cx<R> *__re
   const cx<R> *uc = U + p * ustride + C.uofs + int64_t(j) * bc;
   const int32_t *rl = rel + C.rel_off;
   const int32_t rj = rl[j];
+  // each parent entry receives at most one child entry per launch (one child slot), so the
+  // atomic adds equal load, add, store without a round trip per entry; the relative map is
+  // only read here
   if (rj < Pf.k) {
     cx<R> *dst = L + p * lstride + Pf.lofs + int64_t(rj) * Pf.ld;
-    for (int32_t i = j + threadIdx.x; i < bc; i += blockDim.x) {
-      cx<R> v = uc[i];
-      int32_t ri = rl[i];
-      cx<R> o = dst[ri];
-      dst[ri] = o + v;
-    }
+    for (int32_t i = j + threadIdx.x; i < bc; i += blockDim.x) atomic_add_cx(dst + __ldg(rl + i), uc[i]);
   } else {
     cx<R> *dst = U + p * ustride + Pf.uofs + int64_t(rj - Pf.k) * bp;
-    for (int32_t i = j + threadIdx.x; i < bc; i += blockDim.x) {
-      cx<R> v = uc[i];
-      int32_t ri = rl[i] - Pf.k;   // >= 0: rows below a column >= k lie in the update block
-      cx<R> o = dst[ri];
-      dst[ri] = o + v;
-    }
+    // rows below a column >= k lie in the update block
+    for (int32_t i = j + threadIdx.x; i < bc; i += blockDim.x) atomic_add_cx(dst + (__ldg(rl + i) - Pf.k), uc[i]);
   }
 }
 
@@ -345,7 +339,9 @@ __global__ void __launch_bounds__(256) k_update(cx<R> *__restrict__ L, int64_t l
 #pragma unroll
     for (int i = 0; i < PT; i++) {
       const int64_t r = r0 + tx + 16 * i;
-      if (r < n && r >= s) col[r - roff] = col[r - roff] - acc[i][j];
+      // one tile per entry in a launch: an atomic add of -acc equals load, subtract, store
+      // and leaves the read to the L2 instead of a round trip per entry
+      if (r < n && r >= s) atomic_add_cx(col + (r - roff), mk<R>(-acc[i][j].x, -acc[i][j].y));
     }
   }
 }
